@@ -1,0 +1,414 @@
+#!/usr/bin/env python3
+"""Benchmark of the structured-grid solver hot path on one GB300 (or N replicas).
+
+One STEP is one pass of the whole hot path over the 3-D Poisson workload
+(256^3 interior nodes, 16.8 M unknowns, FP64, rhs ~ U(-1, 1) from seed 0):
+  a1  one stencil SpMV y = A b                     (7-point Laplacian)
+  a2  Jacobi, 200 sweeps                           (Laplacian)
+  a3  lexicographic Gauss-Seidel, 200 sweeps       (Laplacian)
+  a4  CG to 1e-10 relative residual from x0 = 0    (Laplacian)
+  a5  BiCGStab to 1e-10 from x0 = 0                (7-point upwind
+      convection-diffusion, beta = (1, 0.5, 0.25) scaled to cell Peclet 0.5)
+value = algorithmic bytes of the step / step time (GB/s), with the inputs
+already resident in HBM; e2e = the same metric through the public API with
+the right-hand side copied in from pinned host memory and every solution
+copied back out inside the timed region.
+
+The path does not shard (each GPU solves its own system): with --gpus N
+every rank runs an independent replica ("replicas only", weak scaling).
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solver GB/s & % HBM peak; time-to-1e-10 residual, mixed/batched vs plain FP64"
+
+# Algorithmic bytes per unknown (FP64) -- the minimum traffic of each step of
+# the method, counting every vector the algorithm must read and write once.
+BYTES = {
+    "spmv": 16.0,          # read x, write y
+    "jacobi": 24.0,        # per sweep: read x, b; write x'
+    "gauss_seidel": 24.0,  # per sweep: read x, b; write x (in place)
+    "cg": 64.0,            # per iteration: read r, p_old / write p; read x, p, r / write x, r
+    "bicgstab": 136.0,     # per iteration (17 vector passes of 8 B)
+}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=256, help="grid side (default 256 -> 256^3)")
+    p.add_argument("--sweeps", type=int, default=200)
+    p.add_argument("--tol", type=float, default=1e-10)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands on a bounded sample
+# ---------------------------------------------------------------------------
+def oracle_sample(n: int, b: np.ndarray):
+    """Runs the oracle on a bounded sample of the step; returns (bytes, seconds, description)."""
+    import oracle
+    from paper_2305_05988_gb300 import inputs
+    shape = (n, n, n)
+    N = n ** 3
+    A = oracle.Operator(shape)
+    U = oracle.Operator(shape, oracle.UPWIND, inputs.upwind_beta(shape, 0.5))
+    work = []
+    t0 = time.perf_counter()
+    A.spmv(b)
+    work.append(("spmv", 1, time.perf_counter() - t0))
+    t0 = time.perf_counter()
+    oracle.jacobi(A, b, maxit=2)
+    work.append(("jacobi", 2, time.perf_counter() - t0))
+    t0 = time.perf_counter()
+    oracle.gauss_seidel(A, b, maxit=2)
+    work.append(("gauss_seidel", 2, time.perf_counter() - t0))
+    t0 = time.perf_counter()
+    oracle.cg(A, b, maxit=2, tol=0.0)
+    work.append(("cg", 2, time.perf_counter() - t0))
+    t0 = time.perf_counter()
+    oracle.bicgstab(U, b, maxit=1, tol=0.0)
+    work.append(("bicgstab", 1, time.perf_counter() - t0))
+    nbytes = sum(BYTES[k] * N * c for k, c, _ in work)
+    secs = sum(t for _, _, t in work)
+    desc = ("%d^3: 1 SpMV, 2 Jacobi sweeps, 2 GS sweeps, 2 CG iterations (incl. setup), "
+            "1 BiCGStab iteration (incl. setup); single-threaded C oracle" % n)
+    return nbytes, secs, desc
+
+
+# ---------------------------------------------------------------------------
+# reference arm
+# ---------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_2305_05988_gb300 import inputs
+    n = args.n
+    b = inputs.rhs_uniform((n, n, n), 0)
+    for _ in range(args.warmup):
+        oracle_sample(n, b)
+    tot_b, tot_s = 0.0, 0.0
+    desc = ""
+    for _ in range(args.steps):
+        nb, s, desc = oracle_sample(n, b)
+        tot_b += nb
+        tot_s += s
+    value = tot_b / tot_s / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "poisson3d %d^3 FP64 (bounded oracle sample per step)" % n},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world, dist):
+    import torch
+
+    import paper_2305_05988_gb300 as hs
+    from paper_2305_05988_gb300 import inputs
+    from paper_2305_05988_gb300 import _lib
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.n
+    shape = (n, n, n)
+    N = n ** 3
+    b_host = inputs.rhs_uniform(shape, 0)
+    b = torch.from_numpy(b_host).to(dev)
+    A = hs.Operator.laplacian(shape)
+    beta = inputs.upwind_beta(shape, 0.5)
+    U = hs.Operator.upwind(shape, beta)
+    stream = torch.cuda.current_stream(dev)
+    maxk = 20000
+    # workspaces are allocated once, outside the timed region
+    xs = {k: torch.zeros(N, dtype=torch.float64, device=dev) for k in ("y", "jacobi", "gs", "cg", "bicgstab")}
+
+    def step(bv, record=None):
+        info = {}
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)] if record is not None else None
+        if ev:
+            ev[0].record(stream)
+        A.spmv(bv, out=xs["y"])
+        if ev:
+            ev[1].record(stream)
+        xs["jacobi"].zero_()
+        _, info["jacobi"] = hs.jacobi(A, bv, xs["jacobi"], maxit=args.sweeps, inplace=True)
+        if ev:
+            ev[2].record(stream)
+        xs["gs"].zero_()
+        _, info["gauss_seidel"] = hs.gauss_seidel(A, bv, xs["gs"], maxit=args.sweeps, inplace=True)
+        if ev:
+            ev[3].record(stream)
+        xs["cg"].zero_()
+        _, info["cg"] = hs.cg(A, bv, xs["cg"], tol=args.tol, maxit=maxk, inplace=True)
+        if ev:
+            ev[4].record(stream)
+        xs["bicgstab"].zero_()
+        _, info["bicgstab"] = hs.bicgstab(U, bv, xs["bicgstab"], tol=args.tol, maxit=maxk, inplace=True)
+        if ev:
+            ev[5].record(stream)
+            record.append(ev)
+        return info
+
+    def step_bytes(info):
+        tot = BYTES["spmv"] * N
+        tot += BYTES["jacobi"] * N * info["jacobi"].iters
+        tot += BYTES["gauss_seidel"] * N * info["gauss_seidel"].iters
+        tot += BYTES["cg"] * N * info["cg"].iters
+        tot += BYTES["bicgstab"] * N * info["bicgstab"].iters
+        return tot
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(max(args.warmup, 0)):
+        info = step(b)
+    torch.cuda.synchronize()
+
+    # ---- timed region (device-resident inputs) ----
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    recs = []
+    infos = []
+    e0.record(stream)
+    for _ in range(args.steps):
+        infos.append(step(b, recs))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    total_bytes = sum(step_bytes(i) for i in infos) * world
+    value = total_bytes / (ms * 1e-3) / 1e9
+
+    # per-solver breakdown from the in-step events
+    names = ["spmv", "jacobi", "gauss_seidel", "cg", "bicgstab"]
+    per = {k: [] for k in names}
+    for ev in recs:
+        for q, k in enumerate(names):
+            per[k].append(ev[q].elapsed_time(ev[q + 1]))
+    last = infos[-1]
+    breakdown = {}
+    for k in names:
+        t_ms = statistics.median(per[k])
+        its = 1 if k == "spmv" else last[k].iters
+        gbs = BYTES[k] * N * its / (t_ms * 1e-3) / 1e9
+        d = {"ms": round(t_ms, 4), "iters": its, "alg_GBps": round(gbs, 1)}
+        if k != "spmv":
+            d["status"] = last[k].status
+            d["true_rel_res"] = last[k].true_rel_res
+            if k in ("cg", "bicgstab"):
+                d["time_to_tol_ms"] = round(t_ms, 4)
+                d["us_per_iter"] = round(1e3 * t_ms / max(its, 1), 2)
+            else:
+                d["us_per_sweep"] = round(1e3 * t_ms / max(its, 1), 2)
+        breakdown[k] = d
+
+    # ---- roofline of the dominant kernel (largest share of the step) ----
+    peak, peak_kind = load_peaks()
+    dom = max(["jacobi", "gauss_seidel", "cg", "bicgstab"], key=lambda k: statistics.median(per[k]))
+    ra, rb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    dts = []
+    its = 0
+    for _ in range(reps):
+        xs[dom].zero_()
+        torch.cuda.synchronize()
+        ra.record(stream)
+        if dom == "cg":
+            _, inf = hs.cg(A, b, xs["cg"], tol=args.tol, maxit=maxk, inplace=True, true_residual=False)
+        elif dom == "bicgstab":
+            _, inf = hs.bicgstab(U, b, xs["bicgstab"], tol=args.tol, maxit=maxk, inplace=True, true_residual=False)
+        elif dom == "jacobi":
+            _, inf = hs.jacobi(A, b, xs["jacobi"], maxit=args.sweeps, inplace=True, true_residual=False)
+        else:
+            _, inf = hs.gauss_seidel(A, b, xs["gs"], maxit=args.sweeps, inplace=True, true_residual=False)
+        rb.record(stream)
+        torch.cuda.synchronize()
+        dts.append(ra.elapsed_time(rb))
+        its = inf.iters
+    dt = statistics.median(dts)
+    achieved = BYTES[dom] * N * its / (dt * 1e-3) / 1e9
+    kname = {"cg": "k_cg", "bicgstab": "k_bicgstab", "jacobi": "k_jacobi", "gauss_seidel": "k_gs"}[dom]
+    roofline = {"kernel": kname + " (FP64, persistent: one launch per solve)", "bound": "hbm",
+                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "peak_source": peak_kind, "traffic": None,
+                "alg_bytes_per_launch": BYTES[dom] * N * its, "launch_ms": round(dt, 3), "iters": its}
+
+    # ---- e2e: host buffers, copies inside the timed region ----
+    e2e = None
+    if not args.no_e2e:
+        bp = torch.from_numpy(b_host).pin_memory()
+        outs = {k: torch.empty(N, dtype=torch.float64).pin_memory() for k in xs}
+        bd = torch.empty(N, dtype=torch.float64, device=dev)
+        barrier()
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e_infos = []
+        f0.record(stream)
+        for _ in range(args.steps):
+            bd.copy_(bp, non_blocking=True)
+            e_infos.append(step(bd))
+            for k in xs:
+                outs[k].copy_(xs[k], non_blocking=True)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ems = f0.elapsed_time(f1)
+        if dist is not None:
+            t = torch.tensor([ems], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e_bytes = sum(step_bytes(i) for i in e_infos) * world
+        e2e = {"value": e_bytes / (ems * 1e-3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": 8 * N,
+               "d2h_bytes_per_step": 8 * N * len(xs), "ms_per_step": ems / args.steps}
+
+    # ---- CPU baseline (rank 0, N = 1 only) ----
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        nb, secs, desc = oracle_sample(n, b_host)
+        cpu = {"value": nb / secs / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": desc,
+               "seconds": round(secs, 2)}
+
+    # kernels launched per step: spmv 1; jacobi, cg, bicgstab: control init +
+    # persistent solver + residual + finalize = 4 each; gauss-seidel: solver +
+    # residual + finalize = 3 (its control block is uploaded by a copy)
+    launches_per_step = 1 + 4 + 3 + 4 + 4
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "poisson3d %d^3 FP64: SpMV + Jacobi x%d + lexicographic GS x%d + CG and "
+                                   "BiCGStab(upwind, Pe 0.5) to %g" % (n, args.sweeps, args.sweeps, args.tol),
+                       "grid": [n, n, n], "unknowns": N, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs and solver state (>= 2 x 134 MB per solver) exceed the 129 MB L2; no flush"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps, "clocks": clocks, "solvers": breakdown,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if args.impl == "ours" and world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        tdist.init_process_group("nccl")
+        dist = tdist
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, dist)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

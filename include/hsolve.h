@@ -1,0 +1,194 @@
+/*
+ * hsolve.h -- C ABI of libhsolve, a single-GPU (sm_103a) library of the four
+ * classical iterative methods studied in Martinez-Ferrer, Arslan & Beltran,
+ * "Improving the performance of classical linear algebra iterative methods
+ * via hybrid parallelism" (arXiv 2305.05988): Jacobi, Gauss-Seidel,
+ * conjugate gradient and BiCGStab, applied matrix-free to structured-grid
+ * finite-difference operators.
+ *
+ * The paper solves A x = b with a known sparse A arising from a centred
+ * stencil on a structured mesh (section 3.1, section 4.1).  Here A is never
+ * stored: it is one of three stencil operators on a grid of n_x [* n_y
+ * [* n_z]] interior nodes, spacing h_d = 1/(n_d + 1), homogeneous Dirichlet
+ * boundary (zero ghost values):
+ *   - Laplacian   A = -Delta_h                (5-point 2-D, 7-point 3-D)
+ *   - upwind      -Delta u + beta . grad u, beta_d >= 0, first-order upwind
+ *   - diffusion   -div(k grad u), harmonic-mean face coefficients, a
+ *                 boundary face using the cell's own k.
+ *
+ * Conventions shared by every entry point
+ *   - Vectors are dense, contiguous, lexicographic idx = i + n_x (j + n_y k)
+ *     (i fastest), of length N = prod n_d, in DEVICE memory, 16-byte
+ *     aligned, owned by the caller; the library never frees or retains them.
+ *   - dtype HS_F64 means IEEE binary64 elements, HS_F32 binary32.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Every call is stream-ordered; the solver entry points
+ *     synchronise `stream` before returning because they report a host-side
+ *     result.
+ *   - Solvers take a caller-allocated device workspace of at least
+ *     hs_workspace_size() bytes (256-byte aligned); the library allocates
+ *     no device memory per call.  Workspaces must not be shared by calls
+ *     that may overlap on the GPU.
+ *   - Errors are returned, never thrown or trapped on the device.  After a
+ *     non-OK status hs_last_error() gives a message (thread-local).
+ *   - Every device-side wait (grid barrier, wavefront flag) is bounded; a
+ *     wait that runs out ends the kernel with HS_ERR_TIMEOUT instead of
+ *     hanging.
+ */
+#ifndef HSOLVE_H
+#define HSOLVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HS_OK = 0,               /* converged, or ran the requested sweeps            */
+    HS_NOT_CONVERGED = 1,    /* maxit reached; x holds the last iterate           */
+    HS_ERR_INVALID = -1,     /* bad argument (null pointer, shape, dtype, ...)    */
+    HS_ERR_CUDA = -2,        /* a CUDA runtime call failed                         */
+    HS_ERR_BREAKDOWN = -3,   /* a Krylov denominator vanished (e.g. p.Ap <= 0)     */
+    HS_ERR_NONFINITE = -4,   /* NaN or Inf appeared in a reduction                 */
+    HS_ERR_TIMEOUT = -5,     /* a bounded device-side wait ran out                 */
+    HS_ERR_WORKSPACE = -6    /* workspace missing, misaligned or too small         */
+} hs_status;
+
+typedef enum { HS_F64 = 0, HS_F32 = 1 } hs_dtype;
+
+typedef enum {
+    HS_SOLVER_JACOBI = 0,
+    HS_SOLVER_GAUSS_SEIDEL = 1,
+    HS_SOLVER_CG = 2,
+    HS_SOLVER_BICGSTAB = 3
+} hs_solver;
+
+typedef enum { HS_GS_FORWARD = 0, HS_GS_BACKWARD = 1, HS_GS_SYMMETRIC = 2 } hs_gs_mode;
+
+typedef struct hs_grid hs_grid;   /* opaque, library-owned */
+typedef struct hs_op hs_op;       /* opaque, library-owned */
+
+/*
+ * Solver options.  Set struct_size = sizeof(hs_opts); fields beyond a
+ * caller's struct_size take their defaults.  Pass NULL for all defaults.
+ */
+typedef struct {
+    size_t struct_size;
+    int gs_mode;            /* hs_gs_mode; default HS_GS_FORWARD (one sweep per
+                               iteration; HS_GS_SYMMETRIC is the paper's
+                               symmetric GS, section 3.1)                        */
+    int check_every;        /* GS with tol > 0: test the residual every this many
+                               iterations (default 1)                           */
+    double restart_eps;     /* BiCGStab restart threshold eps' on sqrt|alpha_n|,
+                               Algorithm 2 (default 1e-5; 0 disables)           */
+    int true_residual;      /* 1 (default): compute ||b - A x|| / ||b|| of the
+                               returned x into hs_result.true_rel_res           */
+    double timeout_s;       /* bound on any single device-side wait, seconds
+                               (default 2.0)                                     */
+    int max_outer;          /* mixed precision: maximum refinement steps (20)   */
+    double inner_tol;       /* mixed precision: inner relative tolerance (1e-5) */
+    int inner_solver;       /* mixed precision: HS_SOLVER_CG or _BICGSTAB (CG)  */
+    int inner_maxit;        /* mixed precision: inner iteration cap (10000)     */
+} hs_opts;
+
+typedef struct {
+    int iters;              /* iterations (sweeps for Jacobi / forward or backward
+                               GS, forward+backward pairs for symmetric GS)     */
+    int status;             /* hs_status of the solve                            */
+    double rel_res;         /* last recursive relative residual (Krylov) or the
+                               relative residual of the returned iterate        */
+    double true_rel_res;    /* ||b - A x|| / ||b|| of the returned x, or -1      */
+    int restarts;           /* BiCGStab restarts taken                           */
+    int outer;              /* mixed precision: refinement steps taken           */
+    long long inner_iters;  /* mixed precision: total inner iterations           */
+} hs_result;
+
+/* ---- grids and operators (host objects; no device memory is allocated) --- */
+
+/* ndim in {1, 2, 3}; n[d] >= 1 for d < ndim (entries beyond ndim ignored).
+ * N = prod n_d must be below 2^31.  Returns HS_ERR_INVALID otherwise. */
+hs_status hs_grid_create(int ndim, const int64_t n[3], hs_grid **out);
+void hs_grid_destroy(hs_grid *g);
+
+/* Operators keep a copy of the grid; the grid may be destroyed afterwards. */
+hs_status hs_op_laplacian(const hs_grid *g, hs_op **out);
+/* beta[d] >= 0 and finite for d < ndim (first-order upwind). */
+hs_status hs_op_convdiff_upwind(const hs_grid *g, const double beta[3], hs_op **out);
+/* k_dev: device array of N coefficients (> 0) of type kdt, BORROWED: it must
+ * stay valid and unchanged for the operator's lifetime. */
+hs_status hs_op_diffusion(const hs_grid *g, hs_dtype kdt, const void *k_dev, hs_op **out);
+void hs_op_destroy(hs_op *op);
+/* Number of unknowns N of an operator (0 for NULL). */
+int64_t hs_op_size(const hs_op *op);
+
+/* ---- single operator application --------------------------------------- */
+
+/* y = A x (the sparse matrix-vector product of section 3.1, matrix-free).
+ * x, y: device vectors of N elements of `dtype`; must not alias. */
+hs_status hs_spmv(const hs_op *A, hs_dtype dtype, const void *x, void *y, void *stream);
+
+/* r = b - A x (device vectors of N elements of dtype; r must not alias b or x). */
+hs_status hs_residual(const hs_op *A, hs_dtype dtype, const void *b, const void *x, void *r,
+                      void *stream);
+
+/* ---- solvers --------------------------------------------------------------
+ * Common arguments:
+ *   b        device right-hand side (N elements of dtype)
+ *   x        device initial guess on entry, solution on exit (N elements)
+ *   tol      relative-residual target ||b - A x|| / ||b|| (Krylov: recursive
+ *            residual).  tol == 0 runs exactly maxit iterations (Jacobi/GS).
+ *   maxit    iteration cap (>= 0)
+ *   opts     NULL for defaults
+ *   ws       device workspace, ws_bytes >= hs_workspace_size(...)
+ *   res      host hs_result, may be NULL
+ *   hist     host array of maxit + 1 doubles, may be NULL: hist[k] is the
+ *            relative residual after k iterations (entries beyond res.iters
+ *            are left untouched).  Jacobi / GS record it only when tol > 0.
+ * A zero right-hand side returns x = 0 after 0 iterations.
+ */
+hs_status hs_workspace_size(const hs_op *A, hs_solver solver, hs_dtype dtype, const hs_opts *opts,
+                            int maxit, size_t *bytes);
+
+/* Jacobi (section 3.1): x_i <- (b_i - sum_{j != i} a_ij x_j) / a_ii, undamped,
+ * out of place.  With tol > 0 the residual of each iterate is fused into the
+ * next sweep and the first iterate x_k with relative residual <= tol is
+ * returned (iters = k). */
+hs_status hs_jacobi(const hs_op *A, hs_dtype dtype, const void *b, void *x, double tol, int maxit,
+                    const hs_opts *opts, void *ws, size_t ws_bytes, void *stream, hs_result *res,
+                    double *hist);
+
+/* Gauss-Seidel (section 3.1), exactly lexicographic: every update uses the
+ * entries already updated in the same sweep (forward: idx ascending,
+ * backward: descending; symmetric = forward then backward).  No recolouring:
+ * the result equals the sequential sweep up to rounding. */
+hs_status hs_gauss_seidel(const hs_op *A, hs_dtype dtype, const void *b, void *x, double tol,
+                          int maxit, const hs_opts *opts, void *ws, size_t ws_bytes, void *stream,
+                          hs_result *res, double *hist);
+
+/* Conjugate gradient, the classical method HPCCG runs (section 3.2), with the
+ * stencil, vector updates and dot products fused into two passes per
+ * iteration.  A must be symmetric positive definite (Laplacian, diffusion). */
+hs_status hs_cg(const hs_op *A, hs_dtype dtype, const void *b, void *x, double tol, int maxit,
+                const hs_opts *opts, void *ws, size_t ws_bytes, void *stream, hs_result *res,
+                double *hist);
+
+/* BiCGStab with the shadow residual r' = r0/||r0|| and the restart rule of
+ * Algorithm 2 (restart when sqrt|alpha_n| < restart_eps: p = r, r' = r/||r||),
+ * classical statement order (convergence tested after each residual update). */
+hs_status hs_bicgstab(const hs_op *A, hs_dtype dtype, const void *b, void *x, double tol,
+                      int maxit, const hs_opts *opts, void *ws, size_t ws_bytes, void *stream,
+                      hs_result *res, double *hist);
+
+/* Thread-local message describing the last non-OK status (never NULL). */
+const char *hs_last_error(void);
+
+/* Library version string. */
+const char *hs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HSOLVE_H */

@@ -1,0 +1,10 @@
+"""GB300-native (sm_103a) structured-grid iterative solvers after arXiv 2305.05988.
+
+Public API: :class:`Operator` (Laplacian / upwind / diffusion stencils),
+:func:`jacobi`, :func:`gauss_seidel`, :func:`cg`, :func:`bicgstab`.  The
+numerical work runs in libhsolve (hand-written CUDA behind a C ABI,
+``include/hsolve.h``); this package only marshals arguments.
+"""
+from .solvers import Operator, SolveInfo, bicgstab, cg, gauss_seidel, jacobi, make_opts  # noqa: F401
+
+__all__ = ["Operator", "SolveInfo", "jacobi", "gauss_seidel", "cg", "bicgstab", "make_opts"]

@@ -1,0 +1,126 @@
+// hs_internal.h -- host-side internals shared by the libhsolve translation
+// units (operator descriptor, solve context, workspace carving, launchers).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/hsolve.h"
+#include "hs_common.cuh"
+#include "hs_stencil.cuh"
+
+struct hs_grid {
+  int ndim;
+  int64_t n[3];
+};
+
+struct hs_op {
+  int ndim;
+  int kind;           // 0 Laplacian, 1 upwind, 2 diffusion
+  int64_t n[3];       // unused dimensions = 1
+  double h[3];
+  double beta[3];
+  const void* k;      // diffusion: borrowed device pointer
+  int kdt;            // hs_dtype of k
+};
+
+namespace hs {
+
+enum { KIND_LAPLACIAN = 0, KIND_UPWIND = 1, KIND_DIFFUSION = 2 };
+
+void set_error(const char* fmt, ...);
+hs_status cuda_fail(cudaError_t e, const char* what);
+
+inline int opkind_of(const hs_op* A) {
+  if (A->kind == KIND_DIFFUSION) return OP_VARK;
+  if (A->kind == KIND_UPWIND) {
+    for (int d = 0; d < A->ndim; d++)
+      if (A->beta[d] != 0.0) return OP_NONSYM;
+  }
+  return OP_SYM;
+}
+
+inline Geom geom_of(const hs_op* A) {
+  Geom g;
+  g.nx = (int)A->n[0];
+  g.ny = (int)A->n[1];
+  g.nz = (int)A->n[2];
+  g.plane = (long long)g.nx * g.ny;
+  g.N = g.plane * g.nz;
+  return g;
+}
+
+// Unscaled constant row of an operator: diagonal and the six couplings
+// (lower/upper per dimension; missing dimensions give zeros).
+struct ConstRow {
+  double d, xl, xu, yl, yu, zl, zu;
+};
+ConstRow const_row(const hs_op* A);
+
+// Chooses a tiling (rows per tile, z chunk length) for `grid` persistent
+// blocks, or for a one-item-per-block launch when grid == 0.
+Tiling choose_tiling(const Geom& g, int by, int grid, bool src_expensive);
+
+// Workspace carving: every section is 256-byte aligned.
+struct Carve {
+  char* base;
+  size_t off;
+  size_t cap;
+  bool ok;
+  template <typename T>
+  T* take(size_t count) {
+    size_t bytes = (count * sizeof(T) + 255) & ~(size_t)255;
+    if (off + bytes > cap) ok = false;
+    T* p = base ? (T*)(base + off) : nullptr;
+    off += bytes;
+    return p;
+  }
+};
+
+constexpr int MAX_BLOCKS = 4096;   // cap on persistent grid size
+constexpr int MAX_SCAL = 4;        // scalars per grid reduction
+
+struct Common {
+  Ctrl* ctrl;
+  double* partials;
+  double* hist;      // device, maxit + 2 entries
+};
+
+size_t common_bytes(int maxit);
+Common carve_common(Carve& c, int maxit);
+
+struct SolveArgs {
+  const hs_op* A;
+  hs_dtype dtype;
+  const void* b;
+  void* x;
+  double tol;
+  int maxit;
+  hs_opts o;
+  char* ws;
+  size_t ws_bytes;
+  cudaStream_t stream;
+};
+
+// Per-solver workspace size (bytes), excluding nothing: callers add nothing.
+size_t ws_bytes_for(const hs_op* A, hs_solver s, hs_dtype dt, int maxit);
+
+// Solver launchers (hs_kernels.cu / hs_gs.cu).  They fill `res` (iters,
+// status, rel_res, restarts) and copy the history if hist != nullptr.
+hs_status run_jacobi(const SolveArgs& a, hs_result* res, double* hist);
+hs_status run_cg(const SolveArgs& a, hs_result* res, double* hist);
+hs_status run_bicgstab(const SolveArgs& a, hs_result* res, double* hist);
+hs_status run_gauss_seidel(const SolveArgs& a, hs_result* res, double* hist);
+hs_status run_spmv(const hs_op* A, hs_dtype dt, const void* x, void* y, cudaStream_t st);
+hs_status run_residual_plain(const hs_op* A, hs_dtype dt, const void* b, const void* x, void* r, cudaStream_t st);
+size_t vark_coef_bytes(const hs_op* A, hs_dtype dt);
+// Fills D (diagonal, or its inverse when invert_diag), ax, ay, az in dtype dt
+// from the operator's k.
+hs_status setup_vark(const hs_op* A, hs_dtype dt, void* D, void* ax, void* ay, void* az, bool invert_diag,
+                     cudaStream_t st);
+
+int sm_count();
+
+}  // namespace hs

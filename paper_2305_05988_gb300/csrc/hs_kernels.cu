@@ -1,0 +1,1167 @@
+// hs_kernels.cu -- stencil SpMV, residual, Jacobi, CG and BiCGStab kernels.
+//
+// The solver kernels are persistent cooperative kernels: one launch runs the
+// whole iteration, with grid-wide reduce-barriers (hs_common.cuh) in place of
+// the paper's MPI_Allreduce (section 3.3) and every vector update fused into
+// the stencil pass that produces or consumes it.
+#include <math.h>
+#include <stdio.h>
+
+#include <algorithm>
+
+#include "hs_internal.h"
+
+namespace hs {
+
+// Global index / stride helpers for grid-stride element loops.
+__device__ __forceinline__ long long gtid() { return (long long)blockIdx.x * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ long long gstride() { return (long long)gridDim.x * blockDim.x; }
+
+template <typename T>
+__device__ __forceinline__ T ldcg(const T* p) {
+  return __ldcg(p);
+}
+
+__device__ __forceinline__ bool finite_d(double v) { return isfinite(v); }
+
+// Writes the final solver outcome (block 0, thread 0 only).
+__device__ __forceinline__ void finish(Ctrl* c, int status, int iters, double rel) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    c->iters = iters;
+    c->rel_res = rel;
+    atomicCAS(&c->status, 0, status);
+  }
+}
+
+// ===========================================================================
+// SpMV and residual (one work item per block)
+// ===========================================================================
+
+template <typename T, int OPK, int NDIM>
+__global__ void __launch_bounds__(512) k_spmv(Geom g, Tiling tl, Coef<T> cf, T sigma, const T* __restrict__ x,
+                                              T* __restrict__ y) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sm = reinterpret_cast<T*>(smraw);
+  auto src = [&](long long idx, bool) -> T { return __ldg(x + idx); };
+  auto sink = [&](long long idx, const Nbr<T>& nb, int i, int j, int k) {
+    T v = apply_op<T, OPK, NDIM>(cf, g, idx, i, j, k, nb);
+    if (OPK != OP_VARK) v *= sigma;
+    y[idx] = v;
+  };
+  for (int item = blockIdx.x; item < tl.items(); item += gridDim.x) zmarch_item<T, NDIM>(g, tl, item, sm, src, sink);
+}
+
+template <typename T, int OPK, int NDIM>
+__global__ void __launch_bounds__(512) k_residual(Geom g, Tiling tl, Coef<T> cf, T sigma, const T* __restrict__ b,
+                                                  const T* __restrict__ x, T* __restrict__ r, double* partials) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ double sh[32 * 2];
+  T* sm = reinterpret_cast<T*>(smraw);
+  double acc[2] = {0.0, 0.0};
+  auto src = [&](long long idx, bool) -> T { return __ldg(x + idx); };
+  auto sink = [&](long long idx, const Nbr<T>& nb, int i, int j, int k) {
+    T v = apply_op<T, OPK, NDIM>(cf, g, idx, i, j, k, nb);
+    T bv = __ldg(b + idx);
+    T rv = (OPK == OP_VARK) ? bv - v : fma(-sigma, v, bv);
+    r[idx] = rv;
+    acc[0] += (double)rv * (double)rv;
+    acc[1] += (double)bv * (double)bv;
+  };
+  for (int item = blockIdx.x; item < tl.items(); item += gridDim.x) zmarch_item<T, NDIM>(g, tl, item, sm, src, sink);
+  block_sum<2>(acc, sh);
+  if (partials && threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = acc[0];
+    partials[2 * blockIdx.x + 1] = acc[1];
+  }
+}
+
+// Sums nb x ns partials in block order (one block).
+__global__ void k_finalize(const double* partials, int nb, int ns, double* out) {
+  __shared__ double sh[32 * 2];
+  double acc[2] = {0.0, 0.0};
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    acc[0] += partials[(size_t)b * ns];
+    if (ns > 1) acc[1] += partials[(size_t)b * ns + 1];
+  }
+  block_sum<2>(acc, sh);
+  if (threadIdx.x == 0) {
+    out[0] = acc[0];
+    if (ns > 1) out[1] = acc[1];
+  }
+}
+
+// ===========================================================================
+// Variable-coefficient setup: harmonic-mean face couplings from k.
+// D = sum_f kappa_f / h_d^2 (or its inverse), a{x,y,z}_i = kappa of the lower
+// face / h_d^2 (a boundary face uses kappa = k_i).
+// ===========================================================================
+
+__device__ __forceinline__ double harm(double a, double b) { return 2.0 * a * b / (a + b); }
+
+template <typename T, typename K>
+__global__ void k_vark_setup(Geom g, int ndim, const K* __restrict__ kk, double ihx, double ihy, double ihz,
+                             T* D, T* ax, T* ay, T* az, int invert) {
+  for (long long idx = gtid(); idx < g.N; idx += gstride()) {
+    int i = (int)(idx % g.nx);
+    int j = (int)((idx / g.nx) % g.ny);
+    int k = (int)(idx / g.plane);
+    double kc = (double)kk[idx];
+    double d = 0.0;
+    double lo, up;
+    lo = (i > 0) ? harm(kc, (double)kk[idx - 1]) : kc;
+    up = (i + 1 < g.nx) ? harm(kc, (double)kk[idx + 1]) : kc;
+    d += lo * ihx;
+    d += up * ihx;
+    ax[idx] = (T)(lo * ihx);
+    if (ndim >= 2) {
+      lo = (j > 0) ? harm(kc, (double)kk[idx - g.nx]) : kc;
+      up = (j + 1 < g.ny) ? harm(kc, (double)kk[idx + g.nx]) : kc;
+      d += lo * ihy;
+      d += up * ihy;
+      ay[idx] = (T)(lo * ihy);
+    } else {
+      ay[idx] = T(0);
+    }
+    if (ndim >= 3) {
+      lo = (k > 0) ? harm(kc, (double)kk[idx - g.plane]) : kc;
+      up = (k + 1 < g.nz) ? harm(kc, (double)kk[idx + g.plane]) : kc;
+      d += lo * ihz;
+      d += up * ihz;
+      az[idx] = (T)(lo * ihz);
+    } else if (az) {
+      az[idx] = T(0);
+    }
+    D[idx] = invert ? (T)(1.0 / d) : (T)d;
+  }
+}
+
+// ===========================================================================
+// Jacobi (section 3.1), out of place, persistent.
+// ===========================================================================
+
+template <typename T>
+struct JacArgs {
+  Geom g;
+  Tiling tl;
+  Coef<T> cf;      // constant: g = -a/a_ii couplings; variable: D = 1/a_ii
+  T invd;          // constant: 1/a_ii
+  double dscale2;  // constant: a_ii^2 (residual = a_ii (x' - x))
+  const T* b;
+  T* bD;           // workspace b/a_ii (constant coefficients)
+  T* x0;           // caller's x
+  T* x1;           // workspace ping-pong buffer
+  Common cm;
+  int maxit;
+  double tol;
+  int fuse;        // 1: fuse the residual of each iterate into the next sweep
+};
+
+template <typename T, int OPK, int NDIM>
+__global__ void __launch_bounds__(512) k_jacobi(JacArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ double sh[32 * MAX_SCAL];
+  T* sm = reinterpret_cast<T*>(smraw);
+  const long long N = a.g.N;
+
+  double acc[1] = {0.0};
+  for (long long i = gtid(); i < N; i += gstride()) {
+    T bv = a.b[i];
+    if (OPK != OP_VARK) a.bD[i] = bv * a.invd;
+    acc[0] += (double)bv * (double)bv;
+  }
+  block_sum<1>(acc, sh);
+  double bb[1];
+  if (!grid_reduce<1>(a.cm.ctrl, a.cm.partials, acc, bb, sh)) return;
+  if (bb[0] == 0.0) {
+    for (long long i = gtid(); i < N; i += gstride()) a.x0[i] = T(0);
+    finish(a.cm.ctrl, DS_CONVERGED, 0, 0.0);
+    return;
+  }
+  const T* bsrc = (OPK == OP_VARK) ? a.b : a.bD;
+  T* xs = a.x0;
+  T* xd = a.x1;
+  int iters = 0, status = DS_CONVERGED;
+  double rel = -1.0;
+  for (int k = 0;; k++) {
+    if (!a.fuse && k == a.maxit) {
+      iters = k;
+      break;
+    }
+    double racc[1] = {0.0};
+    auto src = [&](long long idx, bool) -> T { return ldcg(xs + idx); };
+    auto sink = [&](long long idx, const Nbr<T>& nb, int i, int j, int kk) {
+      T xn = jacobi_update<T, OPK, NDIM>(a.cf, a.g, idx, i, j, kk, nb, ldcg(bsrc + idx));
+      xd[idx] = xn;
+      if (a.fuse) {
+        T d = xn - nb.c;
+        if (OPK == OP_VARK) d = d / __ldg(a.cf.D + idx);
+        racc[0] += (double)d * (double)d;
+      }
+    };
+    for (int item = blockIdx.x; item < a.tl.items(); item += gridDim.x)
+      zmarch_item<T, NDIM>(a.g, a.tl, item, sm, src, sink);
+    if (a.fuse) {
+      block_sum<1>(racc, sh);
+      double rr[1];
+      if (!grid_reduce<1>(a.cm.ctrl, a.cm.partials, racc, rr, sh)) return;
+      double sc = (OPK == OP_VARK) ? 1.0 : a.dscale2;
+      rel = sqrt(rr[0] * sc / bb[0]);
+      if (blockIdx.x == 0 && threadIdx.x == 0) a.cm.hist[k] = rel;
+      if (!finite_d(rel)) {
+        iters = k;
+        status = DS_NONFINITE;
+        break;
+      }
+      if (rel <= a.tol || k == a.maxit) {
+        iters = k;
+        status = (rel <= a.tol) ? DS_CONVERGED : DS_MAXIT;
+        break;
+      }
+    } else {
+      if (!grid_sync(a.cm.ctrl, a.cm.partials, sh)) return;
+    }
+    T* t = xs;
+    xs = xd;
+    xd = t;
+  }
+  if (xs != a.x0) {
+    for (long long i = gtid(); i < N; i += gstride()) a.x0[i] = ldcg(xs + i);
+  }
+  finish(a.cm.ctrl, status, iters, rel);
+}
+
+// ===========================================================================
+// CG: classical Hestenes-Stiefel (section 3.2) in two fused passes.
+//   pass 1 (stencil):  p = r + beta p_old (on the fly, halo included),
+//                      w = A p / sigma, partial p.w
+//   pass 2 (elements): x += alpha p, r -= alpha A p, partial r.r
+// p is double-buffered so that halo reads of p_old never race with stores.
+// ===========================================================================
+
+template <typename T>
+struct CgArgs {
+  Geom g;
+  Tiling tl;
+  Coef<T> cf;
+  double sigma;   // A = sigma * (scaled operator)
+  const T* b;
+  T* x;
+  T* r;
+  T* p0;
+  T* p1;
+  T* w;
+  Common cm;
+  int maxit;
+  double tol;
+};
+
+template <typename T, int OPK, int NDIM>
+__global__ void __launch_bounds__(512) k_cg(CgArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ double sh[32 * MAX_SCAL];
+  T* sm = reinterpret_cast<T*>(smraw);
+  const long long N = a.g.N;
+  const T sig = (T)a.sigma;
+
+  // r = b - A x ; ||r||^2, ||b||^2
+  double acc2[2] = {0.0, 0.0};
+  {
+    auto src = [&](long long idx, bool) -> T { return ldcg(a.x + idx); };
+    auto sink = [&](long long idx, const Nbr<T>& nb, int i, int j, int k) {
+      T v = apply_op<T, OPK, NDIM>(a.cf, a.g, idx, i, j, k, nb);
+      T bv = __ldg(a.b + idx);
+      T rv = (OPK == OP_VARK) ? bv - v : fma(-sig, v, bv);
+      a.r[idx] = rv;
+      acc2[0] += (double)rv * (double)rv;
+      acc2[1] += (double)bv * (double)bv;
+    };
+    for (int item = blockIdx.x; item < a.tl.items(); item += gridDim.x)
+      zmarch_item<T, NDIM>(a.g, a.tl, item, sm, src, sink);
+  }
+  block_sum<2>(acc2, sh);
+  double s2[2];
+  if (!grid_reduce<2>(a.cm.ctrl, a.cm.partials, acc2, s2, sh)) return;
+  double rr = s2[0];
+  const double bb = s2[1];
+  if (bb == 0.0) {
+    for (long long i = gtid(); i < N; i += gstride()) a.x[i] = T(0);
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.cm.hist[0] = 0.0;
+    finish(a.cm.ctrl, DS_CONVERGED, 0, 0.0);
+    return;
+  }
+  double rel = sqrt(rr / bb);
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.cm.hist[0] = rel;
+  if (rel <= a.tol || a.maxit == 0) {
+    finish(a.cm.ctrl, rel <= a.tol ? DS_CONVERGED : DS_MAXIT, 0, rel);
+    return;
+  }
+
+  double beta = 0.0;
+  bool first = true;
+  int it = 0, status = DS_MAXIT;
+  while (it < a.maxit) {
+    it++;
+    const T* pold = (it & 1) ? a.p0 : a.p1;
+    T* pnew = (it & 1) ? a.p1 : a.p0;
+    const T tb = (T)beta;
+    // ---- pass 1: p = r + beta p_old ; w = A p / sigma ; p.w
+    double acc[1] = {0.0};
+    {
+      auto src = [&](long long idx, bool own) -> T {
+        T rv = ldcg(a.r + idx);
+        T pv = first ? rv : fma(tb, ldcg(pold + idx), rv);
+        if (own) pnew[idx] = pv;
+        return pv;
+      };
+      auto sink = [&](long long idx, const Nbr<T>& nb, int i, int j, int k) {
+        T wv = apply_op<T, OPK, NDIM>(a.cf, a.g, idx, i, j, k, nb);
+        a.w[idx] = wv;
+        acc[0] += (double)nb.c * (double)wv;
+      };
+      for (int item = blockIdx.x; item < a.tl.items(); item += gridDim.x)
+        zmarch_item<T, NDIM>(a.g, a.tl, item, sm, src, sink);
+    }
+    block_sum<1>(acc, sh);
+    double pw[1];
+    if (!grid_reduce<1>(a.cm.ctrl, a.cm.partials, acc, pw, sh)) return;
+    if (!(pw[0] > 0.0) || !finite_d(pw[0])) {
+      status = finite_d(pw[0]) ? DS_BREAKDOWN : DS_NONFINITE;
+      break;
+    }
+    const double ar = rr / pw[0];           // multiplies w = A p / sigma
+    const double axs = ar / a.sigma;        // multiplies p
+    const T tar = (T)ar, tax = (T)axs;
+    // ---- pass 2: x += alpha p ; r -= alpha A p ; r.r
+    double acc1[1] = {0.0};
+    for (long long i = gtid(); i < N; i += gstride()) {
+      T pv = ldcg(pnew + i);
+      T wv = ldcg(a.w + i);
+      T xv = fma(tax, pv, ldcg(a.x + i));
+      T rv = fma(-tar, wv, ldcg(a.r + i));
+      a.x[i] = xv;
+      a.r[i] = rv;
+      acc1[0] += (double)rv * (double)rv;
+    }
+    block_sum<1>(acc1, sh);
+    double rn[1];
+    if (!grid_reduce<1>(a.cm.ctrl, a.cm.partials, acc1, rn, sh)) return;
+    rel = sqrt(rn[0] / bb);
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.cm.hist[it] = rel;
+    if (!finite_d(rel)) {
+      status = DS_NONFINITE;
+      break;
+    }
+    if (rel <= a.tol) {
+      status = DS_CONVERGED;
+      break;
+    }
+    beta = rn[0] / rr;
+    rr = rn[0];
+    first = false;
+  }
+  finish(a.cm.ctrl, status, it, rel);
+}
+
+// ===========================================================================
+// BiCGStab with Algorithm 2's normalised shadow residual and restart rule,
+// three fused passes per iteration:
+//   pass 1 (stencil):  p = r + beta (p_old - omega v_old) (or p = r after a
+//                      start/restart, which also stores r' = r/||r||),
+//                      v = A p / sigma, partial v.r'
+//   pass 2 (stencil):  s = r - alpha A p (on the fly), t = A s / sigma,
+//                      partials s.s, t.s, t.t
+//   pass 3 (elements): x += alpha p + omega s, r = s - omega A s,
+//                      partials r.r', r.r
+// ===========================================================================
+
+template <typename T>
+struct BiArgs {
+  Geom g;
+  Tiling tl;
+  Coef<T> cf;
+  double sigma;
+  const T* b;
+  T* x;
+  T* r;
+  T* rs;
+  T* p0;
+  T* p1;
+  T* v0;
+  T* v1;
+  T* s;
+  T* t;
+  Common cm;
+  int maxit;
+  double tol;
+  double reps;
+};
+
+template <typename T, int OPK, int NDIM>
+__global__ void __launch_bounds__(512) k_bicgstab(BiArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ double sh[32 * MAX_SCAL];
+  T* sm = reinterpret_cast<T*>(smraw);
+  const long long N = a.g.N;
+  const T sig = (T)a.sigma;
+
+  double acc2[2] = {0.0, 0.0};
+  {
+    auto src = [&](long long idx, bool) -> T { return ldcg(a.x + idx); };
+    auto sink = [&](long long idx, const Nbr<T>& nb, int i, int j, int k) {
+      T v = apply_op<T, OPK, NDIM>(a.cf, a.g, idx, i, j, k, nb);
+      T bv = __ldg(a.b + idx);
+      T rv = (OPK == OP_VARK) ? bv - v : fma(-sig, v, bv);
+      a.r[idx] = rv;
+      acc2[0] += (double)rv * (double)rv;
+      acc2[1] += (double)bv * (double)bv;
+    };
+    for (int item = blockIdx.x; item < a.tl.items(); item += gridDim.x)
+      zmarch_item<T, NDIM>(a.g, a.tl, item, sm, src, sink);
+  }
+  block_sum<2>(acc2, sh);
+  double s2[2];
+  if (!grid_reduce<2>(a.cm.ctrl, a.cm.partials, acc2, s2, sh)) return;
+  double brr = s2[0];
+  const double bb = s2[1];
+  if (bb == 0.0) {
+    for (long long i = gtid(); i < N; i += gstride()) a.x[i] = T(0);
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.cm.hist[0] = 0.0;
+    finish(a.cm.ctrl, DS_CONVERGED, 0, 0.0);
+    return;
+  }
+  double rel = sqrt(brr / bb);
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.cm.hist[0] = rel;
+  if (rel <= a.tol || a.maxit == 0) {
+    finish(a.cm.ctrl, rel <= a.tol ? DS_CONVERGED : DS_MAXIT, 0, rel);
+    return;
+  }
+
+  double alpha_n = sqrt(brr);   // r . r' with r' = r / ||r||
+  double inv_rn = 1.0 / sqrt(brr);
+  bool restart = true;          // p = r and r' = r/||r|| in the next pass 1
+  double beta = 0.0, omega = 0.0;
+  int it = 0, status = DS_MAXIT, restarts = 0;
+  while (it < a.maxit) {
+    it++;
+    const T* pold = (it & 1) ? a.p0 : a.p1;
+    T* pnew = (it & 1) ? a.p1 : a.p0;
+    const T* vold = (it & 1) ? a.v0 : a.v1;
+    T* vnew = (it & 1) ? a.v1 : a.v0;
+    // ---- pass 1
+    const T tb = (T)beta, tws = (T)(omega * a.sigma), tinv = (T)inv_rn;
+    double acc1[1] = {0.0};
+    {
+      auto src = [&](long long idx, bool own) -> T {
+        T rv = ldcg(a.r + idx);
+        T pv = restart ? rv : fma(tb, fma(-tws, ldcg(vold + idx), ldcg(pold + idx)), rv);
+        if (own) pnew[idx] = pv;
+        return pv;
+      };
+      auto sink = [&](long long idx, const Nbr<T>& nb, int i, int j, int k) {
+        T vv = apply_op<T, OPK, NDIM>(a.cf, a.g, idx, i, j, k, nb);
+        vnew[idx] = vv;
+        T rsv;
+        if (restart) {
+          rsv = ldcg(a.r + idx) * tinv;
+          a.rs[idx] = rsv;
+        } else {
+          rsv = ldcg(a.rs + idx);
+        }
+        acc1[0] += (double)vv * (double)rsv;
+      };
+      for (int item = blockIdx.x; item < a.tl.items(); item += gridDim.x)
+        zmarch_item<T, NDIM>(a.g, a.tl, item, sm, src, sink);
+    }
+    block_sum<1>(acc1, sh);
+    double ad[1];
+    if (!grid_reduce<1>(a.cm.ctrl, a.cm.partials, acc1, ad, sh)) return;
+    const double alpha_d = a.sigma * ad[0];
+    if (alpha_d == 0.0 || !finite_d(alpha_d)) {
+      status = finite_d(alpha_d) ? DS_BREAKDOWN : DS_NONFINITE;
+      break;
+    }
+    const double alpha = alpha_n / alpha_d;
+    // ---- pass 2
+    const T tas = (T)(alpha * a.sigma);
+    double acc3[3] = {0.0, 0.0, 0.0};
+    {
+      auto src = [&](long long idx, bool own) -> T {
+        T sv = fma(-tas, ldcg(vnew + idx), ldcg(a.r + idx));
+        if (own) a.s[idx] = sv;
+        return sv;
+      };
+      auto sink = [&](long long idx, const Nbr<T>& nb, int i, int j, int k) {
+        T tv = apply_op<T, OPK, NDIM>(a.cf, a.g, idx, i, j, k, nb);
+        a.t[idx] = tv;
+        const double sv = (double)nb.c, td = (double)tv;
+        acc3[0] += sv * sv;
+        acc3[1] += td * sv;
+        acc3[2] += td * td;
+      };
+      for (int item = blockIdx.x; item < a.tl.items(); item += gridDim.x)
+        zmarch_item<T, NDIM>(a.g, a.tl, item, sm, src, sink);
+    }
+    block_sum<3>(acc3, sh);
+    double st[3];
+    if (!grid_reduce<3>(a.cm.ctrl, a.cm.partials, acc3, st, sh)) return;
+    const double srel = sqrt(st[0] / bb);
+    if (srel <= a.tol) {
+      const T ta = (T)alpha;
+      for (long long i = gtid(); i < N; i += gstride()) a.x[i] = fma(ta, ldcg(pnew + i), ldcg(a.x + i));
+      if (blockIdx.x == 0 && threadIdx.x == 0) a.cm.hist[it] = srel;
+      rel = srel;
+      status = DS_CONVERGED;
+      break;
+    }
+    const double ts = a.sigma * st[1], tt = a.sigma * a.sigma * st[2];
+    if (tt == 0.0 || !finite_d(tt) || !finite_d(ts)) {
+      status = finite_d(tt) && finite_d(ts) ? DS_BREAKDOWN : DS_NONFINITE;
+      break;
+    }
+    omega = ts / tt;
+    if (omega == 0.0) {
+      status = DS_BREAKDOWN;
+      break;
+    }
+    // ---- pass 3
+    const T ta = (T)alpha, tom = (T)omega, toms = (T)(omega * a.sigma);
+    double acc4[2] = {0.0, 0.0};
+    for (long long i = gtid(); i < N; i += gstride()) {
+      T sv = ldcg(a.s + i);
+      T xv = fma(tom, sv, fma(ta, ldcg(pnew + i), ldcg(a.x + i)));
+      T rv = fma(-toms, ldcg(a.t + i), sv);
+      a.x[i] = xv;
+      a.r[i] = rv;
+      acc4[0] += (double)rv * (double)ldcg(a.rs + i);
+      acc4[1] += (double)rv * (double)rv;
+    }
+    block_sum<2>(acc4, sh);
+    double rn[2];
+    if (!grid_reduce<2>(a.cm.ctrl, a.cm.partials, acc4, rn, sh)) return;
+    rel = sqrt(rn[1] / bb);
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.cm.hist[it] = rel;
+    if (!finite_d(rel) || !finite_d(rn[0])) {
+      status = DS_NONFINITE;
+      break;
+    }
+    if (rel <= a.tol) {
+      status = DS_CONVERGED;
+      break;
+    }
+    if (a.reps > 0.0 && sqrt(fabs(rn[0])) < a.reps) {
+      restart = true;
+      alpha_n = sqrt(rn[1]);
+      inv_rn = 1.0 / sqrt(rn[1]);
+      restarts++;
+    } else {
+      restart = false;
+      beta = rn[0] / (alpha_d * omega);
+      alpha_n = rn[0];
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.cm.ctrl->restarts = restarts;
+  finish(a.cm.ctrl, status, it, rel);
+}
+
+// ===========================================================================
+// Host side: coefficients, launch shapes, dispatch.
+// ===========================================================================
+
+__global__ void k_init_ctrl(Ctrl* c, unsigned long long timeout_ns) {
+  if (threadIdx.x == 0) {
+    c->count = 0;
+    c->gen = 0;
+    c->status = 0;
+    c->iters = 0;
+    c->restarts = 0;
+    c->timeout_ns = timeout_ns;
+    c->rel_res = -1.0;
+  }
+}
+
+static int g_sm_count = -1;
+int sm_count() {
+  if (g_sm_count < 0) {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    g_sm_count = n > 0 ? n : 1;
+  }
+  return g_sm_count;
+}
+
+Tiling choose_tiling(const Geom& g, int by, int grid, bool src_expensive) {
+  Tiling t;
+  t.by = by;
+  t.tiles_x = (g.nx + BX - 1) / BX;
+  t.tiles_y = (g.ny + by - 1) / by;
+  const int txy = t.tiles_x * t.tiles_y;
+  if (g.nz == 1) {
+    t.chunks = 1;
+    t.lz = 1;
+    return t;
+  }
+  if (grid <= 0) {
+    t.lz = std::min(g.nz, 32);
+    t.chunks = (g.nz + t.lz - 1) / t.lz;
+    return t;
+  }
+  const double over = src_expensive ? 2.0 : 1.0;
+  double best = 1e300;
+  int best_lz = g.nz;
+  for (int lz = 4; lz <= g.nz; lz++) {
+    int chunks = (g.nz + lz - 1) / lz;
+    if (lz > 4 && (g.nz + lz - 2) / (lz - 1) == chunks) continue;  // same chunk count, smaller lz better
+    long long items = (long long)txy * chunks;
+    long long waves = (items + grid - 1) / grid;
+    double cost = (double)waves * (lz + over);
+    if (cost < best - 1e-9) {
+      best = cost;
+      best_lz = lz;
+    }
+  }
+  if (g.nz < 4) best_lz = g.nz;
+  t.lz = best_lz;
+  t.chunks = (g.nz + t.lz - 1) / t.lz;
+  return t;
+}
+
+ConstRow const_row(const hs_op* A) {
+  ConstRow c = {0, 0, 0, 0, 0, 0, 0};
+  double* lo[3] = {&c.xl, &c.yl, &c.zl};
+  double* up[3] = {&c.xu, &c.yu, &c.zu};
+  for (int d = 0; d < A->ndim; d++) {
+    double ih2 = 1.0 / (A->h[d] * A->h[d]);
+    double bh = (A->kind == KIND_UPWIND) ? A->beta[d] / A->h[d] : 0.0;
+    *lo[d] = -ih2 - bh;
+    *up[d] = -ih2;
+    c.d += 2.0 * ih2 + bh;
+  }
+  return c;
+}
+
+// Scaled coefficients: divide by sigma = -xu so that xu becomes exactly -1.
+template <typename T>
+static Coef<T> scaled_coef(const hs_op* A, double* sigma) {
+  Coef<T> cf = {};
+  ConstRow c = const_row(A);
+  double s = -c.xu;
+  *sigma = s;
+  cf.d = (T)(c.d / s);
+  cf.xl = (T)(c.xl / s);
+  cf.xu = (T)(-1.0);
+  cf.yl = (T)(c.yl / s);
+  cf.yu = (T)(c.yu / s);
+  cf.zl = (T)(c.zl / s);
+  cf.zu = (T)(c.zu / s);
+  return cf;
+}
+
+// Jacobi coefficients g = -a/a_ii.
+template <typename T>
+static Coef<T> jacobi_coef(const hs_op* A, T* invd, double* d2) {
+  Coef<T> cf = {};
+  ConstRow c = const_row(A);
+  cf.d = (T)0;
+  cf.xl = (T)(-c.xl / c.d);
+  cf.xu = (T)(-c.xu / c.d);
+  cf.yl = (T)(-c.yl / c.d);
+  cf.yu = (T)(-c.yu / c.d);
+  cf.zl = (T)(-c.zl / c.d);
+  cf.zu = (T)(-c.zu / c.d);
+  *invd = (T)(1.0 / c.d);
+  *d2 = c.d * c.d;
+  return cf;
+}
+
+size_t vark_coef_bytes(const hs_op* A, hs_dtype dt) {
+  if (A->kind != KIND_DIFFUSION) return 0;
+  size_t N = (size_t)(A->n[0] * A->n[1] * A->n[2]);
+  size_t es = dt == HS_F64 ? 8 : 4;
+  return 4 * ((N * es + 255) & ~(size_t)255);
+}
+
+hs_status setup_vark(const hs_op* A, hs_dtype dt, void* D, void* ax, void* ay, void* az, bool invert_diag,
+                     cudaStream_t st) {
+  Geom g = geom_of(A);
+  double ih[3];
+  for (int d = 0; d < 3; d++) ih[d] = d < A->ndim ? 1.0 / (A->h[d] * A->h[d]) : 0.0;
+  int blocks = (int)std::min<long long>((g.N + 255) / 256, (long long)sm_count() * 16);
+  if (blocks < 1) blocks = 1;
+  if (dt == HS_F64) {
+    if (A->kdt == HS_F64)
+      k_vark_setup<double, double><<<blocks, 256, 0, st>>>(g, A->ndim, (const double*)A->k, ih[0], ih[1], ih[2],
+                                                           (double*)D, (double*)ax, (double*)ay, (double*)az,
+                                                           invert_diag);
+    else
+      k_vark_setup<double, float><<<blocks, 256, 0, st>>>(g, A->ndim, (const float*)A->k, ih[0], ih[1], ih[2],
+                                                          (double*)D, (double*)ax, (double*)ay, (double*)az,
+                                                          invert_diag);
+  } else {
+    if (A->kdt == HS_F64)
+      k_vark_setup<float, double><<<blocks, 256, 0, st>>>(g, A->ndim, (const double*)A->k, ih[0], ih[1], ih[2],
+                                                          (float*)D, (float*)ax, (float*)ay, (float*)az,
+                                                          invert_diag);
+    else
+      k_vark_setup<float, float><<<blocks, 256, 0, st>>>(g, A->ndim, (const float*)A->k, ih[0], ih[1], ih[2],
+                                                         (float*)D, (float*)ax, (float*)ay, (float*)az,
+                                                         invert_diag);
+  }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? HS_OK : cuda_fail(e, "variable-coefficient setup launch");
+}
+
+static int rows_per_tile(const Geom& g) {
+  // 2-D grids are small: more, shorter tiles; 3-D: 8 rows (256 threads).
+  if (g.nz == 1) return g.ny >= 64 ? 8 : 4;
+  return 8;
+}
+
+template <typename T>
+static size_t slab_bytes(int by) {
+  return (size_t)2 * (by + 2) * (BX + 2) * sizeof(T);
+}
+
+// ---- dispatch over (element type, operator kind, dimensionality) ---------
+template <typename T_, int OPK_, int NDIM_>
+struct Tag {
+  using T = T_;
+  static constexpr int OPK = OPK_;
+  static constexpr int NDIM = NDIM_;
+};
+
+template <class F>
+static hs_status dispatch(hs_dtype dt, int opk, int ndim, F&& f) {
+  const int nd = ndim >= 3 ? 3 : 2;
+#define HS_CASE(TT, OK, ND) \
+  if (opk == OK && nd == ND) return f(Tag<TT, OK, ND>{});
+  if (dt == HS_F64) {
+    HS_CASE(double, OP_SYM, 2)
+    HS_CASE(double, OP_SYM, 3)
+    HS_CASE(double, OP_NONSYM, 2)
+    HS_CASE(double, OP_NONSYM, 3)
+    HS_CASE(double, OP_VARK, 2)
+    HS_CASE(double, OP_VARK, 3)
+  } else {
+    HS_CASE(float, OP_SYM, 2)
+    HS_CASE(float, OP_SYM, 3)
+    HS_CASE(float, OP_NONSYM, 2)
+    HS_CASE(float, OP_NONSYM, 3)
+    HS_CASE(float, OP_VARK, 2)
+    HS_CASE(float, OP_VARK, 3)
+  }
+#undef HS_CASE
+  set_error("unsupported operator / dtype combination");
+  return HS_ERR_INVALID;
+}
+
+// Operator coefficients for stencil kernels (scaled form, or var-k arrays).
+template <typename T>
+static Coef<T> op_coef(const hs_op* A, const void* D, const void* ax, const void* ay, const void* az,
+                       double* sigma) {
+  if (A->kind == KIND_DIFFUSION) {
+    Coef<T> cf = {};
+    cf.D = (const T*)D;
+    cf.ax = (const T*)ax;
+    cf.ay = (const T*)ay;
+    cf.az = (const T*)az;
+    *sigma = 1.0;
+    return cf;
+  }
+  return scaled_coef<T>(A, sigma);
+}
+
+// Variable-coefficient SpMV without a workspace: face couplings are formed
+// on the fly from k (harmonic means), y_i = sum_f kappa_f (x_i - x_j) / h^2.
+template <typename T, typename K, int NDIM>
+__global__ void __launch_bounds__(512) k_spmv_vark_direct(Geom g, Tiling tl, const K* __restrict__ kk, double ihx,
+                                                          double ihy, double ihz, const T* __restrict__ x,
+                                                          T* __restrict__ y) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sm = reinterpret_cast<T*>(smraw);
+  auto src = [&](long long idx, bool) -> T { return __ldg(x + idx); };
+  auto sink = [&](long long idx, const Nbr<T>& nb, int i, int j, int k) {
+    const double kc = (double)__ldg(kk + idx), xc = (double)nb.c;
+    double acc = 0.0;
+    double kap;
+    kap = (i > 0) ? harm(kc, (double)__ldg(kk + idx - 1)) : kc;
+    acc += kap * ihx * (xc - (double)nb.w);
+    kap = (i + 1 < g.nx) ? harm(kc, (double)__ldg(kk + idx + 1)) : kc;
+    acc += kap * ihx * (xc - (double)nb.e);
+    if (ihy != 0.0) {
+      kap = (j > 0) ? harm(kc, (double)__ldg(kk + idx - g.nx)) : kc;
+      acc += kap * ihy * (xc - (double)nb.s);
+      kap = (j + 1 < g.ny) ? harm(kc, (double)__ldg(kk + idx + g.nx)) : kc;
+      acc += kap * ihy * (xc - (double)nb.n);
+    }
+    if (NDIM == 3) {
+      kap = (k > 0) ? harm(kc, (double)__ldg(kk + idx - g.plane)) : kc;
+      acc += kap * ihz * (xc - (double)nb.b);
+      kap = (k + 1 < g.nz) ? harm(kc, (double)__ldg(kk + idx + g.plane)) : kc;
+      acc += kap * ihz * (xc - (double)nb.t);
+    }
+    y[idx] = (T)acc;
+  };
+  for (int item = blockIdx.x; item < tl.items(); item += gridDim.x) zmarch_item<T, NDIM>(g, tl, item, sm, src, sink);
+}
+
+// r = b - y (elementwise), used by the residual of diffusion operators.
+template <typename T>
+__global__ void k_sub_from(const T* __restrict__ b, T* __restrict__ r, long long N) {
+  for (long long i = gtid(); i < N; i += gstride()) r[i] = b[i] - r[i];
+}
+
+template <typename T, int NDIM>
+static hs_status spmv_vark_direct(const hs_op* A, const void* x, void* y, cudaStream_t st) {
+  Geom g = geom_of(A);
+  int by = rows_per_tile(g);
+  Tiling tl = choose_tiling(g, by, 0, false);
+  double ih[3];
+  for (int d = 0; d < 3; d++) ih[d] = d < A->ndim ? 1.0 / (A->h[d] * A->h[d]) : 0.0;
+  if (A->kdt == HS_F64)
+    k_spmv_vark_direct<T, double, NDIM><<<tl.items(), 32 * by, slab_bytes<T>(by), st>>>(
+        g, tl, (const double*)A->k, ih[0], ih[1], ih[2], (const T*)x, (T*)y);
+  else
+    k_spmv_vark_direct<T, float, NDIM><<<tl.items(), 32 * by, slab_bytes<T>(by), st>>>(
+        g, tl, (const float*)A->k, ih[0], ih[1], ih[2], (const T*)x, (T*)y);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? HS_OK : cuda_fail(e, "spmv launch");
+}
+
+hs_status run_spmv(const hs_op* A, hs_dtype dt, const void* x, void* y, cudaStream_t st) {
+  Geom g = geom_of(A);
+  return dispatch(dt, opkind_of(A), A->ndim, [&](auto tag) -> hs_status {
+    using Tg = decltype(tag);
+    using T = typename Tg::T;
+    constexpr int OPK = Tg::OPK, NDIM = Tg::NDIM;
+    if (OPK == OP_VARK) return spmv_vark_direct<T, NDIM>(A, x, y, st);
+    double sigma;
+    Coef<T> cf = op_coef<T>(A, nullptr, nullptr, nullptr, nullptr, &sigma);
+    int by = rows_per_tile(g);
+    Tiling tl = choose_tiling(g, by, 0, false);
+    k_spmv<T, OPK, NDIM><<<tl.items(), 32 * by, slab_bytes<T>(by), st>>>(g, tl, cf, (T)sigma, (const T*)x, (T*)y);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? HS_OK : cuda_fail(e, "spmv launch");
+  });
+}
+
+hs_status run_residual_plain(const hs_op* A, hs_dtype dt, const void* b, const void* x, void* r, cudaStream_t st) {
+  Geom g = geom_of(A);
+  if (A->kind == KIND_DIFFUSION) {
+    hs_status s = run_spmv(A, dt, x, r, st);
+    if (s != HS_OK) return s;
+    int blocks = (int)std::min<long long>((g.N + 255) / 256, (long long)sm_count() * 16);
+    if (blocks < 1) blocks = 1;
+    if (dt == HS_F64)
+      k_sub_from<double><<<blocks, 256, 0, st>>>((const double*)b, (double*)r, g.N);
+    else
+      k_sub_from<float><<<blocks, 256, 0, st>>>((const float*)b, (float*)r, g.N);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? HS_OK : cuda_fail(e, "residual launch");
+  }
+  return dispatch(dt, opkind_of(A), A->ndim, [&](auto tag) -> hs_status {
+    using Tg = decltype(tag);
+    using T = typename Tg::T;
+    constexpr int OPK = Tg::OPK, NDIM = Tg::NDIM;
+    if (OPK == OP_VARK) return HS_ERR_INVALID;
+    double sigma;
+    Coef<T> cf = op_coef<T>(A, nullptr, nullptr, nullptr, nullptr, &sigma);
+    int by = rows_per_tile(g);
+    Tiling tl = choose_tiling(g, by, 0, false);
+    k_residual<T, OPK, NDIM><<<tl.items(), 32 * by, slab_bytes<T>(by), st>>>(g, tl, cf, (T)sigma, (const T*)b,
+                                                                               (const T*)x, (T*)r, nullptr);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? HS_OK : cuda_fail(e, "residual launch");
+  });
+}
+
+// r = b - A x with the solver's coefficient arrays, plus ||r||^2, ||b||^2
+// reduced deterministically into norms_dev[0..1] (partials: >= grid*2 doubles).
+static hs_status residual_norms(const hs_op* A, hs_dtype dt, const void* D, const void* ax, const void* ay,
+                                const void* az, const void* b, const void* x, void* r, double* norms_dev,
+                                double* partials_dev, cudaStream_t st) {
+  Geom g = geom_of(A);
+  return dispatch(dt, opkind_of(A), A->ndim, [&](auto tag) -> hs_status {
+    using Tg = decltype(tag);
+    using T = typename Tg::T;
+    constexpr int OPK = Tg::OPK, NDIM = Tg::NDIM;
+    double sigma;
+    Coef<T> cf = op_coef<T>(A, D, ax, ay, az, &sigma);
+    int by = rows_per_tile(g);
+    Tiling tl = choose_tiling(g, by, 0, false);
+    int grid = std::min(tl.items(), MAX_BLOCKS * MAX_SCAL / 2);
+    k_residual<T, OPK, NDIM><<<grid, 32 * by, slab_bytes<T>(by), st>>>(g, tl, cf, (T)sigma, (const T*)b,
+                                                                        (const T*)x, (T*)r, partials_dev);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "residual launch");
+    k_finalize<<<1, 256, 0, st>>>(partials_dev, grid, 2, norms_dev);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? HS_OK : cuda_fail(e, "finalize launch");
+  });
+}
+
+// ---- persistent launch planning ------------------------------------------------
+template <typename K>
+static hs_status plan_persistent(K kernel, int block, size_t smem, const Geom& g, int by, bool src_expensive,
+                                 int* grid_out, Tiling* tl_out) {
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem);
+  if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+  if (per_sm < 1) {
+    set_error("persistent kernel cannot be resident (block %d, smem %zu)", block, smem);
+    return HS_ERR_CUDA;
+  }
+  int grid = std::min(per_sm * sm_count(), MAX_BLOCKS);
+  Tiling tl = choose_tiling(g, by, grid, src_expensive);
+  grid = std::max(1, std::min(grid, tl.items()));
+  *tl_out = choose_tiling(g, by, grid, src_expensive);
+  *grid_out = grid;
+  return HS_OK;
+}
+
+static hs_status launch_coop(const void* fn, int grid, int block, void** args, size_t smem, cudaStream_t st) {
+  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, smem, st);
+  if (e != cudaSuccess) return cuda_fail(e, "cooperative launch");
+  return HS_OK;
+}
+
+static hs_status init_ctrl(const Common& cm, const hs_opts& o, cudaStream_t st) {
+  double t = o.timeout_s > 0 ? o.timeout_s : 2.0;
+  k_init_ctrl<<<1, 32, 0, st>>>(cm.ctrl, (unsigned long long)(t * 1e9));
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? HS_OK : cuda_fail(e, "control init");
+}
+
+// Common solver tail: optional true residual of the returned x into
+// ctrl->aux[0..1], then read back the control block and history.
+struct Tail {
+  const hs_op* A;
+  hs_dtype dt;
+  const void *D, *ax, *ay, *az;   // coefficient arrays (diffusion) or null
+  const void* b;
+  const void* x;
+  void* rbuf;                     // scratch vector of N elements
+};
+
+static hs_status finish_solve(const SolveArgs& sa, const Common& cm, const Tail& t, hs_result* res, double* hist,
+                              bool want_hist) {
+  if (sa.o.true_residual) {
+    hs_status s = residual_norms(t.A, t.dt, t.D, t.ax, t.ay, t.az, t.b, t.x, t.rbuf, &cm.ctrl->aux[0], cm.partials,
+                                 sa.stream);
+    if (s != HS_OK) return s;
+  }
+  Ctrl h;
+  cudaError_t e = cudaMemcpyAsync(&h, cm.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, sa.stream);
+  if (e != cudaSuccess) return cuda_fail(e, "control read-back");
+  e = cudaStreamSynchronize(sa.stream);
+  if (e != cudaSuccess) return cuda_fail(e, "solver kernel");
+  if (hist && want_hist) {
+    int n = std::min(h.iters, sa.maxit) + 1;
+    if (n > 0) {
+      e = cudaMemcpy(hist, cm.hist, sizeof(double) * n, cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return cuda_fail(e, "history read-back");
+    }
+  }
+  res->iters = h.iters;
+  res->rel_res = h.rel_res;
+  res->restarts = h.restarts;
+  res->true_rel_res = -1.0;
+  if (sa.o.true_residual) {
+    double rr = h.aux[0], bb = h.aux[1];
+    res->true_rel_res = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+    if (res->rel_res < 0.0) res->rel_res = res->true_rel_res;
+  }
+  switch (h.status) {
+    case DS_CONVERGED: res->status = HS_OK; break;
+    case DS_MAXIT: res->status = HS_NOT_CONVERGED; break;
+    case DS_BREAKDOWN: res->status = HS_ERR_BREAKDOWN; break;
+    case DS_NONFINITE: res->status = HS_ERR_NONFINITE; break;
+    case DS_TIMEOUT: res->status = HS_ERR_TIMEOUT; break;
+    default:
+      res->status = HS_ERR_CUDA;
+      set_error("solver ended without a status (%d)", h.status);
+      return HS_ERR_CUDA;
+  }
+  if (res->status == HS_ERR_TIMEOUT) set_error("a device-side wait ran out (timeout)");
+  if (res->status == HS_ERR_BREAKDOWN) set_error("Krylov breakdown (vanishing denominator)");
+  if (res->status == HS_ERR_NONFINITE) set_error("non-finite value in a reduction");
+  return (hs_status)res->status;
+}
+
+hs_status finish_solve_pub(const SolveArgs& sa, const Common& cm, const void* D, const void* ax, const void* ay,
+                           const void* az, void* rbuf, hs_result* res, double* hist, bool want_hist) {
+  Tail t{sa.A, sa.dtype, D, ax, ay, az, sa.b, sa.x, rbuf};
+  return finish_solve(sa, cm, t, res, hist, want_hist);
+}
+
+// ---- Jacobi -----------------------------------------------------------------
+hs_status run_jacobi(const SolveArgs& sa, hs_result* res, double* hist) {
+  return dispatch(sa.dtype, opkind_of(sa.A), sa.A->ndim, [&](auto tag) -> hs_status {
+    using Tg = decltype(tag);
+    using T = typename Tg::T;
+    constexpr int OPK = Tg::OPK, NDIM = Tg::NDIM;
+    const hs_op* A = sa.A;
+    Geom g = geom_of(A);
+    Carve c{sa.ws, 0, sa.ws_bytes, true};
+    Common cm = carve_common(c, sa.maxit);
+    JacArgs<T> a = {};
+    a.x1 = c.take<T>(g.N);
+    a.bD = c.take<T>(g.N);
+    T *D = nullptr, *ax = nullptr, *ay = nullptr, *az = nullptr;
+    if (OPK == OP_VARK) {
+      D = c.take<T>(g.N);
+      ax = c.take<T>(g.N);
+      ay = c.take<T>(g.N);
+      az = c.take<T>(g.N);
+    }
+    if (!c.ok) {
+      set_error("workspace too small for Jacobi");
+      return HS_ERR_WORKSPACE;
+    }
+    hs_status s = init_ctrl(cm, sa.o, sa.stream);
+    if (s != HS_OK) return s;
+    if (OPK == OP_VARK) {
+      s = setup_vark(A, sa.dtype, D, ax, ay, az, true, sa.stream);
+      if (s != HS_OK) return s;
+      a.cf.D = D;
+      a.cf.ax = ax;
+      a.cf.ay = ay;
+      a.cf.az = az;
+      a.dscale2 = 1.0;
+    } else {
+      a.cf = jacobi_coef<T>(A, &a.invd, &a.dscale2);
+    }
+    a.g = g;
+    a.b = (const T*)sa.b;
+    a.x0 = (T*)sa.x;
+    a.cm = cm;
+    a.maxit = sa.maxit;
+    a.tol = sa.tol;
+    a.fuse = sa.tol > 0.0 ? 1 : 0;
+    int by = rows_per_tile(g);
+    size_t smem = slab_bytes<T>(by);
+    int grid;
+    s = plan_persistent(k_jacobi<T, OPK, NDIM>, 32 * by, smem, g, by, false, &grid, &a.tl);
+    if (s != HS_OK) return s;
+    void* args[] = {&a};
+    s = launch_coop((const void*)k_jacobi<T, OPK, NDIM>, grid, 32 * by, args, smem, sa.stream);
+    if (s != HS_OK) return s;
+    if (OPK == OP_VARK && sa.o.true_residual) {
+      s = setup_vark(A, sa.dtype, D, ax, ay, az, false, sa.stream);  // un-inverted diagonal
+      if (s != HS_OK) return s;
+    }
+    Tail t{A, sa.dtype, D, ax, ay, az, sa.b, sa.x, a.x1};
+    return finish_solve(sa, cm, t, res, hist, sa.tol > 0.0);
+  });
+}
+
+// ---- CG -----------------------------------------------------------------------
+hs_status run_cg(const SolveArgs& sa, hs_result* res, double* hist) {
+  return dispatch(sa.dtype, opkind_of(sa.A), sa.A->ndim, [&](auto tag) -> hs_status {
+    using Tg = decltype(tag);
+    using T = typename Tg::T;
+    constexpr int OPK = Tg::OPK, NDIM = Tg::NDIM;
+    const hs_op* A = sa.A;
+    Geom g = geom_of(A);
+    Carve c{sa.ws, 0, sa.ws_bytes, true};
+    Common cm = carve_common(c, sa.maxit);
+    CgArgs<T> a = {};
+    a.r = c.take<T>(g.N);
+    a.p0 = c.take<T>(g.N);
+    a.p1 = c.take<T>(g.N);
+    a.w = c.take<T>(g.N);
+    T *D = nullptr, *ax = nullptr, *ay = nullptr, *az = nullptr;
+    if (OPK == OP_VARK) {
+      D = c.take<T>(g.N);
+      ax = c.take<T>(g.N);
+      ay = c.take<T>(g.N);
+      az = c.take<T>(g.N);
+    }
+    if (!c.ok) {
+      set_error("workspace too small for CG");
+      return HS_ERR_WORKSPACE;
+    }
+    hs_status s = init_ctrl(cm, sa.o, sa.stream);
+    if (s != HS_OK) return s;
+    if (OPK == OP_VARK) {
+      s = setup_vark(A, sa.dtype, D, ax, ay, az, false, sa.stream);
+      if (s != HS_OK) return s;
+    }
+    a.cf = op_coef<T>(A, D, ax, ay, az, &a.sigma);
+    a.g = g;
+    a.b = (const T*)sa.b;
+    a.x = (T*)sa.x;
+    a.cm = cm;
+    a.maxit = sa.maxit;
+    a.tol = sa.tol;
+    int by = rows_per_tile(g);
+    size_t smem = slab_bytes<T>(by);
+    int grid;
+    s = plan_persistent(k_cg<T, OPK, NDIM>, 32 * by, smem, g, by, true, &grid, &a.tl);
+    if (s != HS_OK) return s;
+    void* args[] = {&a};
+    s = launch_coop((const void*)k_cg<T, OPK, NDIM>, grid, 32 * by, args, smem, sa.stream);
+    if (s != HS_OK) return s;
+    Tail t{A, sa.dtype, D, ax, ay, az, sa.b, sa.x, a.w};
+    return finish_solve(sa, cm, t, res, hist, true);
+  });
+}
+
+// ---- BiCGStab ---------------------------------------------------------------------
+hs_status run_bicgstab(const SolveArgs& sa, hs_result* res, double* hist) {
+  return dispatch(sa.dtype, opkind_of(sa.A), sa.A->ndim, [&](auto tag) -> hs_status {
+    using Tg = decltype(tag);
+    using T = typename Tg::T;
+    constexpr int OPK = Tg::OPK, NDIM = Tg::NDIM;
+    const hs_op* A = sa.A;
+    Geom g = geom_of(A);
+    Carve c{sa.ws, 0, sa.ws_bytes, true};
+    Common cm = carve_common(c, sa.maxit);
+    BiArgs<T> a = {};
+    a.r = c.take<T>(g.N);
+    a.rs = c.take<T>(g.N);
+    a.p0 = c.take<T>(g.N);
+    a.p1 = c.take<T>(g.N);
+    a.v0 = c.take<T>(g.N);
+    a.v1 = c.take<T>(g.N);
+    a.s = c.take<T>(g.N);
+    a.t = c.take<T>(g.N);
+    T *D = nullptr, *ax = nullptr, *ay = nullptr, *az = nullptr;
+    if (OPK == OP_VARK) {
+      D = c.take<T>(g.N);
+      ax = c.take<T>(g.N);
+      ay = c.take<T>(g.N);
+      az = c.take<T>(g.N);
+    }
+    if (!c.ok) {
+      set_error("workspace too small for BiCGStab");
+      return HS_ERR_WORKSPACE;
+    }
+    hs_status s = init_ctrl(cm, sa.o, sa.stream);
+    if (s != HS_OK) return s;
+    if (OPK == OP_VARK) {
+      s = setup_vark(A, sa.dtype, D, ax, ay, az, false, sa.stream);
+      if (s != HS_OK) return s;
+    }
+    a.cf = op_coef<T>(A, D, ax, ay, az, &a.sigma);
+    a.g = g;
+    a.b = (const T*)sa.b;
+    a.x = (T*)sa.x;
+    a.cm = cm;
+    a.maxit = sa.maxit;
+    a.tol = sa.tol;
+    a.reps = sa.o.restart_eps;
+    int by = rows_per_tile(g);
+    size_t smem = slab_bytes<T>(by);
+    int grid;
+    s = plan_persistent(k_bicgstab<T, OPK, NDIM>, 32 * by, smem, g, by, true, &grid, &a.tl);
+    if (s != HS_OK) return s;
+    void* args[] = {&a};
+    s = launch_coop((const void*)k_bicgstab<T, OPK, NDIM>, grid, 32 * by, args, smem, sa.stream);
+    if (s != HS_OK) return s;
+    Tail t{A, sa.dtype, D, ax, ay, az, sa.b, sa.x, a.s};
+    return finish_solve(sa, cm, t, res, hist, true);
+  });
+}
+
+}  // namespace hs

@@ -1,0 +1,235 @@
+"""Python front end of libhsolve: structured-grid operators and the four
+classical iterative methods of arXiv 2305.05988 (Jacobi, Gauss-Seidel, CG,
+BiCGStab), running in hand-written CUDA kernels for sm_103a.
+
+PyTorch only supplies device memory and the current CUDA stream; every step
+of every solve runs inside libhsolve.  Vectors are contiguous CUDA tensors
+of float64 (or float32) in lexicographic order (x fastest), i.e. a tensor of
+shape (n_z, n_y, n_x) flattened.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import check
+
+_DT = {torch.float64: _lib.HS_F64, torch.float32: _lib.HS_F32}
+_GS_MODES = {"forward": _lib.HS_GS_FORWARD, "backward": _lib.HS_GS_BACKWARD, "symmetric": _lib.HS_GS_SYMMETRIC}
+
+
+@dataclass
+class SolveInfo:
+    """Outcome of a solve (mirrors hs_result)."""
+    iters: int
+    status: str
+    status_code: int
+    rel_res: float
+    true_rel_res: float
+    restarts: int = 0
+    history: Optional[np.ndarray] = None
+    outer: int = 0
+    inner_iters: int = 0
+
+    @property
+    def converged(self) -> bool:
+        return self.status_code == _lib.HS_OK
+
+
+class Operator:
+    """A matrix-free structured-grid operator (Laplacian, upwind convection-diffusion
+    or variable-coefficient diffusion) on n_x [* n_y [* n_z]] interior nodes with
+    homogeneous Dirichlet boundaries and spacing h_d = 1/(n_d + 1)."""
+
+    def __init__(self, shape: Sequence[int], kind: str = "laplacian", beta=None, k: Optional[torch.Tensor] = None):
+        lib = _lib.load()
+        self.shape = tuple(int(s) for s in shape)
+        self.ndim = len(self.shape)
+        self.kind = kind
+        self.N = int(np.prod(self.shape))
+        self._grid = ctypes.c_void_p()
+        self._op = ctypes.c_void_p()
+        self._k = None
+        n = (ctypes.c_int64 * 3)(*(list(self.shape) + [1] * (3 - self.ndim)))
+        check(lib.hs_grid_create(self.ndim, n, ctypes.byref(self._grid)), "hs_grid_create")
+        try:
+            if kind == "laplacian":
+                check(lib.hs_op_laplacian(self._grid, ctypes.byref(self._op)), "hs_op_laplacian")
+            elif kind == "upwind":
+                b = (ctypes.c_double * 3)(*(list(beta) + [0.0] * (3 - len(beta))))
+                self.beta = tuple(float(v) for v in beta)
+                check(lib.hs_op_convdiff_upwind(self._grid, b, ctypes.byref(self._op)), "hs_op_convdiff_upwind")
+            elif kind == "diffusion":
+                if k is None or not k.is_cuda:
+                    raise ValueError("diffusion operator needs k as a CUDA tensor")
+                if k.numel() != self.N or k.dtype not in _DT:
+                    raise ValueError("k must hold N float64/float32 values")
+                self._k = k.contiguous()
+                check(lib.hs_op_diffusion(self._grid, _DT[self._k.dtype], ctypes.c_void_p(self._k.data_ptr()),
+                                          ctypes.byref(self._op)), "hs_op_diffusion")
+            else:
+                raise ValueError("unknown operator kind %r" % kind)
+        finally:
+            lib.hs_grid_destroy(self._grid)
+            self._grid = None
+        self._ws = {}
+
+    # -- constructors -------------------------------------------------------
+    @classmethod
+    def laplacian(cls, shape):
+        return cls(shape, "laplacian")
+
+    @classmethod
+    def upwind(cls, shape, beta):
+        return cls(shape, "upwind", beta=beta)
+
+    @classmethod
+    def diffusion(cls, shape, k: torch.Tensor):
+        return cls(shape, "diffusion", k=k)
+
+    def __del__(self):
+        try:
+            if getattr(self, "_op", None) is not None and self._op.value:
+                _lib.load().hs_op_destroy(self._op)
+                self._op = None
+        except Exception:
+            pass
+
+    # -- helpers ----------------------------------------------------------------
+    def _vec(self, t: torch.Tensor, name: str) -> torch.Tensor:
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError("%s must be a CUDA tensor" % name)
+        if t.dtype not in _DT:
+            raise TypeError("%s must be float64 or float32" % name)
+        if t.numel() != self.N:
+            raise ValueError("%s has %d elements, operator has %d" % (name, t.numel(), self.N))
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+        return t
+
+    def workspace(self, solver: int, dtype: torch.dtype, maxit: int, device) -> torch.Tensor:
+        """Device workspace for a solver (cached per size on this operator)."""
+        size = ctypes.c_size_t()
+        check(_lib.load().hs_workspace_size(self._op, solver, _DT[dtype], None, int(maxit), ctypes.byref(size)),
+              "hs_workspace_size")
+        key = (str(device), size.value)
+        ws = self._ws.get(key)
+        if ws is None:
+            self._ws.clear()
+            ws = torch.empty(max(size.value, 256), dtype=torch.uint8, device=device)
+            self._ws[key] = ws
+        return ws
+
+    # -- operator application -----------------------------------------------
+    def spmv(self, x: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """y = A x."""
+        self._vec(x, "x")
+        y = torch.empty_like(x) if out is None else self._vec(out, "out")
+        with torch.cuda.device(x.device):
+            st = torch.cuda.current_stream(x.device).cuda_stream
+            check(_lib.load().hs_spmv(self._op, _DT[x.dtype], ctypes.c_void_p(x.data_ptr()),
+                                      ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(st)), "hs_spmv")
+        return y
+
+    def residual(self, b: torch.Tensor, x: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """r = b - A x."""
+        self._vec(b, "b")
+        self._vec(x, "x")
+        r = torch.empty_like(x) if out is None else self._vec(out, "out")
+        with torch.cuda.device(x.device):
+            st = torch.cuda.current_stream(x.device).cuda_stream
+            check(_lib.load().hs_residual(self._op, _DT[x.dtype], ctypes.c_void_p(b.data_ptr()),
+                                          ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(r.data_ptr()),
+                                          ctypes.c_void_p(st)), "hs_residual")
+        return r
+
+
+def make_opts(**kw) -> _lib.hs_opts:
+    o = _lib.hs_opts()
+    o.struct_size = ctypes.sizeof(_lib.hs_opts)
+    o.gs_mode = _lib.HS_GS_FORWARD
+    o.check_every = 1
+    o.restart_eps = 1e-5
+    o.true_residual = 1
+    o.timeout_s = 2.0
+    o.max_outer = 20
+    o.inner_tol = 1e-5
+    o.inner_solver = _lib.HS_SOLVER_CG
+    o.inner_maxit = 10000
+    for k, v in kw.items():
+        if k == "gs_mode" and isinstance(v, str):
+            v = _GS_MODES[v]
+        if k == "inner_solver" and isinstance(v, str):
+            v = {"cg": _lib.HS_SOLVER_CG, "bicgstab": _lib.HS_SOLVER_BICGSTAB}[v]
+        if k == "true_residual":
+            v = int(bool(v))
+        if not hasattr(o, k):
+            raise TypeError("unknown solver option %r" % k)
+        setattr(o, k, v)
+    return o
+
+
+_SOLVER_FN = {
+    _lib.HS_SOLVER_JACOBI: "hs_jacobi",
+    _lib.HS_SOLVER_GAUSS_SEIDEL: "hs_gauss_seidel",
+    _lib.HS_SOLVER_CG: "hs_cg",
+    _lib.HS_SOLVER_BICGSTAB: "hs_bicgstab",
+}
+
+
+def _solve(solver: int, A: Operator, b: torch.Tensor, x0, tol, maxit, history, inplace=False, **kw):
+    A._vec(b, "b")
+    if x0 is None:
+        x = torch.zeros_like(b)
+    else:
+        A._vec(x0, "x0")
+        if x0.dtype != b.dtype:
+            raise TypeError("x0 and b must have the same dtype")
+        x = x0 if inplace else x0.clone()
+    opts = make_opts(**kw)
+    res = _lib.hs_result()
+    hist = np.full(int(maxit) + 1, np.nan) if history else None
+    hptr = hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if hist is not None else None
+    lib = _lib.load()
+    fn = getattr(lib, _SOLVER_FN[solver])
+    with torch.cuda.device(b.device):
+        ws = A.workspace(solver, b.dtype, maxit, b.device)
+        st = torch.cuda.current_stream(b.device).cuda_stream
+        status = fn(A._op, _DT[b.dtype], ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                    float(tol), int(maxit), ctypes.byref(opts), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                    ctypes.c_void_p(st), ctypes.byref(res), hptr)
+    if status in (_lib.HS_ERR_INVALID, _lib.HS_ERR_CUDA, _lib.HS_ERR_WORKSPACE):
+        raise _lib.HsError(status, _SOLVER_FN[solver])
+    if hist is not None:
+        hist = hist[: res.iters + 1]
+    info = SolveInfo(iters=res.iters, status=_lib.STATUS_NAMES.get(res.status, str(res.status)),
+                     status_code=res.status, rel_res=res.rel_res, true_rel_res=res.true_rel_res,
+                     restarts=res.restarts, history=hist, outer=res.outer, inner_iters=res.inner_iters)
+    return x, info
+
+
+def jacobi(A: Operator, b, x0=None, tol: float = 0.0, maxit: int = 100, history: bool = False, **kw):
+    """Jacobi sweeps (section 3.1); tol = 0 runs exactly maxit sweeps."""
+    return _solve(_lib.HS_SOLVER_JACOBI, A, b, x0, tol, maxit, history, **kw)
+
+
+def gauss_seidel(A: Operator, b, x0=None, tol: float = 0.0, maxit: int = 100, mode: str = "forward",
+                 history: bool = False, **kw):
+    """Exactly lexicographic Gauss-Seidel (forward / backward / symmetric)."""
+    return _solve(_lib.HS_SOLVER_GAUSS_SEIDEL, A, b, x0, tol, maxit, history, gs_mode=mode, **kw)
+
+
+def cg(A: Operator, b, x0=None, tol: float = 1e-10, maxit: int = 10000, history: bool = True, **kw):
+    """Classical conjugate gradient with fused stencil/vector passes."""
+    return _solve(_lib.HS_SOLVER_CG, A, b, x0, tol, maxit, history, **kw)
+
+
+def bicgstab(A: Operator, b, x0=None, tol: float = 1e-10, maxit: int = 10000, history: bool = True,
+             restart_eps: float = 1e-5, **kw):
+    """BiCGStab with Algorithm 2's normalised shadow residual and restart."""
+    return _solve(_lib.HS_SOLVER_BICGSTAB, A, b, x0, tol, maxit, history, restart_eps=restart_eps, **kw)

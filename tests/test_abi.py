@@ -1,0 +1,139 @@
+"""The C-ABI library builds, loads and exports every declared symbol; host-only
+entry points validate their arguments.  No GPU needed (no kernel is launched)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2305_05988_gb300 import _build, _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(hs_[a-z0-9_]+)\s*\(", text))
+    return names
+
+
+def _gpu_visible():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+# These tests hand fake device addresses to entry points that must reject the
+# call before touching the GPU.  They run only where no GPU is visible, so a
+# regression in the validation order can never send a bogus pointer to a kernel.
+no_gpu_only = pytest.mark.skipif(_gpu_visible(), reason="fake-pointer validation tests run on CPU-only hosts")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return _lib.load()
+
+
+def test_every_declared_symbol_is_exported_and_bound(lib):
+    decl = declared_symbols()
+    assert len(decl) >= 16
+    for name in sorted(decl):
+        assert hasattr(lib, name), name
+        assert name in _lib.SIGNATURES, "binding misses " + name
+
+
+def test_version_and_error_strings(lib):
+    assert b"sm_103a" in lib.hs_version()
+    assert isinstance(lib.hs_last_error(), bytes)
+
+
+def test_grid_validation(lib):
+    g = ctypes.c_void_p()
+    n = (ctypes.c_int64 * 3)(4, 0, 1)
+    assert lib.hs_grid_create(2, n, ctypes.byref(g)) == _lib.HS_ERR_INVALID
+    assert b"n[1]" in lib.hs_last_error()
+    assert lib.hs_grid_create(4, (ctypes.c_int64 * 3)(1, 1, 1), ctypes.byref(g)) == _lib.HS_ERR_INVALID
+    big = (ctypes.c_int64 * 3)(2048, 2048, 1024)
+    assert lib.hs_grid_create(3, big, ctypes.byref(g)) == _lib.HS_ERR_INVALID
+    assert lib.hs_grid_create(3, (ctypes.c_int64 * 3)(5, 6, 7), ctypes.byref(g)) == _lib.HS_OK
+    op = ctypes.c_void_p()
+    beta_bad = (ctypes.c_double * 3)(1.0, -0.5, 0.0)
+    assert lib.hs_op_convdiff_upwind(g, beta_bad, ctypes.byref(op)) == _lib.HS_ERR_INVALID
+    assert lib.hs_op_diffusion(g, _lib.HS_F64, None, ctypes.byref(op)) == _lib.HS_ERR_INVALID
+    assert lib.hs_op_laplacian(g, ctypes.byref(op)) == _lib.HS_OK
+    assert lib.hs_op_size(op) == 210
+    lib.hs_grid_destroy(g)
+    # workspace sizes grow with the number of solver vectors
+    sizes = {}
+    for s in (0, 1, 2, 3):
+        b = ctypes.c_size_t()
+        assert lib.hs_workspace_size(op, s, _lib.HS_F64, None, 100, ctypes.byref(b)) == _lib.HS_OK
+        sizes[s] = b.value
+    assert sizes[3] > sizes[2] > sizes[0] > 0
+    b32 = ctypes.c_size_t()
+    lib.hs_workspace_size(op, 2, _lib.HS_F32, None, 100, ctypes.byref(b32))
+    assert b32.value < sizes[2]
+    assert lib.hs_workspace_size(op, 7, _lib.HS_F64, None, 100, ctypes.byref(b32)) == _lib.HS_ERR_INVALID
+    lib.hs_op_destroy(op)
+
+
+@no_gpu_only
+def test_solver_rejects_bad_arguments_without_touching_the_gpu(lib):
+    g = ctypes.c_void_p()
+    lib.hs_grid_create(2, (ctypes.c_int64 * 3)(8, 8, 1), ctypes.byref(g))
+    op = ctypes.c_void_p()
+    lib.hs_op_laplacian(g, ctypes.byref(op))
+    lib.hs_grid_destroy(g)
+    res = _lib.hs_result()
+    # null b / x
+    st = lib.hs_cg(op, 0, None, None, 1e-8, 10, None, None, 0, None, ctypes.byref(res), None)
+    assert st == _lib.HS_ERR_INVALID and res.status == _lib.HS_ERR_INVALID
+    # misaligned vectors
+    st = lib.hs_cg(op, 0, ctypes.c_void_p(0x1008), ctypes.c_void_p(0x2000), 1e-8, 10, None, None, 0, None,
+                   ctypes.byref(res), None)
+    assert st == _lib.HS_ERR_INVALID
+    # negative tolerance, negative maxit
+    st = lib.hs_jacobi(op, 0, ctypes.c_void_p(0x1000), ctypes.c_void_p(0x2000), -1.0, 10, None, None, 0, None,
+                       ctypes.byref(res), None)
+    assert st == _lib.HS_ERR_INVALID
+    st = lib.hs_jacobi(op, 0, ctypes.c_void_p(0x1000), ctypes.c_void_p(0x2000), 0.0, -3, None, None, 0, None,
+                       ctypes.byref(res), None)
+    assert st == _lib.HS_ERR_INVALID
+    # missing / small / misaligned workspace
+    st = lib.hs_jacobi(op, 0, ctypes.c_void_p(0x1000), ctypes.c_void_p(0x2000), 0.0, 3, None, None, 0, None,
+                       ctypes.byref(res), None)
+    assert st == _lib.HS_ERR_WORKSPACE
+    st = lib.hs_jacobi(op, 0, ctypes.c_void_p(0x1000), ctypes.c_void_p(0x2000), 0.0, 3, None,
+                       ctypes.c_void_p(0x10000), 64, None, ctypes.byref(res), None)
+    assert st == _lib.HS_ERR_WORKSPACE and b"too small" in lib.hs_last_error()
+    st = lib.hs_jacobi(op, 0, ctypes.c_void_p(0x1000), ctypes.c_void_p(0x2000), 0.0, 3, None,
+                       ctypes.c_void_p(0x10010), 1 << 30, None, ctypes.byref(res), None)
+    assert st == _lib.HS_ERR_WORKSPACE and b"aligned" in lib.hs_last_error()
+    # bad options
+    o = _lib.hs_opts()
+    o.struct_size = 0
+    st = lib.hs_bicgstab(op, 0, ctypes.c_void_p(0x1000), ctypes.c_void_p(0x2000), 1e-8, 3, ctypes.byref(o),
+                         ctypes.c_void_p(0x100000), 1 << 30, None, ctypes.byref(res), None)
+    assert st == _lib.HS_ERR_INVALID
+    lib.hs_op_destroy(op)
+
+
+@no_gpu_only
+def test_cg_rejects_nonsymmetric_operator(lib):
+    g = ctypes.c_void_p()
+    lib.hs_grid_create(2, (ctypes.c_int64 * 3)(8, 8, 1), ctypes.byref(g))
+    op = ctypes.c_void_p()
+    lib.hs_op_convdiff_upwind(g, (ctypes.c_double * 3)(3.0, 1.0, 0.0), ctypes.byref(op))
+    lib.hs_grid_destroy(g)
+    res = _lib.hs_result()
+    st = lib.hs_cg(op, 0, ctypes.c_void_p(0x1000), ctypes.c_void_p(0x2000), 1e-8, 3, None,
+                   ctypes.c_void_p(0x100000), 1 << 30, None, ctypes.byref(res), None)
+    assert st == _lib.HS_ERR_INVALID and b"symmetric" in lib.hs_last_error()
+    lib.hs_op_destroy(op)
