@@ -71,6 +71,7 @@ def _load():
             lib.ora_spmv.argtypes = [op, dp, dp]; lib.ora_spmv.restype = None
             lib.ora_dense.argtypes = [op, dp, ctypes.c_int64]; lib.ora_dense.restype = ctypes.c_int
             lib.ora_relres.argtypes = [op, dp, dp]; lib.ora_relres.restype = ctypes.c_double
+            lib.ora_dot.argtypes = [ctypes.c_int64, dp, dp]; lib.ora_dot.restype = ctypes.c_double
             lib.ora_jacobi.argtypes = [op, dp, dp, ctypes.c_int, ctypes.c_double, dp, P(ctypes.c_int)]
             lib.ora_jacobi.restype = ctypes.c_int
             lib.ora_gs_sweep.argtypes = [op, dp, dp, ctypes.c_int]; lib.ora_gs_sweep.restype = None
@@ -157,6 +158,13 @@ class Operator:
     def relres(self, b, x):
         b = _f64(b).reshape(-1); x = _f64(x).reshape(-1)
         return _load().ora_relres(self._ref(), _ptr(b), _ptr(x))
+
+
+def dot(a, b):
+    """Inner product of two vectors (compensated summation in index order)."""
+    a = _f64(a).reshape(-1); b = _f64(b).reshape(-1)
+    assert a.size == b.size
+    return _load().ora_dot(a.size, _ptr(a), _ptr(b))
 
 
 def _hist(maxit, want):

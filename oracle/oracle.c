@@ -10,7 +10,9 @@
  * path and never calls it.
  *
  * Every loop runs in lexicographic order idx = i + nx*(j + ny*k) (i fastest),
- * every sum is a plain left-to-right sum, and the file is compiled with
+ * every stencil sum is a plain left-to-right sum, inner products are the
+ * exact sum of the rounded products to within a few units in the last place
+ * (compensated summation, see ora_dot), and the file is compiled with
  * -O2 -ffp-contract=off so that no fused multiply-add reorders the rounding.
  *
  * Operators (readings of points the paper leaves open; the paper solves
@@ -146,11 +148,25 @@ int ora_dense(const ora_op *A, double *M, int64_t maxN)
 /* Vector helpers (plain sequential loops)                                  */
 /* ------------------------------------------------------------------------ */
 
+/*
+ * Inner product sum_i a_i b_i.  The terms are added in index order with
+ * Neumaier's compensated summation (A. Neumaier, "Rundungsfehleranalyse
+ * einiger Verfahren zur Summation endlicher Summen", ZAMM 54, 1974): the
+ * rounding error of every addition is carried in c and added back at the
+ * end, so the result stays within a few units of the exactly rounded sum of
+ * the rounded products instead of drifting by O(N) units with the length.
+ */
 double ora_dot(int64_t N, const double *a, const double *b)
 {
-    double s = 0.0;
-    for (int64_t i = 0; i < N; i++) s += a[i] * b[i];
-    return s;
+    double s = 0.0, c = 0.0;
+    for (int64_t i = 0; i < N; i++) {
+        double t = a[i] * b[i];
+        double u = s + t;
+        if (fabs(s) >= fabs(t)) c += (s - u) + t;
+        else                    c += (t - u) + s;
+        s = u;
+    }
+    return s + c;
 }
 
 /* r = b - A x */

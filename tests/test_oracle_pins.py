@@ -132,6 +132,21 @@ def test_diffusion_quadratic_form_and_symmetry():
     assert np.all(np.linalg.eigvalsh(M) > 0)
 
 
+def test_dot_is_nearly_correctly_rounded():
+    # math.fsum is the correctly rounded sum of the rounded products; the
+    # oracle's inner product must sit within 2 ulps of it, even where plain
+    # left-to-right summation cancels catastrophically.
+    a = np.array([1e16, 1.0, -1e16, 3.0])
+    b = np.ones(4)
+    assert oracle.dot(a, b) == 4.0
+    rng = np.random.default_rng(0)
+    for n in (1, 17, 1000, 100000):
+        x = rng.standard_normal(n) * np.exp(rng.uniform(-20, 20, n))
+        y = rng.standard_normal(n)
+        ref = math.fsum((x * y).tolist())
+        assert abs(oracle.dot(x, y) - ref) <= 2 * np.spacing(abs(ref)) + 1e-300
+
+
 # --------------------------------------------------------------------------
 # Jacobi
 # --------------------------------------------------------------------------
