@@ -61,6 +61,8 @@ def parse():
     p.add_argument("--tol", type=float, default=1e-10)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-roofline", action="store_true", help="skip the roofline repeats (profiling runs)")
+    p.add_argument("--timeout-s", type=float, default=2.0, help="bound on device-side waits")
     return p.parse_args()
 
 
@@ -213,6 +215,7 @@ def run_ours(args, rank, world, dist):
     U = hs.Operator.upwind(shape, beta)
     stream = torch.cuda.current_stream(dev)
     maxk = 20000
+    tmo = args.timeout_s
     # workspaces are allocated once, outside the timed region
     xs = {k: torch.zeros(N, dtype=torch.float64, device=dev) for k in ("y", "jacobi", "gs", "cg", "bicgstab")}
 
@@ -225,19 +228,21 @@ def run_ours(args, rank, world, dist):
         if ev:
             ev[1].record(stream)
         xs["jacobi"].zero_()
-        _, info["jacobi"] = hs.jacobi(A, bv, xs["jacobi"], maxit=args.sweeps, inplace=True)
+        _, info["jacobi"] = hs.jacobi(A, bv, xs["jacobi"], maxit=args.sweeps, inplace=True, timeout_s=tmo)
         if ev:
             ev[2].record(stream)
         xs["gs"].zero_()
-        _, info["gauss_seidel"] = hs.gauss_seidel(A, bv, xs["gs"], maxit=args.sweeps, inplace=True)
+        _, info["gauss_seidel"] = hs.gauss_seidel(A, bv, xs["gs"], maxit=args.sweeps, inplace=True,
+                                                  timeout_s=tmo)
         if ev:
             ev[3].record(stream)
         xs["cg"].zero_()
-        _, info["cg"] = hs.cg(A, bv, xs["cg"], tol=args.tol, maxit=maxk, inplace=True)
+        _, info["cg"] = hs.cg(A, bv, xs["cg"], tol=args.tol, maxit=maxk, inplace=True, timeout_s=tmo)
         if ev:
             ev[4].record(stream)
         xs["bicgstab"].zero_()
-        _, info["bicgstab"] = hs.bicgstab(U, bv, xs["bicgstab"], tol=args.tol, maxit=maxk, inplace=True)
+        _, info["bicgstab"] = hs.bicgstab(U, bv, xs["bicgstab"], tol=args.tol, maxit=maxk, inplace=True,
+                                          timeout_s=tmo)
         if ev:
             ev[5].record(stream)
             record.append(ev)
@@ -309,34 +314,38 @@ def run_ours(args, rank, world, dist):
 
     # ---- roofline of the dominant kernel (largest share of the step) ----
     peak, peak_kind = load_peaks()
-    dom = max(["jacobi", "gauss_seidel", "cg", "bicgstab"], key=lambda k: statistics.median(per[k]))
-    ra, rb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = 3
-    dts = []
-    its = 0
-    for _ in range(reps):
-        xs[dom].zero_()
-        torch.cuda.synchronize()
-        ra.record(stream)
-        if dom == "cg":
-            _, inf = hs.cg(A, b, xs["cg"], tol=args.tol, maxit=maxk, inplace=True, true_residual=False)
-        elif dom == "bicgstab":
-            _, inf = hs.bicgstab(U, b, xs["bicgstab"], tol=args.tol, maxit=maxk, inplace=True, true_residual=False)
-        elif dom == "jacobi":
-            _, inf = hs.jacobi(A, b, xs["jacobi"], maxit=args.sweeps, inplace=True, true_residual=False)
-        else:
-            _, inf = hs.gauss_seidel(A, b, xs["gs"], maxit=args.sweeps, inplace=True, true_residual=False)
-        rb.record(stream)
-        torch.cuda.synchronize()
-        dts.append(ra.elapsed_time(rb))
-        its = inf.iters
-    dt = statistics.median(dts)
-    achieved = BYTES[dom] * N * its / (dt * 1e-3) / 1e9
-    kname = {"cg": "k_cg", "bicgstab": "k_bicgstab", "jacobi": "k_jacobi", "gauss_seidel": "k_gs"}[dom]
-    roofline = {"kernel": kname + " (FP64, persistent: one launch per solve)", "bound": "hbm",
-                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "peak_source": peak_kind, "traffic": None,
-                "alg_bytes_per_launch": BYTES[dom] * N * its, "launch_ms": round(dt, 3), "iters": its}
+    roofline = None
+    if not args.no_roofline:
+        dom = max(["jacobi", "gauss_seidel", "cg", "bicgstab"], key=lambda k: statistics.median(per[k]))
+        ra, rb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        dts, its = [], 0
+        for _ in range(3):
+            xs[dom].zero_()
+            torch.cuda.synchronize()
+            ra.record(stream)
+            if dom == "cg":
+                _, inf = hs.cg(A, b, xs["cg"], tol=args.tol, maxit=maxk, inplace=True, true_residual=False,
+                               timeout_s=tmo)
+            elif dom == "bicgstab":
+                _, inf = hs.bicgstab(U, b, xs["bicgstab"], tol=args.tol, maxit=maxk, inplace=True,
+                                     true_residual=False, timeout_s=tmo)
+            elif dom == "jacobi":
+                _, inf = hs.jacobi(A, b, xs["jacobi"], maxit=args.sweeps, inplace=True, true_residual=False,
+                                   timeout_s=tmo)
+            else:
+                _, inf = hs.gauss_seidel(A, b, xs["gs"], maxit=args.sweeps, inplace=True, true_residual=False,
+                                         timeout_s=tmo)
+            rb.record(stream)
+            torch.cuda.synchronize()
+            dts.append(ra.elapsed_time(rb))
+            its = inf.iters
+        dt = statistics.median(dts)
+        achieved = BYTES[dom] * N * its / (dt * 1e-3) / 1e9
+        kname = {"cg": "k_cg", "bicgstab": "k_bicgstab", "jacobi": "k_jacobi", "gauss_seidel": "k_gs"}[dom]
+        roofline = {"kernel": kname + " (FP64, persistent: one launch per solve)", "bound": "hbm",
+                    "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                    "frac": round(achieved / peak, 4), "peak_source": peak_kind, "traffic": None,
+                    "alg_bytes_per_launch": BYTES[dom] * N * its, "launch_ms": round(dt, 3), "iters": its}
 
     # ---- e2e: host buffers, copies inside the timed region ----
     e2e = None

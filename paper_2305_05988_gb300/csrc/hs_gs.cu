@@ -60,25 +60,57 @@ struct GsArgs {
   int mode;               // HS_GS_FORWARD / BACKWARD / SYMMETRIC
   int check_every;
   double tol;
-  unsigned short line_of[128];  // thread -> (jl | kl << 8), sorted by jl + kl
 };
 
-// Residual of x (via the Jacobi form r = a_ii (x' - x)) reduced over the grid.
+// Line (jl, kl) of thread t when the TY x TZ lines are ordered by jl + kl
+// (then kl): the 32 lines of a warp start within a few substeps of each other.
+__device__ __forceinline__ void line_of_thread(int t, int TY, int TZ, int& jl, int& kl) {
+  int rem = t;
+  jl = 0;
+  kl = 0;
+  for (int dsum = 0; dsum <= TY + TZ - 2; dsum++) {
+    const int klo = max(0, dsum - (TY - 1)), khi = min(TZ - 1, dsum);
+    const int cnt = khi - klo + 1;
+    if (rem < cnt) {
+      kl = klo + rem;
+      jl = dsum - kl;
+      return;
+    }
+    rem -= cnt;
+  }
+}
+
+// Residual of x via the Jacobi form r = a_ii (x' - x), accumulated per thread.
+template <typename T, int OPK, int NDIM>
+struct GsResSink {
+  Coef<T> cf;
+  Geom g;
+  const T* bsrc;
+  double acc[1];
+  struct Raw {
+    OpRaw<T, OPK> o;
+    T b;
+  };
+  __device__ __forceinline__ Raw fetch(long long idx, int i, int j, int k) const {
+    return Raw{op_fetch<T, OPK, NDIM>(cf, g, idx, i, j, k), __ldcg(bsrc + idx)};
+  }
+  __device__ __forceinline__ void operator()(long long, const Nbr<T>& nb, const Raw& q, int, int, int) {
+    T d = jacobi_apply<T, OPK, NDIM>(cf, q.o, nb, q.b) - nb.c;
+    if constexpr (OPK == OP_VARK) d = d / q.o.d;
+    acc[0] += (double)d * (double)d;
+  }
+};
+
+// Relative residual of x reduced over the grid.
 template <typename T, int OPK, int NDIM>
 __device__ bool gs_residual(const GsArgs<T>& a, T* sm, double* sh, double bb, double* rel) {
-  double racc[1] = {0.0};
   const T* bsrc = (OPK == OP_VARK) ? a.b : a.bD;
-  auto src = [&](long long idx, bool) -> T { return __ldcg(a.x + idx); };
-  auto sink = [&](long long idx, const Nbr<T>& nb, int i, int j, int kk) {
-    T xn = jacobi_update<T, OPK, NDIM>(a.cf, a.g, idx, i, j, kk, nb, __ldcg(bsrc + idx));
-    T d = xn - nb.c;
-    if (OPK == OP_VARK) d = d / __ldg(a.cf.D + idx);
-    racc[0] += (double)d * (double)d;
-  };
+  LoadSrc<T, true> src{a.x};
+  GsResSink<T, OPK, NDIM> sink{a.cf, a.g, bsrc, {0.0}};
   for (int item = blockIdx.x; item < a.tl.items(); item += gridDim.x) zmarch_item<T, NDIM>(a.g, a.tl, item, sm, src, sink);
-  block_sum<1>(racc, sh);
+  block_sum<1>(sink.acc, sh);
   double rr[1];
-  if (!grid_reduce<1>(a.cm.ctrl, a.cm.partials, racc, rr, sh)) return false;
+  if (!grid_reduce<1>(a.cm.ctrl, a.cm.partials, sink.acc, rr, sh)) return false;
   double sc = (OPK == OP_VARK) ? 1.0 : a.dscale2;
   *rel = sqrt(rr[0] * sc / bb);
   return true;
@@ -108,8 +140,8 @@ __device__ __forceinline__ void gs_tile(const GsArgs<T>& a, T* sm, int tile, boo
   }
   __syncthreads();
 
-  const unsigned short ln = a.line_of[threadIdx.x];
-  int jl = ln & 0xff, kl = ln >> 8;
+  int jl, kl;
+  line_of_thread(threadIdx.x, TY, TZ, jl, kl);
   if (backward) {
     jl = TY - 1 - jl;
     kl = TZ - 1 - kl;
@@ -120,10 +152,27 @@ __device__ __forceinline__ void gs_tile(const GsArgs<T>& a, T* sm, int tile, boo
   const int base = ((kl + ZOFF) * SY + (jl + 1)) * SX + 1;
   const long long gbase = (long long)gk * g.plane + (long long)gj * g.nx + i0;
   const int nsteps = TX + TY + TZ - 2;
+  // per-node operands of the next substep are loaded one substep ahead
+  // local x index of this line at substep s, or -1 when the line is idle
+#define HS_IL_AT(S) ((((S) - d) < 0 || ((S) - d) >= TX) ? -1 : \
+                     ((line_in && i0 + (backward ? TX - 1 - ((S) - d) : ((S) - d)) < g.nx) ? \
+                      (backward ? TX - 1 - ((S) - d) : ((S) - d)) : -1))
+  int il = HS_IL_AT(0);
+  T bcur = T(0);
+  OpRaw<T, OPK> ocur{};
+  if (il >= 0) {
+    bcur = __ldcg(bsrc + gbase + il);
+    ocur = op_fetch<T, OPK, NDIM>(a.cf, g, gbase + il, i0 + il, gj, gk);
+  }
   for (int s = 0; s < nsteps; s++) {
-    int il = s - d;
-    if (backward) il = TX - 1 - il;
-    if (line_in && il >= 0 && il < TX && i0 + il < g.nx) {
+    const int il_n = HS_IL_AT(s + 1);
+    T bnext = T(0);
+    OpRaw<T, OPK> onext{};
+    if (il_n >= 0) {
+      bnext = __ldcg(bsrc + gbase + il_n);
+      onext = op_fetch<T, OPK, NDIM>(a.cf, g, gbase + il_n, i0 + il_n, gj, gk);
+    }
+    if (il >= 0) {
       const int c = base + il;
       Nbr<T> nb;
       nb.c = sm[c];
@@ -138,11 +187,14 @@ __device__ __forceinline__ void gs_tile(const GsArgs<T>& a, T* sm, int tile, boo
         nb.b = T(0);
         nb.t = T(0);
       }
-      const long long idx = gbase + il;
-      sm[c] = jacobi_update<T, OPK, NDIM>(a.cf, g, idx, i0 + il, gj, gk, nb, __ldcg(bsrc + idx));
+      sm[c] = jacobi_apply<T, OPK, NDIM>(a.cf, ocur, nb, bcur);
     }
     __syncthreads();
+    il = il_n;
+    bcur = bnext;
+    ocur = onext;
   }
+#undef HS_IL_AT
 
   // store the tile interior
   for (int e = threadIdx.x; e < TX * TY * TZ; e += blockDim.x) {
@@ -372,15 +424,6 @@ static hs_status gs_run_t(const SolveArgs& sa, hs_result* res, double* hist) {
     a.dscale2 = 1.0;
   } else {
     a.cf = gs_jacobi_coef<T>(A, &a.invd, &a.dscale2);
-  }
-  // lines sorted by jl + kl
-  {
-    int k = 0;
-    for (int dsum = 0; dsum <= TY + TZ - 2; dsum++)
-      for (int kl = 0; kl < TZ; kl++) {
-        int jl = dsum - kl;
-        if (jl >= 0 && jl < TY) a.line_of[k++] = (unsigned short)(jl | (kl << 8));
-      }
   }
   a.g = g;
   a.b = (const T*)sa.b;

@@ -34,6 +34,53 @@ __device__ __forceinline__ void finish(Ctrl* c, int status, int iters, double re
 }
 
 // ===========================================================================
+// Common sinks
+// ===========================================================================
+
+// y = A x (scaled operator times sigma).
+template <typename T, int OPK, int NDIM>
+struct SpmvSink {
+  Coef<T> cf;
+  Geom g;
+  T sigma;
+  T* y;
+  using Raw = OpRaw<T, OPK>;
+  __device__ __forceinline__ Raw fetch(long long idx, int i, int j, int k) const {
+    return op_fetch<T, OPK, NDIM>(cf, g, idx, i, j, k);
+  }
+  __device__ __forceinline__ void operator()(long long idx, const Nbr<T>& nb, const Raw& o, int, int, int) {
+    T v = op_apply<T, OPK, NDIM>(cf, o, nb);
+    if (OPK != OP_VARK) v *= sigma;
+    y[idx] = v;
+  }
+};
+
+// r = b - A x, accumulating ||r||^2 and ||b||^2.
+template <typename T, int OPK, int NDIM>
+struct ResidualSink {
+  Coef<T> cf;
+  Geom g;
+  T sigma;
+  const T* b;
+  T* r;
+  double acc[2];
+  struct Raw {
+    OpRaw<T, OPK> o;
+    T b;
+  };
+  __device__ __forceinline__ Raw fetch(long long idx, int i, int j, int k) const {
+    return Raw{op_fetch<T, OPK, NDIM>(cf, g, idx, i, j, k), __ldg(b + idx)};
+  }
+  __device__ __forceinline__ void operator()(long long idx, const Nbr<T>& nb, const Raw& q, int, int, int) {
+    T v = op_apply<T, OPK, NDIM>(cf, q.o, nb);
+    T rv = (OPK == OP_VARK) ? q.b - v : fma(-sigma, v, q.b);
+    r[idx] = rv;
+    acc[0] += (double)rv * (double)rv;
+    acc[1] += (double)q.b * (double)q.b;
+  }
+};
+
+// ===========================================================================
 // SpMV and residual (one work item per block)
 // ===========================================================================
 
@@ -42,12 +89,8 @@ __global__ void __launch_bounds__(512) k_spmv(Geom g, Tiling tl, Coef<T> cf, T s
                                               T* __restrict__ y) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
-  auto src = [&](long long idx, bool) -> T { return __ldg(x + idx); };
-  auto sink = [&](long long idx, const Nbr<T>& nb, int i, int j, int k) {
-    T v = apply_op<T, OPK, NDIM>(cf, g, idx, i, j, k, nb);
-    if (OPK != OP_VARK) v *= sigma;
-    y[idx] = v;
-  };
+  LoadSrc<T, false> src{x};
+  SpmvSink<T, OPK, NDIM> sink{cf, g, sigma, y};
   for (int item = blockIdx.x; item < tl.items(); item += gridDim.x) zmarch_item<T, NDIM>(g, tl, item, sm, src, sink);
 }
 
@@ -57,21 +100,13 @@ __global__ void __launch_bounds__(512) k_residual(Geom g, Tiling tl, Coef<T> cf,
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double sh[32 * 2];
   T* sm = reinterpret_cast<T*>(smraw);
-  double acc[2] = {0.0, 0.0};
-  auto src = [&](long long idx, bool) -> T { return __ldg(x + idx); };
-  auto sink = [&](long long idx, const Nbr<T>& nb, int i, int j, int k) {
-    T v = apply_op<T, OPK, NDIM>(cf, g, idx, i, j, k, nb);
-    T bv = __ldg(b + idx);
-    T rv = (OPK == OP_VARK) ? bv - v : fma(-sigma, v, bv);
-    r[idx] = rv;
-    acc[0] += (double)rv * (double)rv;
-    acc[1] += (double)bv * (double)bv;
-  };
+  LoadSrc<T, false> src{x};
+  ResidualSink<T, OPK, NDIM> sink{cf, g, sigma, b, r, {0.0, 0.0}};
   for (int item = blockIdx.x; item < tl.items(); item += gridDim.x) zmarch_item<T, NDIM>(g, tl, item, sm, src, sink);
-  block_sum<2>(acc, sh);
+  block_sum<2>(sink.acc, sh);
   if (partials && threadIdx.x == 0) {
-    partials[2 * blockIdx.x] = acc[0];
-    partials[2 * blockIdx.x + 1] = acc[1];
+    partials[2 * blockIdx.x] = sink.acc[0];
+    partials[2 * blockIdx.x + 1] = sink.acc[1];
   }
 }
 
@@ -135,6 +170,12 @@ __global__ void k_vark_setup(Geom g, int ndim, const K* __restrict__ kk, double 
   }
 }
 
+// Elementwise passes process ILP elements per thread per round: all loads of
+// a round are issued before any arithmetic or store, so several memory
+// requests are in flight per thread.  The element -> thread assignment and
+// the per-thread accumulation order are fixed by the launch shape.
+constexpr int ILP = 4;
+
 // ===========================================================================
 // Jacobi (section 3.1), out of place, persistent.
 // ===========================================================================
@@ -154,6 +195,34 @@ struct JacArgs {
   int maxit;
   double tol;
   int fuse;        // 1: fuse the residual of each iterate into the next sweep
+};
+
+// x' = Jacobi update of x; optionally accumulates the residual of x,
+// r = a_ii (x' - x).
+template <typename T, int OPK, int NDIM>
+struct JacobiSink {
+  Coef<T> cf;
+  Geom g;
+  const T* bsrc;   // b/a_ii (constant) or b (variable)
+  T* xd;
+  int fuse;
+  double acc[1];
+  struct Raw {
+    OpRaw<T, OPK> o;
+    T b;
+  };
+  __device__ __forceinline__ Raw fetch(long long idx, int i, int j, int k) const {
+    return Raw{op_fetch<T, OPK, NDIM>(cf, g, idx, i, j, k), __ldcg(bsrc + idx)};
+  }
+  __device__ __forceinline__ void operator()(long long idx, const Nbr<T>& nb, const Raw& q, int, int, int) {
+    T xn = jacobi_apply<T, OPK, NDIM>(cf, q.o, nb, q.b);
+    xd[idx] = xn;
+    if (fuse) {
+      T d = xn - nb.c;
+      if constexpr (OPK == OP_VARK) d = d / q.o.d;
+      acc[0] += (double)d * (double)d;
+    }
+  }
 };
 
 template <typename T, int OPK, int NDIM>
@@ -187,23 +256,14 @@ __global__ void __launch_bounds__(512) k_jacobi(JacArgs<T> a) {
       iters = k;
       break;
     }
-    double racc[1] = {0.0};
-    auto src = [&](long long idx, bool) -> T { return ldcg(xs + idx); };
-    auto sink = [&](long long idx, const Nbr<T>& nb, int i, int j, int kk) {
-      T xn = jacobi_update<T, OPK, NDIM>(a.cf, a.g, idx, i, j, kk, nb, ldcg(bsrc + idx));
-      xd[idx] = xn;
-      if (a.fuse) {
-        T d = xn - nb.c;
-        if (OPK == OP_VARK) d = d / __ldg(a.cf.D + idx);
-        racc[0] += (double)d * (double)d;
-      }
-    };
+    LoadSrc<T, true> src{xs};
+    JacobiSink<T, OPK, NDIM> sink{a.cf, a.g, bsrc, xd, a.fuse, {0.0}};
     for (int item = blockIdx.x; item < a.tl.items(); item += gridDim.x)
       zmarch_item<T, NDIM>(a.g, a.tl, item, sm, src, sink);
     if (a.fuse) {
-      block_sum<1>(racc, sh);
+      block_sum<1>(sink.acc, sh);
       double rr[1];
-      if (!grid_reduce<1>(a.cm.ctrl, a.cm.partials, racc, rr, sh)) return;
+      if (!grid_reduce<1>(a.cm.ctrl, a.cm.partials, sink.acc, rr, sh)) return;
       double sc = (OPK == OP_VARK) ? 1.0 : a.dscale2;
       rel = sqrt(rr[0] * sc / bb[0]);
       if (blockIdx.x == 0 && threadIdx.x == 0) a.cm.hist[k] = rel;
@@ -255,6 +315,48 @@ struct CgArgs {
   double tol;
 };
 
+// p = r + beta p_old (or p = r), stored for owned nodes.
+template <typename T>
+struct PUpdateSrc {
+  const T* r;
+  const T* pold;
+  T* pnew;
+  T beta;
+  bool first;
+  struct Raw {
+    T r, p;
+  };
+  __device__ __forceinline__ Raw fetch(long long idx) const {
+    Raw q;
+    q.r = __ldcg(r + idx);
+    q.p = first ? T(0) : __ldcg(pold + idx);
+    return q;
+  }
+  __device__ __forceinline__ T make(const Raw& q, long long idx, bool own) const {
+    T pv = first ? q.r : fma(beta, q.p, q.r);
+    if (own) pnew[idx] = pv;
+    return pv;
+  }
+};
+
+// w = A p / sigma, accumulating p.w.
+template <typename T, int OPK, int NDIM>
+struct ApDotSink {
+  Coef<T> cf;
+  Geom g;
+  T* w;
+  double acc[1];
+  using Raw = OpRaw<T, OPK>;
+  __device__ __forceinline__ Raw fetch(long long idx, int i, int j, int k) const {
+    return op_fetch<T, OPK, NDIM>(cf, g, idx, i, j, k);
+  }
+  __device__ __forceinline__ void operator()(long long idx, const Nbr<T>& nb, const Raw& o, int, int, int) {
+    T wv = op_apply<T, OPK, NDIM>(cf, o, nb);
+    w[idx] = wv;
+    acc[0] += (double)nb.c * (double)wv;
+  }
+};
+
 template <typename T, int OPK, int NDIM>
 __global__ void __launch_bounds__(512) k_cg(CgArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -264,23 +366,15 @@ __global__ void __launch_bounds__(512) k_cg(CgArgs<T> a) {
   const T sig = (T)a.sigma;
 
   // r = b - A x ; ||r||^2, ||b||^2
-  double acc2[2] = {0.0, 0.0};
+  ResidualSink<T, OPK, NDIM> rsink{a.cf, a.g, sig, a.b, a.r, {0.0, 0.0}};
   {
-    auto src = [&](long long idx, bool) -> T { return ldcg(a.x + idx); };
-    auto sink = [&](long long idx, const Nbr<T>& nb, int i, int j, int k) {
-      T v = apply_op<T, OPK, NDIM>(a.cf, a.g, idx, i, j, k, nb);
-      T bv = __ldg(a.b + idx);
-      T rv = (OPK == OP_VARK) ? bv - v : fma(-sig, v, bv);
-      a.r[idx] = rv;
-      acc2[0] += (double)rv * (double)rv;
-      acc2[1] += (double)bv * (double)bv;
-    };
+    LoadSrc<T, true> src{a.x};
     for (int item = blockIdx.x; item < a.tl.items(); item += gridDim.x)
-      zmarch_item<T, NDIM>(a.g, a.tl, item, sm, src, sink);
+      zmarch_item<T, NDIM>(a.g, a.tl, item, sm, src, rsink);
   }
-  block_sum<2>(acc2, sh);
+  block_sum<2>(rsink.acc, sh);
   double s2[2];
-  if (!grid_reduce<2>(a.cm.ctrl, a.cm.partials, acc2, s2, sh)) return;
+  if (!grid_reduce<2>(a.cm.ctrl, a.cm.partials, rsink.acc, s2, sh)) return;
   double rr = s2[0];
   const double bb = s2[1];
   if (bb == 0.0) {
@@ -299,31 +393,19 @@ __global__ void __launch_bounds__(512) k_cg(CgArgs<T> a) {
   double beta = 0.0;
   bool first = true;
   int it = 0, status = DS_MAXIT;
+  const long long st = gstride();
   while (it < a.maxit) {
     it++;
     const T* pold = (it & 1) ? a.p0 : a.p1;
     T* pnew = (it & 1) ? a.p1 : a.p0;
-    const T tb = (T)beta;
     // ---- pass 1: p = r + beta p_old ; w = A p / sigma ; p.w
-    double acc[1] = {0.0};
-    {
-      auto src = [&](long long idx, bool own) -> T {
-        T rv = ldcg(a.r + idx);
-        T pv = first ? rv : fma(tb, ldcg(pold + idx), rv);
-        if (own) pnew[idx] = pv;
-        return pv;
-      };
-      auto sink = [&](long long idx, const Nbr<T>& nb, int i, int j, int k) {
-        T wv = apply_op<T, OPK, NDIM>(a.cf, a.g, idx, i, j, k, nb);
-        a.w[idx] = wv;
-        acc[0] += (double)nb.c * (double)wv;
-      };
-      for (int item = blockIdx.x; item < a.tl.items(); item += gridDim.x)
-        zmarch_item<T, NDIM>(a.g, a.tl, item, sm, src, sink);
-    }
-    block_sum<1>(acc, sh);
+    PUpdateSrc<T> src{a.r, pold, pnew, (T)beta, first};
+    ApDotSink<T, OPK, NDIM> sink{a.cf, a.g, a.w, {0.0}};
+    for (int item = blockIdx.x; item < a.tl.items(); item += gridDim.x)
+      zmarch_item<T, NDIM>(a.g, a.tl, item, sm, src, sink);
+    block_sum<1>(sink.acc, sh);
     double pw[1];
-    if (!grid_reduce<1>(a.cm.ctrl, a.cm.partials, acc, pw, sh)) return;
+    if (!grid_reduce<1>(a.cm.ctrl, a.cm.partials, sink.acc, pw, sh)) return;
     if (!(pw[0] > 0.0) || !finite_d(pw[0])) {
       status = finite_d(pw[0]) ? DS_BREAKDOWN : DS_NONFINITE;
       break;
@@ -333,11 +415,30 @@ __global__ void __launch_bounds__(512) k_cg(CgArgs<T> a) {
     const T tar = (T)ar, tax = (T)axs;
     // ---- pass 2: x += alpha p ; r -= alpha A p ; r.r
     double acc1[1] = {0.0};
-    for (long long i = gtid(); i < N; i += gstride()) {
-      T pv = ldcg(pnew + i);
-      T wv = ldcg(a.w + i);
-      T xv = fma(tax, pv, ldcg(a.x + i));
-      T rv = fma(-tar, wv, ldcg(a.r + i));
+    long long i = gtid();
+    for (; i + (ILP - 1) * st < N; i += ILP * st) {
+      T pv[ILP], wv[ILP], xv[ILP], rv[ILP];
+#pragma unroll
+      for (int u = 0; u < ILP; u++) {
+        const long long q = i + u * st;
+        pv[u] = ldcg(pnew + q);
+        wv[u] = ldcg(a.w + q);
+        xv[u] = ldcg(a.x + q);
+        rv[u] = ldcg(a.r + q);
+      }
+#pragma unroll
+      for (int u = 0; u < ILP; u++) {
+        const long long q = i + u * st;
+        xv[u] = fma(tax, pv[u], xv[u]);
+        rv[u] = fma(-tar, wv[u], rv[u]);
+        a.x[q] = xv[u];
+        a.r[q] = rv[u];
+        acc1[0] += (double)rv[u] * (double)rv[u];
+      }
+    }
+    for (; i < N; i += st) {
+      T xv = fma(tax, ldcg(pnew + i), ldcg(a.x + i));
+      T rv = fma(-tar, ldcg(a.w + i), ldcg(a.r + i));
       a.x[i] = xv;
       a.r[i] = rv;
       acc1[0] += (double)rv * (double)rv;
@@ -396,6 +497,106 @@ struct BiArgs {
   double reps;
 };
 
+// p = r + beta (p_old - omega sigma v_old), or p = r on (re)start.
+template <typename T>
+struct BiPSrc {
+  const T* r;
+  const T* pold;
+  const T* vold;
+  T* pnew;
+  T beta, ws;
+  bool restart;
+  struct Raw {
+    T r, p, v;
+  };
+  __device__ __forceinline__ Raw fetch(long long idx) const {
+    Raw q;
+    q.r = __ldcg(r + idx);
+    if (restart) {
+      q.p = T(0);
+      q.v = T(0);
+    } else {
+      q.p = __ldcg(pold + idx);
+      q.v = __ldcg(vold + idx);
+    }
+    return q;
+  }
+  __device__ __forceinline__ T make(const Raw& q, long long idx, bool own) const {
+    T pv = restart ? q.r : fma(beta, fma(-ws, q.v, q.p), q.r);
+    if (own) pnew[idx] = pv;
+    return pv;
+  }
+};
+
+// v = A p / sigma; r' = r/||r|| stored on (re)start; partial v.r'.
+template <typename T, int OPK, int NDIM>
+struct BiVSink {
+  Coef<T> cf;
+  Geom g;
+  const T* r;
+  T* rs;
+  T* vnew;
+  T inv_rn;
+  bool restart;
+  double acc[1];
+  struct Raw {
+    OpRaw<T, OPK> o;
+    T q;   // r (restart) or r'
+  };
+  __device__ __forceinline__ Raw fetch(long long idx, int i, int j, int k) const {
+    return Raw{op_fetch<T, OPK, NDIM>(cf, g, idx, i, j, k), restart ? __ldcg(r + idx) : __ldcg(rs + idx)};
+  }
+  __device__ __forceinline__ void operator()(long long idx, const Nbr<T>& nb, const Raw& q, int, int, int) {
+    T vv = op_apply<T, OPK, NDIM>(cf, q.o, nb);
+    vnew[idx] = vv;
+    T rsv = q.q;
+    if (restart) {
+      rsv = q.q * inv_rn;
+      rs[idx] = rsv;
+    }
+    acc[0] += (double)vv * (double)rsv;
+  }
+};
+
+// s = r - alpha sigma v, stored for owned nodes.
+template <typename T>
+struct BiSSrc {
+  const T* r;
+  const T* v;
+  T* s;
+  T as;
+  struct Raw {
+    T r, v;
+  };
+  __device__ __forceinline__ Raw fetch(long long idx) const { return Raw{__ldcg(r + idx), __ldcg(v + idx)}; }
+  __device__ __forceinline__ T make(const Raw& q, long long idx, bool own) const {
+    T sv = fma(-as, q.v, q.r);
+    if (own) s[idx] = sv;
+    return sv;
+  }
+};
+
+// t = A s / sigma; partials s.s, t.s, t.t.
+template <typename T, int OPK, int NDIM>
+struct BiTSink {
+  Coef<T> cf;
+  Geom g;
+  T* t;
+  double acc[3];
+  using Raw = OpRaw<T, OPK>;
+  __device__ __forceinline__ Raw fetch(long long idx, int i, int j, int k) const {
+    return op_fetch<T, OPK, NDIM>(cf, g, idx, i, j, k);
+  }
+  __device__ __forceinline__ void operator()(long long idx, const Nbr<T>& nb, const Raw& o, int, int, int) {
+    T tv = op_apply<T, OPK, NDIM>(cf, o, nb);
+    t[idx] = tv;
+    const double sv = (double)nb.c, td = (double)tv;
+    acc[0] += sv * sv;
+    acc[1] += td * sv;
+    acc[2] += td * td;
+  }
+};
+
 template <typename T, int OPK, int NDIM>
 __global__ void __launch_bounds__(512) k_bicgstab(BiArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -404,23 +605,15 @@ __global__ void __launch_bounds__(512) k_bicgstab(BiArgs<T> a) {
   const long long N = a.g.N;
   const T sig = (T)a.sigma;
 
-  double acc2[2] = {0.0, 0.0};
+  ResidualSink<T, OPK, NDIM> rsink{a.cf, a.g, sig, a.b, a.r, {0.0, 0.0}};
   {
-    auto src = [&](long long idx, bool) -> T { return ldcg(a.x + idx); };
-    auto sink = [&](long long idx, const Nbr<T>& nb, int i, int j, int k) {
-      T v = apply_op<T, OPK, NDIM>(a.cf, a.g, idx, i, j, k, nb);
-      T bv = __ldg(a.b + idx);
-      T rv = (OPK == OP_VARK) ? bv - v : fma(-sig, v, bv);
-      a.r[idx] = rv;
-      acc2[0] += (double)rv * (double)rv;
-      acc2[1] += (double)bv * (double)bv;
-    };
+    LoadSrc<T, true> src{a.x};
     for (int item = blockIdx.x; item < a.tl.items(); item += gridDim.x)
-      zmarch_item<T, NDIM>(a.g, a.tl, item, sm, src, sink);
+      zmarch_item<T, NDIM>(a.g, a.tl, item, sm, src, rsink);
   }
-  block_sum<2>(acc2, sh);
+  block_sum<2>(rsink.acc, sh);
   double s2[2];
-  if (!grid_reduce<2>(a.cm.ctrl, a.cm.partials, acc2, s2, sh)) return;
+  if (!grid_reduce<2>(a.cm.ctrl, a.cm.partials, rsink.acc, s2, sh)) return;
   double brr = s2[0];
   const double bb = s2[1];
   if (bb == 0.0) {
@@ -441,6 +634,7 @@ __global__ void __launch_bounds__(512) k_bicgstab(BiArgs<T> a) {
   bool restart = true;          // p = r and r' = r/||r|| in the next pass 1
   double beta = 0.0, omega = 0.0;
   int it = 0, status = DS_MAXIT, restarts = 0;
+  const long long st = gstride();
   while (it < a.maxit) {
     it++;
     const T* pold = (it & 1) ? a.p0 : a.p1;
@@ -448,33 +642,15 @@ __global__ void __launch_bounds__(512) k_bicgstab(BiArgs<T> a) {
     const T* vold = (it & 1) ? a.v0 : a.v1;
     T* vnew = (it & 1) ? a.v1 : a.v0;
     // ---- pass 1
-    const T tb = (T)beta, tws = (T)(omega * a.sigma), tinv = (T)inv_rn;
-    double acc1[1] = {0.0};
+    double ad[1];
     {
-      auto src = [&](long long idx, bool own) -> T {
-        T rv = ldcg(a.r + idx);
-        T pv = restart ? rv : fma(tb, fma(-tws, ldcg(vold + idx), ldcg(pold + idx)), rv);
-        if (own) pnew[idx] = pv;
-        return pv;
-      };
-      auto sink = [&](long long idx, const Nbr<T>& nb, int i, int j, int k) {
-        T vv = apply_op<T, OPK, NDIM>(a.cf, a.g, idx, i, j, k, nb);
-        vnew[idx] = vv;
-        T rsv;
-        if (restart) {
-          rsv = ldcg(a.r + idx) * tinv;
-          a.rs[idx] = rsv;
-        } else {
-          rsv = ldcg(a.rs + idx);
-        }
-        acc1[0] += (double)vv * (double)rsv;
-      };
+      BiPSrc<T> src{a.r, pold, vold, pnew, (T)beta, (T)(omega * a.sigma), restart};
+      BiVSink<T, OPK, NDIM> sink{a.cf, a.g, a.r, a.rs, vnew, (T)inv_rn, restart, {0.0}};
       for (int item = blockIdx.x; item < a.tl.items(); item += gridDim.x)
         zmarch_item<T, NDIM>(a.g, a.tl, item, sm, src, sink);
+      block_sum<1>(sink.acc, sh);
+      if (!grid_reduce<1>(a.cm.ctrl, a.cm.partials, sink.acc, ad, sh)) return;
     }
-    block_sum<1>(acc1, sh);
-    double ad[1];
-    if (!grid_reduce<1>(a.cm.ctrl, a.cm.partials, acc1, ad, sh)) return;
     const double alpha_d = a.sigma * ad[0];
     if (alpha_d == 0.0 || !finite_d(alpha_d)) {
       status = finite_d(alpha_d) ? DS_BREAKDOWN : DS_NONFINITE;
@@ -482,38 +658,25 @@ __global__ void __launch_bounds__(512) k_bicgstab(BiArgs<T> a) {
     }
     const double alpha = alpha_n / alpha_d;
     // ---- pass 2
-    const T tas = (T)(alpha * a.sigma);
-    double acc3[3] = {0.0, 0.0, 0.0};
+    double st3[3];
     {
-      auto src = [&](long long idx, bool own) -> T {
-        T sv = fma(-tas, ldcg(vnew + idx), ldcg(a.r + idx));
-        if (own) a.s[idx] = sv;
-        return sv;
-      };
-      auto sink = [&](long long idx, const Nbr<T>& nb, int i, int j, int k) {
-        T tv = apply_op<T, OPK, NDIM>(a.cf, a.g, idx, i, j, k, nb);
-        a.t[idx] = tv;
-        const double sv = (double)nb.c, td = (double)tv;
-        acc3[0] += sv * sv;
-        acc3[1] += td * sv;
-        acc3[2] += td * td;
-      };
+      BiSSrc<T> src{a.r, vnew, a.s, (T)(alpha * a.sigma)};
+      BiTSink<T, OPK, NDIM> sink{a.cf, a.g, a.t, {0.0, 0.0, 0.0}};
       for (int item = blockIdx.x; item < a.tl.items(); item += gridDim.x)
         zmarch_item<T, NDIM>(a.g, a.tl, item, sm, src, sink);
+      block_sum<3>(sink.acc, sh);
+      if (!grid_reduce<3>(a.cm.ctrl, a.cm.partials, sink.acc, st3, sh)) return;
     }
-    block_sum<3>(acc3, sh);
-    double st[3];
-    if (!grid_reduce<3>(a.cm.ctrl, a.cm.partials, acc3, st, sh)) return;
-    const double srel = sqrt(st[0] / bb);
+    const double srel = sqrt(st3[0] / bb);
     if (srel <= a.tol) {
       const T ta = (T)alpha;
-      for (long long i = gtid(); i < N; i += gstride()) a.x[i] = fma(ta, ldcg(pnew + i), ldcg(a.x + i));
+      for (long long i = gtid(); i < N; i += st) a.x[i] = fma(ta, ldcg(pnew + i), ldcg(a.x + i));
       if (blockIdx.x == 0 && threadIdx.x == 0) a.cm.hist[it] = srel;
       rel = srel;
       status = DS_CONVERGED;
       break;
     }
-    const double ts = a.sigma * st[1], tt = a.sigma * a.sigma * st[2];
+    const double ts = a.sigma * st3[1], tt = a.sigma * a.sigma * st3[2];
     if (tt == 0.0 || !finite_d(tt) || !finite_d(ts)) {
       status = finite_d(tt) && finite_d(ts) ? DS_BREAKDOWN : DS_NONFINITE;
       break;
@@ -526,21 +689,44 @@ __global__ void __launch_bounds__(512) k_bicgstab(BiArgs<T> a) {
     // ---- pass 3
     const T ta = (T)alpha, tom = (T)omega, toms = (T)(omega * a.sigma);
     double acc4[2] = {0.0, 0.0};
-    for (long long i = gtid(); i < N; i += gstride()) {
+    long long i = gtid();
+    for (; i + (ILP - 1) * st < N; i += ILP * st) {
+      T sv[ILP], pv[ILP], xv[ILP], tv[ILP], rsv[ILP];
+#pragma unroll
+      for (int u = 0; u < ILP; u++) {
+        const long long q = i + u * st;
+        sv[u] = ldcg(a.s + q);
+        pv[u] = ldcg(pnew + q);
+        xv[u] = ldcg(a.x + q);
+        tv[u] = ldcg(a.t + q);
+        rsv[u] = ldcg(a.rs + q);
+      }
+#pragma unroll
+      for (int u = 0; u < ILP; u++) {
+        const long long q = i + u * st;
+        T xn = fma(tom, sv[u], fma(ta, pv[u], xv[u]));
+        T rn = fma(-toms, tv[u], sv[u]);
+        a.x[q] = xn;
+        a.r[q] = rn;
+        acc4[0] += (double)rn * (double)rsv[u];
+        acc4[1] += (double)rn * (double)rn;
+      }
+    }
+    for (; i < N; i += st) {
       T sv = ldcg(a.s + i);
-      T xv = fma(tom, sv, fma(ta, ldcg(pnew + i), ldcg(a.x + i)));
-      T rv = fma(-toms, ldcg(a.t + i), sv);
-      a.x[i] = xv;
-      a.r[i] = rv;
-      acc4[0] += (double)rv * (double)ldcg(a.rs + i);
-      acc4[1] += (double)rv * (double)rv;
+      T xn = fma(tom, sv, fma(ta, ldcg(pnew + i), ldcg(a.x + i)));
+      T rn = fma(-toms, ldcg(a.t + i), sv);
+      a.x[i] = xn;
+      a.r[i] = rn;
+      acc4[0] += (double)rn * (double)ldcg(a.rs + i);
+      acc4[1] += (double)rn * (double)rn;
     }
     block_sum<2>(acc4, sh);
-    double rn[2];
-    if (!grid_reduce<2>(a.cm.ctrl, a.cm.partials, acc4, rn, sh)) return;
-    rel = sqrt(rn[1] / bb);
+    double rn2[2];
+    if (!grid_reduce<2>(a.cm.ctrl, a.cm.partials, acc4, rn2, sh)) return;
+    rel = sqrt(rn2[1] / bb);
     if (blockIdx.x == 0 && threadIdx.x == 0) a.cm.hist[it] = rel;
-    if (!finite_d(rel) || !finite_d(rn[0])) {
+    if (!finite_d(rel) || !finite_d(rn2[0])) {
       status = DS_NONFINITE;
       break;
     }
@@ -548,15 +734,15 @@ __global__ void __launch_bounds__(512) k_bicgstab(BiArgs<T> a) {
       status = DS_CONVERGED;
       break;
     }
-    if (a.reps > 0.0 && sqrt(fabs(rn[0])) < a.reps) {
+    if (a.reps > 0.0 && sqrt(fabs(rn2[0])) < a.reps) {
       restart = true;
-      alpha_n = sqrt(rn[1]);
-      inv_rn = 1.0 / sqrt(rn[1]);
+      alpha_n = sqrt(rn2[1]);
+      inv_rn = 1.0 / sqrt(rn2[1]);
       restarts++;
     } else {
       restart = false;
-      beta = rn[0] / (alpha_d * omega);
-      alpha_n = rn[0];
+      beta = rn2[0] / (alpha_d * omega);
+      alpha_n = rn2[0];
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) a.cm.ctrl->restarts = restarts;
@@ -774,13 +960,14 @@ static Coef<T> op_coef(const hs_op* A, const void* D, const void* ax, const void
 // Variable-coefficient SpMV without a workspace: face couplings are formed
 // on the fly from k (harmonic means), y_i = sum_f kappa_f (x_i - x_j) / h^2.
 template <typename T, typename K, int NDIM>
-__global__ void __launch_bounds__(512) k_spmv_vark_direct(Geom g, Tiling tl, const K* __restrict__ kk, double ihx,
-                                                          double ihy, double ihz, const T* __restrict__ x,
-                                                          T* __restrict__ y) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  T* sm = reinterpret_cast<T*>(smraw);
-  auto src = [&](long long idx, bool) -> T { return __ldg(x + idx); };
-  auto sink = [&](long long idx, const Nbr<T>& nb, int i, int j, int k) {
+struct VarkDirectSink {
+  Geom g;
+  const K* kk;
+  double ihx, ihy, ihz;
+  T* y;
+  struct Raw {};
+  __device__ __forceinline__ Raw fetch(long long, int, int, int) const { return Raw{}; }
+  __device__ __forceinline__ void operator()(long long idx, const Nbr<T>& nb, const Raw&, int i, int j, int k) {
     const double kc = (double)__ldg(kk + idx), xc = (double)nb.c;
     double acc = 0.0;
     double kap;
@@ -801,7 +988,17 @@ __global__ void __launch_bounds__(512) k_spmv_vark_direct(Geom g, Tiling tl, con
       acc += kap * ihz * (xc - (double)nb.t);
     }
     y[idx] = (T)acc;
-  };
+  }
+};
+
+template <typename T, typename K, int NDIM>
+__global__ void __launch_bounds__(512) k_spmv_vark_direct(Geom g, Tiling tl, const K* __restrict__ kk, double ihx,
+                                                          double ihy, double ihz, const T* __restrict__ x,
+                                                          T* __restrict__ y) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sm = reinterpret_cast<T*>(smraw);
+  LoadSrc<T, false> src{x};
+  VarkDirectSink<T, K, NDIM> sink{g, kk, ihx, ihy, ihz, y};
   for (int item = blockIdx.x; item < tl.items(); item += gridDim.x) zmarch_item<T, NDIM>(g, tl, item, sm, src, sink);
 }
 

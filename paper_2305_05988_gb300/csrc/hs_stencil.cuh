@@ -47,49 +47,34 @@ __device__ __forceinline__ T& slab(T* sm, int by, int buf, int row, int col) {
   return sm[(buf * (by + 2) + row) * (BX + 2) + col];
 }
 
-// Fill the halo of plane kk into slab buffer `buf` (warps 0..2 only).
-template <typename T, class Src>
-__device__ __forceinline__ void fill_halo(const Geom& g, int by, T* sm, int buf, int i0, int j0, int kk,
-                                          Src& src) {
-  const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
-  const long long pk = (long long)kk * g.plane;
-  if (ly == 0) {
-    int i = i0 + lx, j = j0 - 1;
-    T v = T(0);
-    if (j >= 0 && i < g.nx) v = src(pk + (long long)j * g.nx + i, false);
-    slab(sm, by, buf, 0, lx + 1) = v;
-  } else if (ly == 1) {
-    int i = i0 + lx, j = j0 + by;
-    T v = T(0);
-    if (j < g.ny && i < g.nx) v = src(pk + (long long)j * g.nx + i, false);
-    slab(sm, by, buf, by + 1, lx + 1) = v;
-  } else if (ly == 2) {
-    if (lx < by) {
-      int i = i0 - 1, j = j0 + lx;
-      T v = T(0);
-      if (i >= 0 && j < g.ny) v = src(pk + (long long)j * g.nx + i, false);
-      slab(sm, by, buf, lx + 1, 0) = v;
-    } else if (lx >= 16 && lx < 16 + by) {
-      int i = i0 + BX, j = j0 + lx - 16;
-      T v = T(0);
-      if (i < g.nx && j < g.ny) v = src(pk + (long long)j * g.nx + i, false);
-      slab(sm, by, buf, lx - 16 + 1, BX + 1) = v;
-    }
-  }
-}
-
 // Neighbour values of the current node handed to the stencil functor.
 template <typename T>
 struct Nbr {
   T c, w, e, s, n, b, t;
 };
 
-// Process one work item.  `src(idx, own)` returns the stencil input at a
-// node (own = the node belongs to this item, so side outputs may be stored);
-// `sink(idx, nb, i, j, k)` consumes the neighbourhood of each owned node.
+// Process one work item, software-pipelined along z.
+//
+// The input functor `src` has two phases: src.fetch(idx) issues the loads
+// of a node (returning a plain struct of raw values) and src.make(raw, idx,
+// own) turns them into the stencil input (own = the node belongs to this
+// item, so side outputs such as p may be stored).  The consumer `sink` has
+// the same split: sink.fetch(idx, i, j, k) loads per-node operands (b, r',
+// variable coefficients) and sink(idx, nb, raw, i, j, k) consumes the
+// neighbourhood.  At plane step k the block issues the src loads of plane
+// k+2 and the sink loads of plane k+1, then builds plane k+1 from loads
+// issued one step earlier, then applies the stencil at plane k: global-memory
+// latency is hidden behind a whole plane of work instead of sitting in front
+// of the barrier.
+//
+// Halo points are produced by whole warps: warp 0 the row below the tile,
+// warp 1 the row above, warp 2 the two side columns (lanes 0..by-1 left,
+// 16..16+by-1 right).  Requires 3 <= by <= 16.
 template <typename T, int NDIM, class Src, class Sink>
-__device__ __forceinline__ void zmarch_item(const Geom& g, const Tiling& tl, int item, T* sm, Src& src,
+__device__ __forceinline__ void zmarch_item(const Geom& g, const Tiling& tl, int item, T* sm, const Src& src,
                                             Sink& sink) {
+  using SR = typename Src::Raw;
+  using KR = typename Sink::Raw;
   int i0, j0, z0, z1;
   decode_item(tl, g, item, i0, j0, z0, z1);
   const int by = tl.by;
@@ -97,24 +82,62 @@ __device__ __forceinline__ void zmarch_item(const Geom& g, const Tiling& tl, int
   const int i = i0 + lx, j = j0 + ly;
   const bool inside = (i < g.nx) && (j < g.ny);
   const long long col = (long long)j * g.nx + i;
+  const long long P = g.plane;
+
+  // the halo node this thread produces (warps 0..2 only)
+  int hrow = -1, hcp = 0, hi = 0, hj = 0;
+  if (ly == 0) {
+    hi = i0 + lx; hj = j0 - 1; hrow = 0; hcp = lx + 1;
+  } else if (ly == 1) {
+    hi = i0 + lx; hj = j0 + by; hrow = by + 1; hcp = lx + 1;
+  } else if (ly == 2) {
+    if (lx < by) {
+      hi = i0 - 1; hj = j0 + lx; hrow = lx + 1; hcp = 0;
+    } else if (lx >= 16 && lx < 16 + by) {
+      hi = i0 + BX; hj = j0 + lx - 16; hrow = lx - 15; hcp = BX + 1;
+    }
+  }
+  const bool hany = hrow >= 0;
+  const bool hin = hany && hi >= 0 && hi < g.nx && hj >= 0 && hj < g.ny;
+  const long long hcol = hin ? (long long)hj * g.nx + hi : 0;
 
   T vb = T(0), vc = T(0), vt = T(0);
-  if (NDIM == 3 && inside && z0 > 0) vb = src(col + (long long)(z0 - 1) * g.plane, false);
-  if (inside) vc = src(col + (long long)z0 * g.plane, true);
-  slab(sm, by, 0, ly + 1, lx + 1) = vc;
-  fill_halo<T>(g, by, sm, 0, i0, j0, z0, src);
+  SR rown{}, rhal{};   // raw src values of plane k+1
+  KR kown{};           // raw sink values of plane k
+  {
+    if (NDIM == 3 && inside && z0 > 0) {
+      SR rb = src.fetch(col + (long long)(z0 - 1) * P);
+      vb = src.make(rb, col + (long long)(z0 - 1) * P, false);
+    }
+    SR r0{}, h0{};
+    if (inside) r0 = src.fetch(col + (long long)z0 * P);
+    if (hin) h0 = src.fetch(hcol + (long long)z0 * P);
+    if (inside) kown = sink.fetch(col + (long long)z0 * P, i, j, z0);
+    if (NDIM == 3 && z0 + 1 < g.nz) {
+      if (inside) rown = src.fetch(col + (long long)(z0 + 1) * P);
+      if (hin && z0 + 1 < z1) rhal = src.fetch(hcol + (long long)(z0 + 1) * P);
+    }
+    vc = inside ? src.make(r0, col + (long long)z0 * P, true) : T(0);
+    slab(sm, by, 0, ly + 1, lx + 1) = vc;
+    if (hany) slab(sm, by, 0, hrow, hcp) = hin ? src.make(h0, hcol + (long long)z0 * P, false) : T(0);
+  }
   __syncthreads();
 
   for (int k = z0; k < z1; k++) {
     const int buf = (k - z0) & 1;
+    SR rown2{}, rhal2{};
+    KR kown2{};
     if (NDIM == 3) {
+      if (inside && k + 2 < g.nz && k + 2 <= z1) rown2 = src.fetch(col + (long long)(k + 2) * P);
+      if (hin && k + 2 < z1) rhal2 = src.fetch(hcol + (long long)(k + 2) * P);
+      if (inside && k + 1 < z1) kown2 = sink.fetch(col + (long long)(k + 1) * P, i, j, k + 1);
       vt = T(0);
       if (k + 1 < g.nz) {
         const bool own_next = (k + 1 < z1);
-        if (inside) vt = src(col + (long long)(k + 1) * g.plane, own_next);
+        if (inside) vt = src.make(rown, col + (long long)(k + 1) * P, own_next);
         if (own_next) {
           slab(sm, by, buf ^ 1, ly + 1, lx + 1) = vt;
-          fill_halo<T>(g, by, sm, buf ^ 1, i0, j0, k + 1, src);
+          if (hany) slab(sm, by, buf ^ 1, hrow, hcp) = hin ? src.make(rhal, hcol + (long long)(k + 1) * P, false) : T(0);
         }
       }
     }
@@ -127,30 +150,73 @@ __device__ __forceinline__ void zmarch_item(const Geom& g, const Tiling& tl, int
       nb.n = slab(sm, by, buf, ly + 2, lx + 1);
       nb.b = vb;
       nb.t = vt;
-      sink(col + (long long)k * g.plane, nb, i, j, k);
+      sink(col + (long long)k * P, nb, kown, i, j, k);
     }
     __syncthreads();
     vb = vc;
     vc = vt;
+    rown = rown2;
+    rhal = rhal2;
+    kown = kown2;
   }
 }
+
+// Plain load of one vector as the stencil input.  CG = true reads through
+// L2 only (data written earlier in the same persistent kernel).
+template <typename T, bool CG>
+struct LoadSrc {
+  const T* x;
+  struct Raw {
+    T v;
+  };
+  __device__ __forceinline__ Raw fetch(long long idx) const { return Raw{CG ? __ldcg(x + idx) : __ldg(x + idx)}; }
+  __device__ __forceinline__ T make(const Raw& r, long long, bool) const { return r.v; }
+};
 
 // ---------------------------------------------------------------------------
 // Stencil arithmetic.  Counts below are FP64-pipe instructions per node, the
 // binding resource for FP64 on this GPU (2 lanes / clock / SM).
 // ---------------------------------------------------------------------------
 
-// Scaled operator, constant coefficients: returns (A x)_i / sigma where the
-// host scaled all coefficients by 1/sigma so that the upper x coupling is
-// exactly -1.  6 instructions in 3-D (4 in 2-D).
+// Per-node operator operands, prefetched one plane ahead.  Constant
+// coefficients need none; variable coefficients carry the diagonal (or its
+// inverse for the Jacobi form) and the six positive face couplings.
+template <typename T, int OPK>
+struct OpRaw {};
+template <typename T>
+struct OpRaw<T, OP_VARK> {
+  T d, xl, xu, yl, yu, zl, zu;
+};
+
 template <typename T, int OPK, int NDIM>
-__device__ __forceinline__ T apply_unit(const Coef<T>& cf, const Nbr<T>& nb) {
-  if (OPK == OP_SYM) {
+__device__ __forceinline__ OpRaw<T, OPK> op_fetch(const Coef<T>& cf, const Geom& g, long long idx, int i, int j,
+                                                  int k) {
+  OpRaw<T, OPK> r{};
+  if constexpr (OPK == OP_VARK) {
+    r.d = __ldg(cf.D + idx);
+    r.xl = __ldg(cf.ax + idx);
+    r.xu = (i + 1 < g.nx) ? __ldg(cf.ax + idx + 1) : T(0);
+    r.yl = __ldg(cf.ay + idx);
+    r.yu = (j + 1 < g.ny) ? __ldg(cf.ay + idx + g.nx) : T(0);
+    if (NDIM == 3) {
+      r.zl = __ldg(cf.az + idx);
+      r.zu = (k + 1 < g.nz) ? __ldg(cf.az + idx + g.plane) : T(0);
+    }
+  }
+  return r;
+}
+
+// (A x)_i / sigma.  Constant coefficients: the host scaled every coupling by
+// 1/sigma so that the upper x coupling is exactly -1 (6 FP64 instructions in
+// 3-D, 4 in 2-D).  Variable coefficients (sigma = 1): 7 instructions.
+template <typename T, int OPK, int NDIM>
+__device__ __forceinline__ T op_apply(const Coef<T>& cf, const OpRaw<T, OPK>& o, const Nbr<T>& nb) {
+  if constexpr (OPK == OP_SYM) {
     T y = fma(cf.d, nb.c, -(nb.w + nb.e));
     y = fma(cf.yl, nb.s + nb.n, y);
     if (NDIM == 3) y = fma(cf.zl, nb.b + nb.t, y);
     return y;
-  } else {
+  } else if constexpr (OPK == OP_NONSYM) {
     T y = fma(cf.d, nb.c, -nb.e);
     y = fma(cf.xl, nb.w, y);
     y = fma(cf.yl, nb.s, y);
@@ -160,48 +226,32 @@ __device__ __forceinline__ T apply_unit(const Coef<T>& cf, const Nbr<T>& nb) {
       y = fma(cf.zu, nb.t, y);
     }
     return y;
+  } else {
+    T y = o.d * nb.c;
+    y = fma(-o.xl, nb.w, y);
+    y = fma(-o.xu, nb.e, y);
+    y = fma(-o.yl, nb.s, y);
+    y = fma(-o.yu, nb.n, y);
+    if (NDIM == 3) {
+      y = fma(-o.zl, nb.b, y);
+      y = fma(-o.zu, nb.t, y);
+    }
+    return y;
   }
 }
 
-// Variable-coefficient operator (sigma = 1): 7 instructions in 3-D.
-template <typename T, int NDIM>
-__device__ __forceinline__ T apply_vark(const Coef<T>& cf, const Geom& g, long long idx, int i, int j, int k,
-                                        const Nbr<T>& nb) {
-  T axu = (i + 1 < g.nx) ? __ldg(cf.ax + idx + 1) : T(0);
-  T ayu = (j + 1 < g.ny) ? __ldg(cf.ay + idx + g.nx) : T(0);
-  T y = __ldg(cf.D + idx) * nb.c;
-  y = fma(-__ldg(cf.ax + idx), nb.w, y);
-  y = fma(-axu, nb.e, y);
-  y = fma(-__ldg(cf.ay + idx), nb.s, y);
-  y = fma(-ayu, nb.n, y);
-  if (NDIM == 3) {
-    T azu = (k + 1 < g.nz) ? __ldg(cf.az + idx + g.plane) : T(0);
-    y = fma(-__ldg(cf.az + idx), nb.b, y);
-    y = fma(-azu, nb.t, y);
-  }
-  return y;
-}
-
+// Jacobi update x' = (b - sum_{j!=i} a_ij x_j) / a_ii.  Constant
+// coefficients: the host passes g = -a/a_ii in the Coef slots and bv = b/a_ii
+// (6 instructions in 3-D).  Variable coefficients: x' = (b + sum a x) * invD
+// with o.d = 1/a_ii (7 instructions).
 template <typename T, int OPK, int NDIM>
-__device__ __forceinline__ T apply_op(const Coef<T>& cf, const Geom& g, long long idx, int i, int j, int k,
-                                      const Nbr<T>& nb) {
-  if (OPK == OP_VARK) return apply_vark<T, NDIM>(cf, g, idx, i, j, k, nb);
-  return apply_unit<T, OPK, NDIM>(cf, nb);
-}
-
-// Jacobi update x' = (b - sum_{j!=i} a_ij x_j) / a_ii.  For constant
-// coefficients the host passes g = -a/a_ii in the Coef slots and bD = b/a_ii
-// (6 instructions in 3-D); for variable k, x' = (b + sum a x) * invD
-// (7 instructions).  `bv` is bD (constant) or b (variable).
-template <typename T, int OPK, int NDIM>
-__device__ __forceinline__ T jacobi_update(const Coef<T>& cf, const Geom& g, long long idx, int i, int j, int k,
-                                           const Nbr<T>& nb, T bv) {
-  if (OPK == OP_SYM) {
+__device__ __forceinline__ T jacobi_apply(const Coef<T>& cf, const OpRaw<T, OPK>& o, const Nbr<T>& nb, T bv) {
+  if constexpr (OPK == OP_SYM) {
     T y = fma(cf.xl, nb.w + nb.e, bv);
     y = fma(cf.yl, nb.s + nb.n, y);
     if (NDIM == 3) y = fma(cf.zl, nb.b + nb.t, y);
     return y;
-  } else if (OPK == OP_NONSYM) {
+  } else if constexpr (OPK == OP_NONSYM) {
     T y = fma(cf.xl, nb.w, bv);
     y = fma(cf.xu, nb.e, y);
     y = fma(cf.yl, nb.s, y);
@@ -212,18 +262,15 @@ __device__ __forceinline__ T jacobi_update(const Coef<T>& cf, const Geom& g, lon
     }
     return y;
   } else {
-    T axu = (i + 1 < g.nx) ? __ldg(cf.ax + idx + 1) : T(0);
-    T ayu = (j + 1 < g.ny) ? __ldg(cf.ay + idx + g.nx) : T(0);
-    T y = fma(__ldg(cf.ax + idx), nb.w, bv);
-    y = fma(axu, nb.e, y);
-    y = fma(__ldg(cf.ay + idx), nb.s, y);
-    y = fma(ayu, nb.n, y);
+    T y = fma(o.xl, nb.w, bv);
+    y = fma(o.xu, nb.e, y);
+    y = fma(o.yl, nb.s, y);
+    y = fma(o.yu, nb.n, y);
     if (NDIM == 3) {
-      T azu = (k + 1 < g.nz) ? __ldg(cf.az + idx + g.plane) : T(0);
-      y = fma(__ldg(cf.az + idx), nb.b, y);
-      y = fma(azu, nb.t, y);
+      y = fma(o.zl, nb.b, y);
+      y = fma(o.zu, nb.t, y);
     }
-    return y * __ldg(cf.D + idx);  // D holds 1/a_ii for the Jacobi setup
+    return y * o.d;
   }
 }
 
