@@ -181,6 +181,32 @@ hs_status hs_bicgstab(const hs_op *A, hs_dtype dtype, const void *b, void *x, do
                       int maxit, const hs_opts *opts, void *ws, size_t ws_bytes, void *stream,
                       hs_result *res, double *hist);
 
+/* ---- conjugate gradient without any allocation --------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory themselves -- for example a plug-in
+ * inside a host application that hands out all GPU memory through its own
+ * pool and forbids foreign cudaMalloc calls, or a latency-critical path that
+ * must not enter an allocator.  hs_cg_static runs exactly the solver of
+ * hs_cg, but its workspace is a fixed array of HS_STATIC_SCRATCH_BYTES bytes
+ * inside the library's device image (held by every GPU that loads the
+ * library until the process exits), so the call allocates nothing; the
+ * caller still owns b and x.
+ *   - Problems whose CG workspace (hs_workspace_size with HS_SOLVER_CG, the
+ *     same dtype and maxit) exceeds HS_STATIC_SCRATCH_BYTES are rejected with
+ *     HS_ERR_INVALID and a message naming both sizes.  With FP64 and a
+ *     constant-coefficient operator that is about 500 k unknowns.
+ *   - The first call on a device, with that device current, looks up the
+ *     array's device address (cudaGetSymbolAddress) and keeps it: make that
+ *     first call before any stream capture on that device.
+ *   - All calls on a device share the one array and it keeps the previous
+ *     call's contents; the solver initialises what it reads first.  Calls that
+ *     may overlap on the GPU (other streams, other host threads) race on the
+ *     array and must be serialised by the caller.
+ * Arguments and results are those of hs_cg. */
+#define HS_STATIC_SCRATCH_BYTES (16u << 20)
+hs_status hs_cg_static(const hs_op *A, hs_dtype dtype, const void *b, void *x, double tol, int maxit,
+                       const hs_opts *opts, void *stream, hs_result *res, double *hist);
+
 /* Thread-local message describing the last non-OK status (never NULL). */
 const char *hs_last_error(void);
 
