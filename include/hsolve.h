@@ -62,7 +62,8 @@ typedef enum {
     HS_SOLVER_JACOBI = 0,
     HS_SOLVER_GAUSS_SEIDEL = 1,
     HS_SOLVER_CG = 2,
-    HS_SOLVER_BICGSTAB = 3
+    HS_SOLVER_BICGSTAB = 3,
+    HS_SOLVER_MIXED = 4      /* hs_solve_mixed (dtype HS_F64) */
 } hs_solver;
 
 typedef enum { HS_GS_FORWARD = 0, HS_GS_BACKWARD = 1, HS_GS_SYMMETRIC = 2 } hs_gs_mode;
@@ -87,7 +88,6 @@ typedef struct {
                                returned x into hs_result.true_rel_res           */
     double timeout_s;       /* bound on any single device-side wait, seconds
                                (default 2.0)                                     */
-    int max_outer;          /* mixed precision: maximum refinement steps (20)   */
     double inner_tol;       /* mixed precision: inner relative tolerance (1e-5) */
     int inner_solver;       /* mixed precision: HS_SOLVER_CG or _BICGSTAB (CG)  */
     int inner_maxit;        /* mixed precision: inner iteration cap (10000)     */
@@ -180,6 +180,23 @@ hs_status hs_cg(const hs_op *A, hs_dtype dtype, const void *b, void *x, double t
 hs_status hs_bicgstab(const hs_op *A, hs_dtype dtype, const void *b, void *x, double tol,
                       int maxit, const hs_opts *opts, void *ws, size_t ws_bytes, void *stream,
                       hs_result *res, double *hist);
+
+/* Mixed-precision iterative refinement.  Not in the paper (which is FP64
+ * throughout); it gets the FP64 answer of A x = b at FP32 cost on a GPU whose
+ * FP32 pipe is 64x its FP64 pipe.  Each refinement step computes the FP64
+ * residual r = b - A x and its relative norm on the GPU (stop when <= tol),
+ * solves A d = r/||r|| with CG (opts.inner_solver = HS_SOLVER_CG, symmetric
+ * operators) or BiCGStab on FP32 vectors and FP32 coefficients with dot
+ * products accumulated in FP64, to the relative tolerance opts.inner_tol
+ * (default 1e-5) or opts.inner_maxit iterations, and updates x += ||r|| d in
+ * FP64.  b, x: FP64 device vectors.  maxit bounds the refinement steps.
+ * res.iters = res.outer = refinement steps, res.inner_iters = their total
+ * inner iterations, res.rel_res = res.true_rel_res = FP64 relative residual
+ * of the returned x; hist[k] = that residual after k steps (maxit + 1 doubles).
+ * Workspace: hs_workspace_size(A, HS_SOLVER_MIXED, HS_F64, opts, maxit, &n). */
+hs_status hs_solve_mixed(const hs_op *A, const double *b, double *x, double tol, int maxit,
+                         const hs_opts *opts, void *ws, size_t ws_bytes, void *stream,
+                         hs_result *res, double *hist);
 
 /* ---- conjugate gradient without any allocation --------------------------
  * The paper has no counterpart to this entry point; it exists for callers

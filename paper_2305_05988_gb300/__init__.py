@@ -5,6 +5,7 @@ Public API: :class:`Operator` (Laplacian / upwind / diffusion stencils),
 numerical work runs in libhsolve (hand-written CUDA behind a C ABI,
 ``include/hsolve.h``); this package only marshals arguments.
 """
-from .solvers import Operator, SolveInfo, bicgstab, cg, gauss_seidel, jacobi, make_opts  # noqa: F401
+from .solvers import (Operator, SolveInfo, bicgstab, cg, gauss_seidel, jacobi, make_opts,  # noqa: F401
+                      solve_mixed)
 
-__all__ = ["Operator", "SolveInfo", "jacobi", "gauss_seidel", "cg", "bicgstab", "make_opts"]
+__all__ = ["Operator", "SolveInfo", "jacobi", "gauss_seidel", "cg", "bicgstab", "solve_mixed", "make_opts"]

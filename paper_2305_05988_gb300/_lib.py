@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", -1: "ERR_INVALID", -2: "ERR_CUDA", 
                 -4: "ERR_NONFINITE", -5: "ERR_TIMEOUT", -6: "ERR_WORKSPACE"}
 
 HS_F64, HS_F32 = 0, 1
-HS_SOLVER_JACOBI, HS_SOLVER_GAUSS_SEIDEL, HS_SOLVER_CG, HS_SOLVER_BICGSTAB = 0, 1, 2, 3
+HS_SOLVER_JACOBI, HS_SOLVER_GAUSS_SEIDEL, HS_SOLVER_CG, HS_SOLVER_BICGSTAB, HS_SOLVER_MIXED = 0, 1, 2, 3, 4
 HS_GS_FORWARD, HS_GS_BACKWARD, HS_GS_SYMMETRIC = 0, 1, 2
 HS_STATIC_SCRATCH_BYTES = 16 << 20   # include/hsolve.h
 
@@ -37,7 +37,6 @@ class hs_opts(ctypes.Structure):
                 ("restart_eps", ctypes.c_double),
                 ("true_residual", ctypes.c_int),
                 ("timeout_s", ctypes.c_double),
-                ("max_outer", ctypes.c_int),
                 ("inner_tol", ctypes.c_double),
                 ("inner_solver", ctypes.c_int),
                 ("inner_maxit", ctypes.c_int)]
@@ -77,6 +76,8 @@ SIGNATURES = {
                    ctypes.POINTER(hs_result), ctypes.POINTER(_d)]),
     "hs_bicgstab": (_i, [_vp, _i, _vp, _vp, _d, _i, ctypes.POINTER(hs_opts), _vp, _sz, _vp,
                          ctypes.POINTER(hs_result), ctypes.POINTER(_d)]),
+    "hs_solve_mixed": (_i, [_vp, _vp, _vp, _d, _i, ctypes.POINTER(hs_opts), _vp, _sz, _vp,
+                            ctypes.POINTER(hs_result), ctypes.POINTER(_d)]),
     "hs_cg_static": (_i, [_vp, _i, _vp, _vp, _d, _i, ctypes.POINTER(hs_opts), _vp,
                           ctypes.POINTER(hs_result), ctypes.POINTER(_d)]),
     "hs_last_error": (ctypes.c_char_p, []),

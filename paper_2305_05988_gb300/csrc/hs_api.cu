@@ -43,6 +43,8 @@ Common carve_common(Carve& c, int maxit) {
 }
 
 size_t gs_ws_vectors(const hs_op* A, hs_dtype dt);  // hs_gs.cu
+size_t mixed_ws_bytes(const hs_op* A, const hs_opts& o, int max_outer);  // hs_kernels.cu
+hs_status run_mixed(const SolveArgs& sa, hs_result* res, double* hist);   // hs_kernels.cu
 
 size_t ws_bytes_for(const hs_op* A, hs_solver s, hs_dtype dt, int maxit) {
   size_t N = (size_t)(A->n[0] * A->n[1] * A->n[2]);
@@ -54,6 +56,7 @@ size_t ws_bytes_for(const hs_op* A, hs_solver s, hs_dtype dt, int maxit) {
     case HS_SOLVER_CG: nvec = 4; break;
     case HS_SOLVER_BICGSTAB: nvec = 8; break;
     case HS_SOLVER_GAUSS_SEIDEL: return common_bytes(maxit) + gs_ws_vectors(A, dt) + vark_coef_bytes(A, dt);
+    case HS_SOLVER_MIXED: return 0;  // sized by mixed_ws_bytes with the options
   }
   return common_bytes(maxit) + nvec * vec + vark_coef_bytes(A, dt);
 }
@@ -67,7 +70,6 @@ static hs_opts default_opts() {
   o.restart_eps = 1e-5;
   o.true_residual = 1;
   o.timeout_s = 2.0;
-  o.max_outer = 20;
   o.inner_tol = 1e-5;
   o.inner_solver = HS_SOLVER_CG;
   o.inner_maxit = 10000;
@@ -94,13 +96,30 @@ static bool merge_opts(const hs_opts* in, hs_opts* out) {
     return false;
   }
   if (!(out->timeout_s > 0.0) || out->timeout_s > 3600.0) out->timeout_s = 2.0;
+  if (!(out->inner_tol >= 0.0) || !isfinite(out->inner_tol)) {
+    set_error("hs_opts.inner_tol must be finite and >= 0");
+    return false;
+  }
+  if (out->inner_solver != HS_SOLVER_CG && out->inner_solver != HS_SOLVER_BICGSTAB) {
+    set_error("hs_opts.inner_solver must be HS_SOLVER_CG or HS_SOLVER_BICGSTAB");
+    return false;
+  }
+  if (out->inner_maxit < 1 || out->inner_maxit > 100000000) out->inner_maxit = 10000;
   return true;
 }
 
 static bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
+static hs_opts default_opts();
+static bool merge_opts(const hs_opts* in, hs_opts* out);
+
+static size_t ws_need(const hs_op* A, hs_solver s, hs_dtype dt, const hs_opts& o, int maxit) {
+  if (s == HS_SOLVER_MIXED) return mixed_ws_bytes(A, o, maxit);
+  return ws_bytes_for(A, s, dt, maxit);
+}
+
 static hs_status check_solve(const hs_op* A, hs_dtype dt, const void* b, const void* x, double tol, int maxit,
-                             const void* ws, size_t ws_bytes, hs_solver s) {
+                             const void* ws, size_t ws_bytes, hs_solver s, const hs_opts& o) {
   if (!A) { set_error("operator is NULL"); return HS_ERR_INVALID; }
   if (dt != HS_F64 && dt != HS_F32) { set_error("dtype must be HS_F64 or HS_F32"); return HS_ERR_INVALID; }
   if (!b || !x) { set_error("b and x must be device pointers"); return HS_ERR_INVALID; }
@@ -110,7 +129,7 @@ static hs_status check_solve(const hs_op* A, hs_dtype dt, const void* b, const v
   if (maxit < 0 || maxit > 100000000) { set_error("maxit out of range"); return HS_ERR_INVALID; }
   if (!ws) { set_error("workspace is NULL"); return HS_ERR_WORKSPACE; }
   if (!aligned(ws, 256)) { set_error("workspace must be 256-byte aligned"); return HS_ERR_WORKSPACE; }
-  size_t need = ws_bytes_for(A, s, dt, maxit);
+  size_t need = ws_need(A, s, dt, o, maxit);
   if (ws_bytes < need) {
     set_error("workspace too small: %zu bytes given, %zu needed", ws_bytes, need);
     return HS_ERR_WORKSPACE;
@@ -134,7 +153,9 @@ static hs_status solve_common(runner_t run, hs_solver which, const hs_op* A, hs_
   hs_result local;
   hs_result* r = res ? res : &local;
   fill_res(r);
-  hs_status s = check_solve(A, dt, b, x, tol, maxit, ws, ws_bytes, which);
+  hs_opts o;
+  if (!merge_opts(opts, &o)) return HS_ERR_INVALID;
+  hs_status s = check_solve(A, dt, b, x, tol, maxit, ws, ws_bytes, which, o);
   if (s != HS_OK) return s;
   SolveArgs a;
   a.A = A;
@@ -143,7 +164,7 @@ static hs_status solve_common(runner_t run, hs_solver which, const hs_op* A, hs_
   a.x = x;
   a.tol = tol;
   a.maxit = maxit;
-  if (!merge_opts(opts, &a.o)) return HS_ERR_INVALID;
+  a.o = o;
   a.ws = (char*)ws;
   a.ws_bytes = ws_bytes;
   a.stream = (cudaStream_t)stream;
@@ -245,13 +266,21 @@ hs_status hs_residual(const hs_op* A, hs_dtype dtype, const void* b, const void*
 
 hs_status hs_workspace_size(const hs_op* A, hs_solver solver, hs_dtype dtype, const hs_opts* opts, int maxit,
                             size_t* bytes) {
-  (void)opts;
   if (!A || !bytes) { set_error("NULL argument"); return HS_ERR_INVALID; }
   if (dtype != HS_F64 && dtype != HS_F32) { set_error("bad dtype"); return HS_ERR_INVALID; }
-  if (solver < HS_SOLVER_JACOBI || solver > HS_SOLVER_BICGSTAB) { set_error("bad solver"); return HS_ERR_INVALID; }
+  if (solver < HS_SOLVER_JACOBI || solver > HS_SOLVER_MIXED) { set_error("bad solver"); return HS_ERR_INVALID; }
+  if (solver == HS_SOLVER_MIXED && dtype != HS_F64) { set_error("mixed precision takes FP64 b and x"); return HS_ERR_INVALID; }
   if (maxit < 0) { set_error("maxit must be >= 0"); return HS_ERR_INVALID; }
-  *bytes = ws_bytes_for(A, solver, dtype, maxit);
+  hs_opts o;
+  if (!merge_opts(opts, &o)) return HS_ERR_INVALID;
+  *bytes = ws_need(A, solver, dtype, o, maxit);
   return HS_OK;
+}
+
+hs_status hs_solve_mixed(const hs_op* A, const double* b, double* x, double tol, int maxit, const hs_opts* opts,
+                         void* ws, size_t ws_bytes, void* stream, hs_result* res, double* hist) {
+  return solve_common(run_mixed, HS_SOLVER_MIXED, A, HS_F64, b, x, tol, maxit, opts, ws, ws_bytes, stream, res,
+                      hist);
 }
 
 hs_status hs_jacobi(const hs_op* A, hs_dtype dtype, const void* b, void* x, double tol, int maxit,

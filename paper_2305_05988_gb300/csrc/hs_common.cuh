@@ -44,6 +44,26 @@ struct Geom {
 };
 
 // ---------------------------------------------------------------------------
+// Exact binary32 -> binary64 widening with integer operations.  On this GPU
+// the F2F.F64.F32 conversion instruction issues on the FP64 pipe (measured at
+// about the FP64 FMA rate), so the FP64-accumulated dot products of FP32
+// vectors build the binary64 bit pattern from the binary32 fields instead:
+// exponent rebiased by 1023 - 127 = 896, fraction shifted left by 29.  Normal
+// numbers, zeros, infinities and NaNs are widened exactly; binary32
+// subnormals (magnitude below 2^-126) are flushed to zero.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double widen(double d) { return d; }
+__device__ __forceinline__ double widen(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ef = (u >> 23) & 0xffu;
+  const unsigned de = (ef == 0u) ? 0u : (ef == 255u ? 2047u : ef + 896u);
+  const unsigned m = (ef == 0u) ? 0u : (u & 0x7fffffu);
+  const unsigned hi = (u & 0x80000000u) | (de << 20) | (m >> 3);
+  const unsigned lo = (m & 7u) << 29;
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// ---------------------------------------------------------------------------
 // Deterministic reductions.  Every sum below is taken in a fixed order that
 // depends only on the launch shape, never on timing, so repeated solves give
 // bit-identical scalars.

@@ -97,7 +97,7 @@ struct GsResSink {
   __device__ __forceinline__ void operator()(long long, const Nbr<T>& nb, const Raw& q, int, int, int) {
     T d = jacobi_apply<T, OPK, NDIM>(cf, q.o, nb, q.b) - nb.c;
     if constexpr (OPK == OP_VARK) d = d / q.o.d;
-    acc[0] += (double)d * (double)d;
+    acc[0] += widen(d) * widen(d);
   }
 };
 
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(128) k_gs(GsArgs<T> a) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
     T bv = a.b[i];
     if (OPK != OP_VARK) a.bD[i] = bv * a.invd;
-    acc[0] += (double)bv * (double)bv;
+    acc[0] += widen(bv) * widen(bv);
   }
   block_sum<1>(acc, sh);
   double bb[1];

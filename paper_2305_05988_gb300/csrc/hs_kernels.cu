@@ -8,6 +8,8 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <cmath>
+#include <type_traits>
 
 #include "hs_internal.h"
 
@@ -75,8 +77,8 @@ struct ResidualSink {
     T v = op_apply<T, OPK, NDIM>(cf, q.o, nb);
     T rv = (OPK == OP_VARK) ? q.b - v : fma(-sigma, v, q.b);
     r[idx] = rv;
-    acc[0] += (double)rv * (double)rv;
-    acc[1] += (double)q.b * (double)q.b;
+    acc[0] += widen(rv) * widen(rv);
+    acc[1] += widen(q.b) * widen(q.b);
   }
 };
 
@@ -220,7 +222,7 @@ struct JacobiSink {
     if (fuse) {
       T d = xn - nb.c;
       if constexpr (OPK == OP_VARK) d = d / q.o.d;
-      acc[0] += (double)d * (double)d;
+      acc[0] += widen(d) * widen(d);
     }
   }
 };
@@ -236,7 +238,7 @@ __global__ void __launch_bounds__(512) k_jacobi(JacArgs<T> a) {
   for (long long i = gtid(); i < N; i += gstride()) {
     T bv = a.b[i];
     if (OPK != OP_VARK) a.bD[i] = bv * a.invd;
-    acc[0] += (double)bv * (double)bv;
+    acc[0] += widen(bv) * widen(bv);
   }
   block_sum<1>(acc, sh);
   double bb[1];
@@ -353,7 +355,7 @@ struct ApDotSink {
   __device__ __forceinline__ void operator()(long long idx, const Nbr<T>& nb, const Raw& o, int, int, int) {
     T wv = op_apply<T, OPK, NDIM>(cf, o, nb);
     w[idx] = wv;
-    acc[0] += (double)nb.c * (double)wv;
+    acc[0] += widen(nb.c) * widen(wv);
   }
 };
 
@@ -433,7 +435,7 @@ __global__ void __launch_bounds__(512) k_cg(CgArgs<T> a) {
         rv[u] = fma(-tar, wv[u], rv[u]);
         a.x[q] = xv[u];
         a.r[q] = rv[u];
-        acc1[0] += (double)rv[u] * (double)rv[u];
+        acc1[0] += widen(rv[u]) * widen(rv[u]);
       }
     }
     for (; i < N; i += st) {
@@ -441,7 +443,7 @@ __global__ void __launch_bounds__(512) k_cg(CgArgs<T> a) {
       T rv = fma(-tar, ldcg(a.w + i), ldcg(a.r + i));
       a.x[i] = xv;
       a.r[i] = rv;
-      acc1[0] += (double)rv * (double)rv;
+      acc1[0] += widen(rv) * widen(rv);
     }
     block_sum<1>(acc1, sh);
     double rn[1];
@@ -554,7 +556,7 @@ struct BiVSink {
       rsv = q.q * inv_rn;
       rs[idx] = rsv;
     }
-    acc[0] += (double)vv * (double)rsv;
+    acc[0] += widen(vv) * widen(rsv);
   }
 };
 
@@ -590,7 +592,7 @@ struct BiTSink {
   __device__ __forceinline__ void operator()(long long idx, const Nbr<T>& nb, const Raw& o, int, int, int) {
     T tv = op_apply<T, OPK, NDIM>(cf, o, nb);
     t[idx] = tv;
-    const double sv = (double)nb.c, td = (double)tv;
+    const double sv = widen(nb.c), td = widen(tv);
     acc[0] += sv * sv;
     acc[1] += td * sv;
     acc[2] += td * td;
@@ -708,8 +710,8 @@ __global__ void __launch_bounds__(512) k_bicgstab(BiArgs<T> a) {
         T rn = fma(-toms, tv[u], sv[u]);
         a.x[q] = xn;
         a.r[q] = rn;
-        acc4[0] += (double)rn * (double)rsv[u];
-        acc4[1] += (double)rn * (double)rn;
+        acc4[0] += widen(rn) * widen(rsv[u]);
+        acc4[1] += widen(rn) * widen(rn);
       }
     }
     for (; i < N; i += st) {
@@ -718,8 +720,8 @@ __global__ void __launch_bounds__(512) k_bicgstab(BiArgs<T> a) {
       T rn = fma(-toms, ldcg(a.t + i), sv);
       a.x[i] = xn;
       a.r[i] = rn;
-      acc4[0] += (double)rn * (double)ldcg(a.rs + i);
-      acc4[1] += (double)rn * (double)rn;
+      acc4[0] += widen(rn) * widen(ldcg(a.rs + i));
+      acc4[1] += widen(rn) * widen(rn);
     }
     block_sum<2>(acc4, sh);
     double rn2[2];
@@ -1252,6 +1254,66 @@ hs_status run_jacobi(const SolveArgs& sa, hs_result* res, double* hist) {
   });
 }
 
+// ---- Krylov cores: launch one persistent solve on given coefficients --------
+template <typename T, int OPK, int NDIM>
+static hs_status cg_core(const hs_op* A, const Coef<T>& cf, double sigma, const T* b, T* x, double tol, int maxit,
+                         const Common& cm, T* r, T* p0, T* p1, T* w, const hs_opts& o, cudaStream_t st) {
+  CgArgs<T> a = {};
+  a.g = geom_of(A);
+  a.cf = cf;
+  a.sigma = sigma;
+  a.b = b;
+  a.x = x;
+  a.r = r;
+  a.p0 = p0;
+  a.p1 = p1;
+  a.w = w;
+  a.cm = cm;
+  a.maxit = maxit;
+  a.tol = tol;
+  hs_status s = init_ctrl(cm, o, st);
+  if (s != HS_OK) return s;
+  int by = rows_per_tile(a.g);
+  size_t smem = slab_bytes<T>(by);
+  int grid;
+  s = plan_persistent(k_cg<T, OPK, NDIM>, 32 * by, smem, a.g, by, true, &grid, &a.tl);
+  if (s != HS_OK) return s;
+  void* args[] = {&a};
+  return launch_coop((const void*)k_cg<T, OPK, NDIM>, grid, 32 * by, args, smem, st);
+}
+
+template <typename T, int OPK, int NDIM>
+static hs_status bicgstab_core(const hs_op* A, const Coef<T>& cf, double sigma, const T* b, T* x, double tol,
+                               int maxit, const Common& cm, T* const v[8], const hs_opts& o, cudaStream_t st) {
+  BiArgs<T> a = {};
+  a.g = geom_of(A);
+  a.cf = cf;
+  a.sigma = sigma;
+  a.b = b;
+  a.x = x;
+  a.r = v[0];
+  a.rs = v[1];
+  a.p0 = v[2];
+  a.p1 = v[3];
+  a.v0 = v[4];
+  a.v1 = v[5];
+  a.s = v[6];
+  a.t = v[7];
+  a.cm = cm;
+  a.maxit = maxit;
+  a.tol = tol;
+  a.reps = o.restart_eps;
+  hs_status s = init_ctrl(cm, o, st);
+  if (s != HS_OK) return s;
+  int by = rows_per_tile(a.g);
+  size_t smem = slab_bytes<T>(by);
+  int grid;
+  s = plan_persistent(k_bicgstab<T, OPK, NDIM>, 32 * by, smem, a.g, by, true, &grid, &a.tl);
+  if (s != HS_OK) return s;
+  void* args[] = {&a};
+  return launch_coop((const void*)k_bicgstab<T, OPK, NDIM>, grid, 32 * by, args, smem, st);
+}
+
 // ---- CG -----------------------------------------------------------------------
 hs_status run_cg(const SolveArgs& sa, hs_result* res, double* hist) {
   return dispatch(sa.dtype, opkind_of(sa.A), sa.A->ndim, [&](auto tag) -> hs_status {
@@ -1262,11 +1324,10 @@ hs_status run_cg(const SolveArgs& sa, hs_result* res, double* hist) {
     Geom g = geom_of(A);
     Carve c{sa.ws, 0, sa.ws_bytes, true};
     Common cm = carve_common(c, sa.maxit);
-    CgArgs<T> a = {};
-    a.r = c.take<T>(g.N);
-    a.p0 = c.take<T>(g.N);
-    a.p1 = c.take<T>(g.N);
-    a.w = c.take<T>(g.N);
+    T* r = c.take<T>(g.N);
+    T* p0 = c.take<T>(g.N);
+    T* p1 = c.take<T>(g.N);
+    T* w = c.take<T>(g.N);
     T *D = nullptr, *ax = nullptr, *ay = nullptr, *az = nullptr;
     if (OPK == OP_VARK) {
       D = c.take<T>(g.N);
@@ -1278,28 +1339,16 @@ hs_status run_cg(const SolveArgs& sa, hs_result* res, double* hist) {
       set_error("workspace too small for CG");
       return HS_ERR_WORKSPACE;
     }
-    hs_status s = init_ctrl(cm, sa.o, sa.stream);
-    if (s != HS_OK) return s;
     if (OPK == OP_VARK) {
-      s = setup_vark(A, sa.dtype, D, ax, ay, az, false, sa.stream);
+      hs_status s = setup_vark(A, sa.dtype, D, ax, ay, az, false, sa.stream);
       if (s != HS_OK) return s;
     }
-    a.cf = op_coef<T>(A, D, ax, ay, az, &a.sigma);
-    a.g = g;
-    a.b = (const T*)sa.b;
-    a.x = (T*)sa.x;
-    a.cm = cm;
-    a.maxit = sa.maxit;
-    a.tol = sa.tol;
-    int by = rows_per_tile(g);
-    size_t smem = slab_bytes<T>(by);
-    int grid;
-    s = plan_persistent(k_cg<T, OPK, NDIM>, 32 * by, smem, g, by, true, &grid, &a.tl);
+    double sigma;
+    Coef<T> cf = op_coef<T>(A, D, ax, ay, az, &sigma);
+    hs_status s = cg_core<T, OPK, NDIM>(A, cf, sigma, (const T*)sa.b, (T*)sa.x, sa.tol, sa.maxit, cm, r, p0, p1, w,
+                                        sa.o, sa.stream);
     if (s != HS_OK) return s;
-    void* args[] = {&a};
-    s = launch_coop((const void*)k_cg<T, OPK, NDIM>, grid, 32 * by, args, smem, sa.stream);
-    if (s != HS_OK) return s;
-    Tail t{A, sa.dtype, D, ax, ay, az, sa.b, sa.x, a.w};
+    Tail t{A, sa.dtype, D, ax, ay, az, sa.b, sa.x, w};
     return finish_solve(sa, cm, t, res, hist, true);
   });
 }
@@ -1314,15 +1363,8 @@ hs_status run_bicgstab(const SolveArgs& sa, hs_result* res, double* hist) {
     Geom g = geom_of(A);
     Carve c{sa.ws, 0, sa.ws_bytes, true};
     Common cm = carve_common(c, sa.maxit);
-    BiArgs<T> a = {};
-    a.r = c.take<T>(g.N);
-    a.rs = c.take<T>(g.N);
-    a.p0 = c.take<T>(g.N);
-    a.p1 = c.take<T>(g.N);
-    a.v0 = c.take<T>(g.N);
-    a.v1 = c.take<T>(g.N);
-    a.s = c.take<T>(g.N);
-    a.t = c.take<T>(g.N);
+    T* v[8];
+    for (int q = 0; q < 8; q++) v[q] = c.take<T>(g.N);
     T *D = nullptr, *ax = nullptr, *ay = nullptr, *az = nullptr;
     if (OPK == OP_VARK) {
       D = c.take<T>(g.N);
@@ -1334,31 +1376,191 @@ hs_status run_bicgstab(const SolveArgs& sa, hs_result* res, double* hist) {
       set_error("workspace too small for BiCGStab");
       return HS_ERR_WORKSPACE;
     }
-    hs_status s = init_ctrl(cm, sa.o, sa.stream);
-    if (s != HS_OK) return s;
     if (OPK == OP_VARK) {
-      s = setup_vark(A, sa.dtype, D, ax, ay, az, false, sa.stream);
+      hs_status s = setup_vark(A, sa.dtype, D, ax, ay, az, false, sa.stream);
       if (s != HS_OK) return s;
     }
-    a.cf = op_coef<T>(A, D, ax, ay, az, &a.sigma);
-    a.g = g;
-    a.b = (const T*)sa.b;
-    a.x = (T*)sa.x;
-    a.cm = cm;
-    a.maxit = sa.maxit;
-    a.tol = sa.tol;
-    a.reps = sa.o.restart_eps;
-    int by = rows_per_tile(g);
-    size_t smem = slab_bytes<T>(by);
-    int grid;
-    s = plan_persistent(k_bicgstab<T, OPK, NDIM>, 32 * by, smem, g, by, true, &grid, &a.tl);
+    double sigma;
+    Coef<T> cf = op_coef<T>(A, D, ax, ay, az, &sigma);
+    hs_status s = bicgstab_core<T, OPK, NDIM>(A, cf, sigma, (const T*)sa.b, (T*)sa.x, sa.tol, sa.maxit, cm, v, sa.o,
+                                              sa.stream);
     if (s != HS_OK) return s;
-    void* args[] = {&a};
-    s = launch_coop((const void*)k_bicgstab<T, OPK, NDIM>, grid, 32 * by, args, smem, sa.stream);
-    if (s != HS_OK) return s;
-    Tail t{A, sa.dtype, D, ax, ay, az, sa.b, sa.x, a.s};
+    Tail t{A, sa.dtype, D, ax, ay, az, sa.b, sa.x, v[6]};
     return finish_solve(sa, cm, t, res, hist, true);
   });
+}
+
+// ===========================================================================
+// Mixed-precision iterative refinement (FP64 outer, FP32 inner).
+//   outer, FP64 on the GPU: r = b - A x, ||r|| / ||b|| (stop at tol)
+//   inner, FP32:            solve A d = r / ||r|| to inner_tol with CG or
+//                           BiCGStab on FP32 vectors and FP32 coefficients,
+//                           dot products accumulated in FP64
+//   outer, FP64:            x += ||r|| d
+// The FP64 and FP32 coefficient arrays of a diffusion operator are formed
+// once per solve from the operator's k.
+// ===========================================================================
+
+__global__ void k_r_to_f32(const double* __restrict__ r, float* __restrict__ r32, double scale, long long N) {
+  for (long long i = gtid(); i < N; i += gstride()) r32[i] = (float)(r[i] * scale);
+}
+__global__ void k_x_add_f32(double* __restrict__ x, const float* __restrict__ d, double scale, long long N) {
+  for (long long i = gtid(); i < N; i += gstride()) x[i] = fma(scale, widen(d[i]), x[i]);
+}
+
+struct MixedLayout {
+  Common outer;
+  double* r64;
+  double *D64, *ax64, *ay64, *az64;
+  Common inner;
+  float* r32;
+  float* d32;
+  float* v32[8];
+  float *D32, *ax32, *ay32, *az32;
+};
+
+static MixedLayout carve_mixed(Carve& c, const hs_op* A, const hs_opts& o, int max_outer) {
+  MixedLayout L = {};
+  const size_t N = (size_t)(A->n[0] * A->n[1] * A->n[2]);
+  const bool vark = A->kind == KIND_DIFFUSION;
+  const int nvec = (o.inner_solver == HS_SOLVER_BICGSTAB) ? 8 : 4;
+  L.outer = carve_common(c, max_outer);
+  L.r64 = c.take<double>(N);
+  if (vark) {
+    L.D64 = c.take<double>(N);
+    L.ax64 = c.take<double>(N);
+    L.ay64 = c.take<double>(N);
+    L.az64 = c.take<double>(N);
+  }
+  L.inner = carve_common(c, std::max(o.inner_maxit, 1));
+  L.r32 = c.take<float>(N);
+  L.d32 = c.take<float>(N);
+  for (int q = 0; q < nvec; q++) L.v32[q] = c.take<float>(N);
+  if (vark) {
+    L.D32 = c.take<float>(N);
+    L.ax32 = c.take<float>(N);
+    L.ay32 = c.take<float>(N);
+    L.az32 = c.take<float>(N);
+  }
+  return L;
+}
+
+size_t mixed_ws_bytes(const hs_op* A, const hs_opts& o, int max_outer) {
+  Carve c{nullptr, 0, (size_t)-1, true};
+  carve_mixed(c, A, o, max_outer);
+  return c.off;
+}
+
+hs_status run_mixed(const SolveArgs& sa, hs_result* res, double* hist) {
+  const hs_op* A = sa.A;
+  const Geom g = geom_of(A);
+  const int max_outer = sa.maxit;
+  Carve c{sa.ws, 0, sa.ws_bytes, true};
+  MixedLayout L = carve_mixed(c, A, sa.o, max_outer);
+  if (!c.ok) {
+    set_error("workspace too small for mixed-precision refinement");
+    return HS_ERR_WORKSPACE;
+  }
+  cudaStream_t st = sa.stream;
+  hs_status s;
+  if (A->kind == KIND_DIFFUSION) {
+    s = setup_vark(A, HS_F64, L.D64, L.ax64, L.ay64, L.az64, false, st);
+    if (s != HS_OK) return s;
+    s = setup_vark(A, HS_F32, L.D32, L.ax32, L.ay32, L.az32, false, st);
+    if (s != HS_OK) return s;
+  }
+  const int blocks = (int)std::max<long long>(1, std::min<long long>((g.N + 255) / 256, (long long)sm_count() * 8));
+  const bool use_bicg = sa.o.inner_solver == HS_SOLVER_BICGSTAB;
+  const int opk = opkind_of(A);
+  if (!use_bicg && opk == OP_NONSYM) {
+    set_error("mixed precision with inner CG needs a symmetric operator");
+    return HS_ERR_INVALID;
+  }
+  long long inner_total = 0;
+  int outer = 0, status = HS_NOT_CONVERGED;
+  double rel = -1.0;
+  for (;; outer++) {
+    // FP64 residual and its norm
+    s = residual_norms(A, HS_F64, L.D64, L.ax64, L.ay64, L.az64, sa.b, sa.x, L.r64, &L.outer.ctrl->aux[0],
+                       L.outer.partials, st);
+    if (s != HS_OK) return s;
+    double nrm[2];
+    cudaError_t e = cudaMemcpyAsync(nrm, &L.outer.ctrl->aux[0], 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "mixed: residual read-back");
+    if (nrm[1] == 0.0) {
+      e = cudaMemsetAsync(sa.x, 0, sizeof(double) * (size_t)g.N, st);
+      if (e != cudaSuccess) return cuda_fail(e, "mixed: zero x");
+      rel = 0.0;
+      status = HS_OK;
+      if (hist) hist[outer] = 0.0;
+      break;
+    }
+    rel = sqrt(nrm[0] / nrm[1]);
+    if (hist && outer <= max_outer) hist[outer] = rel;
+    if (!std::isfinite(rel)) {
+      status = HS_ERR_NONFINITE;
+      break;
+    }
+    if (rel <= sa.tol) {
+      status = HS_OK;
+      break;
+    }
+    if (outer == max_outer) break;
+    // FP32 correction solve on the normalised residual
+    const double rn = sqrt(nrm[0]);
+    k_r_to_f32<<<blocks, 256, 0, st>>>(L.r64, L.r32, 1.0 / rn, g.N);
+    e = cudaMemsetAsync(L.d32, 0, sizeof(float) * (size_t)g.N, st);
+    if (e != cudaSuccess) return cuda_fail(e, "mixed: zero correction");
+    s = dispatch(HS_F32, opk, A->ndim, [&](auto tag) -> hs_status {
+      using Tg = decltype(tag);
+      using T = typename Tg::T;
+      constexpr int OPK = Tg::OPK, NDIM = Tg::NDIM;
+      if constexpr (!std::is_same<T, float>::value) {
+        return HS_ERR_INVALID;
+      } else {
+        double sigma;
+        Coef<T> cf = op_coef<T>(A, L.D32, L.ax32, L.ay32, L.az32, &sigma);
+        if (use_bicg)
+          return bicgstab_core<T, OPK, NDIM>(A, cf, sigma, L.r32, L.d32, sa.o.inner_tol, sa.o.inner_maxit, L.inner,
+                                             L.v32, sa.o, st);
+        if constexpr (OPK == OP_NONSYM) {
+          return HS_ERR_INVALID;
+        } else {
+          return cg_core<T, OPK, NDIM>(A, cf, sigma, L.r32, L.d32, sa.o.inner_tol, sa.o.inner_maxit, L.inner,
+                                       L.v32[0], L.v32[1], L.v32[2], L.v32[3], sa.o, st);
+        }
+      }
+    });
+    if (s != HS_OK) return s;
+    Ctrl h;
+    e = cudaMemcpyAsync(&h, L.inner.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "mixed: inner solve");
+    inner_total += h.iters;
+    if (h.status == DS_TIMEOUT) {
+      status = HS_ERR_TIMEOUT;
+      break;
+    }
+    if (h.status == DS_NONFINITE) {
+      status = HS_ERR_NONFINITE;
+      break;
+    }
+    // a breakdown or an unconverged inner solve still yields a usable
+    // correction; the FP64 residual of the next outer step decides
+    k_x_add_f32<<<blocks, 256, 0, st>>>((double*)sa.x, L.d32, rn, g.N);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "mixed: correction update");
+  }
+  res->iters = outer;
+  res->outer = outer;
+  res->inner_iters = inner_total;
+  res->rel_res = rel;
+  res->true_rel_res = rel;
+  res->status = status;
+  if (status == HS_ERR_NONFINITE) set_error("non-finite value in the refinement");
+  if (status == HS_ERR_TIMEOUT) set_error("a device-side wait ran out (timeout)");
+  return (hs_status)status;
 }
 
 }  // namespace hs

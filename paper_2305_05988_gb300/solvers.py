@@ -112,10 +112,11 @@ class Operator:
             raise ValueError("%s must be contiguous" % name)
         return t
 
-    def workspace(self, solver: int, dtype: torch.dtype, maxit: int, device) -> torch.Tensor:
+    def workspace(self, solver: int, dtype: torch.dtype, maxit: int, device, opts=None) -> torch.Tensor:
         """Device workspace for a solver (cached per size on this operator)."""
         size = ctypes.c_size_t()
-        check(_lib.load().hs_workspace_size(self._op, solver, _DT[dtype], None, int(maxit), ctypes.byref(size)),
+        optr = ctypes.byref(opts) if opts is not None else None
+        check(_lib.load().hs_workspace_size(self._op, solver, _DT[dtype], optr, int(maxit), ctypes.byref(size)),
               "hs_workspace_size")
         key = (str(device), size.value)
         ws = self._ws.get(key)
@@ -157,7 +158,6 @@ def make_opts(**kw) -> _lib.hs_opts:
     o.restart_eps = 1e-5
     o.true_residual = 1
     o.timeout_s = 2.0
-    o.max_outer = 20
     o.inner_tol = 1e-5
     o.inner_solver = _lib.HS_SOLVER_CG
     o.inner_maxit = 10000
@@ -211,6 +211,38 @@ def _solve(solver: int, A: Operator, b: torch.Tensor, x0, tol, maxit, history, i
                      status_code=res.status, rel_res=res.rel_res, true_rel_res=res.true_rel_res,
                      restarts=res.restarts, history=hist, outer=res.outer, inner_iters=res.inner_iters)
     return x, info
+
+
+def solve_mixed(A: Operator, b, x0=None, tol: float = 1e-10, maxit: int = 20, history: bool = True,
+                inner_tol: float = 1e-5, inner_solver: str = "cg", inner_maxit: int = 10000, inplace=False, **kw):
+    """Mixed-precision iterative refinement: FP64 residual and update, FP32 inner
+    CG / BiCGStab with FP64-accumulated dots.  b, x0: float64 CUDA tensors."""
+    A._vec(b, "b")
+    if b.dtype != torch.float64:
+        raise TypeError("solve_mixed takes float64 b and x")
+    if x0 is None:
+        x = torch.zeros_like(b)
+    else:
+        A._vec(x0, "x0")
+        x = x0 if inplace else x0.clone()
+    opts = make_opts(inner_tol=inner_tol, inner_solver=inner_solver, inner_maxit=inner_maxit, **kw)
+    res = _lib.hs_result()
+    hist = np.full(int(maxit) + 1, np.nan) if history else None
+    hptr = hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if hist is not None else None
+    lib = _lib.load()
+    with torch.cuda.device(b.device):
+        ws = A.workspace(_lib.HS_SOLVER_MIXED, torch.float64, maxit, b.device, opts)
+        st = torch.cuda.current_stream(b.device).cuda_stream
+        status = lib.hs_solve_mixed(A._op, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                    float(tol), int(maxit), ctypes.byref(opts), ctypes.c_void_p(ws.data_ptr()),
+                                    ws.numel(), ctypes.c_void_p(st), ctypes.byref(res), hptr)
+    if status in (_lib.HS_ERR_INVALID, _lib.HS_ERR_CUDA, _lib.HS_ERR_WORKSPACE):
+        raise _lib.HsError(status, "hs_solve_mixed")
+    if hist is not None:
+        hist = hist[: res.iters + 1]
+    return x, SolveInfo(iters=res.iters, status=_lib.STATUS_NAMES.get(res.status, str(res.status)),
+                        status_code=res.status, rel_res=res.rel_res, true_rel_res=res.true_rel_res,
+                        restarts=res.restarts, history=hist, outer=res.outer, inner_iters=res.inner_iters)
 
 
 def jacobi(A: Operator, b, x0=None, tol: float = 0.0, maxit: int = 100, history: bool = False, **kw):
