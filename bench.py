@@ -49,6 +49,21 @@ BYTES = {
     "bicgstab": 136.0,     # per iteration (17 vector passes of 8 B)
 }
 
+# FP64 flops per unknown and iteration executed by the kernels (FMA = 2),
+# counted from the kernel code for the 7-point operators of the workload:
+#   spmv      3 pair adds + 3 FMA + 1 scaling multiply             = 10
+#   jacobi    3 pair adds + 3 FMA                                   =  9
+#   gs        as jacobi                                             =  9
+#   cg        p update FMA, stencil 3 adds + 3 FMA, p.w FMA;
+#             x and r FMA, r.r FMA                                  = 19
+#   bicgstab  p update 2 FMA, upwind stencil 6 FMA, v.r' FMA;
+#             s FMA, stencil 6 FMA, 3 dot FMA; x 2 FMA, r FMA,
+#             2 dot FMA                                             = 48
+FLOPS = {"spmv": 10.0, "jacobi": 9.0, "gauss_seidel": 9.0, "cg": 19.0, "bicgstab": 48.0}
+# FP64 pipe: 2 FMA lanes per SM per clock (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on
+# peak_sustained = 2 per SM per cycle) x 2 flops x 152 SMs.
+FP64_FLOPS_PER_CLK = 2 * 2 * 152
+
 
 def parse():
     p = argparse.ArgumentParser()
@@ -63,6 +78,8 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-roofline", action="store_true", help="skip the roofline repeats (profiling runs)")
     p.add_argument("--timeout-s", type=float, default=2.0, help="bound on device-side waits")
+    p.add_argument("--mixed-n", type=int, default=512, help="grid side of the mixed-precision comparison (0: skip)")
+    p.add_argument("--adjoint-n", type=int, default=256, help="grid side of the adjoint-gradient timing (0: skip)")
     return p.parse_args()
 
 
@@ -340,12 +357,20 @@ def run_ours(args, rank, world, dist):
             dts.append(ra.elapsed_time(rb))
             its = inf.iters
         dt = statistics.median(dts)
-        achieved = BYTES[dom] * N * its / (dt * 1e-3) / 1e9
+        hbm_gbs = BYTES[dom] * N * its / (dt * 1e-3) / 1e9
+        tflops = FLOPS[dom] * N * its / (dt * 1e-3) / 1e12
+        clk = (clocks.get("sm_mhz") or 2070.0) * 1e6
+        fp64_peak = FP64_FLOPS_PER_CLK * clk / 1e12
         kname = {"cg": "k_cg", "bicgstab": "k_bicgstab", "jacobi": "k_jacobi", "gauss_seidel": "k_gs"}[dom]
-        roofline = {"kernel": kname + " (FP64, persistent: one launch per solve)", "bound": "hbm",
-                    "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                    "frac": round(achieved / peak, 4), "peak_source": peak_kind, "traffic": None,
-                    "alg_bytes_per_launch": BYTES[dom] * N * its, "launch_ms": round(dt, 3), "iters": its}
+        roofline = {"kernel": kname + " (FP64, persistent: one launch per solve)", "bound": "alu",
+                    "achieved": round(tflops, 4), "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
+                    "frac": round(tflops / fp64_peak, 4),
+                    "peak_source": "FP64 pipe: 2 FMA lanes/SM/clock x 2 flops x 152 SMs x %.0f MHz (median SM "
+                                   "clock sampled in the timed region)" % (clk / 1e6),
+                    "traffic": None, "flops_per_unknown_iter": FLOPS[dom], "iters": its, "launch_ms": round(dt, 3),
+                    "hbm": {"achieved": round(hbm_gbs, 1), "peak": peak, "unit": "GB/s",
+                            "frac": round(hbm_gbs / peak, 4), "peak_source": peak_kind,
+                            "alg_bytes_per_unknown_iter": BYTES[dom]}}
 
     # ---- e2e: host buffers, copies inside the timed region ----
     e2e = None
@@ -381,6 +406,12 @@ def run_ours(args, rank, world, dist):
         cpu = {"value": nb / secs / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": desc,
                "seconds": round(secs, 2)}
 
+    extras = {}
+    if rank == 0 and args.mixed_n > 0:
+        extras["mixed_vs_fp64"] = mixed_comparison(args.mixed_n, dev, tmo)
+    if rank == 0 and args.adjoint_n > 0:
+        extras["adjoint"] = adjoint_timing(args.adjoint_n, dev, tmo)
+
     # kernels launched per step: spmv 1; jacobi, cg, bicgstab: control init +
     # persistent solver + residual + finalize = 4 each; gauss-seidel: solver +
     # residual + finalize = 3 (its control block is uploaded by a copy)
@@ -396,8 +427,79 @@ def run_ours(args, rank, world, dist):
                        "l2": "inputs and solver state (>= 2 x 134 MB per solver) exceed the 129 MB L2; no flush"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps, "clocks": clocks, "solvers": breakdown,
+            "extras": extras,
         }
         print(json.dumps(line), flush=True)
+
+
+def mixed_comparison(n, dev, tmo):
+    """Time-to-1e-10 on the variable-coefficient diffusion system (log k ~ N(0,1)):
+    plain FP64 CG against FP32-inner / FP64-outer refinement on the same GPU."""
+    import torch
+
+    import paper_2305_05988_gb300 as hs
+    from paper_2305_05988_gb300 import inputs
+    shape = (n, n, n)
+    k = torch.from_numpy(np.exp(inputs.log_k(shape, 1.0, 0))).to(dev)
+    b = torch.from_numpy(inputs.rhs_uniform(shape, 0)).to(dev)
+    A = hs.Operator.diffusion(shape, k)
+    out = {"workload": "%d^3 diffusion, log k ~ N(0,1), f ~ U(-1,1), tol 1e-10" % n}
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    stream = torch.cuda.current_stream(dev)
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    x, info = hs.cg(A, b, tol=1e-10, maxit=200000, history=False, timeout_s=max(tmo, 10.0))
+    ev[1].record(stream)
+    xm, im = hs.solve_mixed(A, b, tol=1e-10, maxit=40, inner_tol=1e-4, inner_maxit=200000,
+                            timeout_s=max(tmo, 10.0))
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    t64 = ev[0].elapsed_time(ev[1])
+    tmx = ev[1].elapsed_time(ev[2])
+    err = (torch.linalg.norm(xm - x) / torch.linalg.norm(x)).item()
+    out["fp64_cg"] = {"ms": round(t64, 2), "iters": info.iters, "true_rel_res": info.true_rel_res,
+                      "status": info.status}
+    out["mixed"] = {"ms": round(tmx, 2), "outer": im.outer, "inner_iters": im.inner_iters,
+                    "true_rel_res": im.true_rel_res, "status": im.status, "inner_tol": 1e-4,
+                    "rel_err_vs_fp64_solution": err}
+    out["speedup"] = round(t64 / tmx, 3)
+    del A, k, b, x, xm
+    torch.cuda.empty_cache()
+    return out
+
+
+def adjoint_timing(n, dev, tmo):
+    """Forward solve, adjoint solve and per-cell gradient of L = ||u - u_obs||^2
+    on the 256^3 inverse-diffusion workload (log k ~ N(0, 0.5^2))."""
+    import torch
+
+    import paper_2305_05988_gb300 as hs
+    from paper_2305_05988_gb300 import inputs
+    shape = (n, n, n)
+    logk = torch.from_numpy(inputs.log_k(shape, 0.5, 0)).to(dev).requires_grad_(True)
+    f = torch.from_numpy(inputs.rhs_uniform(shape, 0)).to(dev).requires_grad_(True)
+    k2 = torch.from_numpy(np.exp(inputs.log_k(shape, 0.5, 0, inputs.STREAM_K2))).to(dev)
+    u_obs = hs.cg(hs.Operator.diffusion(shape, k2), f.detach(), tol=1e-12, maxit=200000, history=False,
+                  timeout_s=max(tmo, 10.0))[0]
+    stream = torch.cuda.current_stream(dev)
+    out = {"workload": "%d^3 inverse diffusion, log k ~ N(0, 0.5^2), tol 1e-10" % n}
+    for mixed in (False, True):
+        logk.grad = None
+        f.grad = None
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        u = hs.diffusion_solve(logk, f, shape, tol=1e-10, mixed=mixed, maxit=200000)
+        L = torch.sum((u - u_obs) ** 2)
+        L.backward()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out["mixed" if mixed else "fp64"] = {"ms_forward_adjoint_gradient": round(e0.elapsed_time(e1), 2),
+                                             "loss": L.item(),
+                                             "grad_logk_norm": torch.linalg.norm(logk.grad).item()}
+    del logk, f, k2, u_obs
+    torch.cuda.empty_cache()
+    return out
 
 
 def main():

@@ -198,6 +198,19 @@ hs_status hs_solve_mixed(const hs_op *A, const double *b, double *x, double tol,
                          const hs_opts *opts, void *ws, size_t ws_bytes, void *stream,
                          hs_result *res, double *hist);
 
+/* Adjoint gradient through the diffusion solve.  Not in the paper: it
+ * differentiates a loss L(u) with A(k) u = f for inverse problems.  Given the
+ * forward solution u and the adjoint lam solving A^T lam = dL/du (A is
+ * symmetric, so lam comes from hs_cg with right-hand side dL/du), writes
+ *   g_i = dL/dlog k_i = -k_i sum_{faces f of i} dkappa_f/dk_i
+ *                        (lam_i - lam_j)(u_i - u_j) / h_d^2,
+ * dkappa_f/dk_i = 2 k_j^2 / (k_i + k_j)^2 for an interior face and 1 for a
+ * boundary face (lam_j = u_j = 0).  dL/df is lam itself.  u, lam, g: FP64
+ * device vectors of N elements; g must not alias u or lam.  A must be a
+ * diffusion operator (HS_ERR_INVALID otherwise). */
+hs_status hs_diffusion_grad_logk(const hs_op *A, const double *u, const double *lam, double *g,
+                                 void *stream);
+
 /* ---- conjugate gradient without any allocation --------------------------
  * The paper has no counterpart to this entry point; it exists for callers
  * that cannot allocate device memory themselves -- for example a plug-in

@@ -78,6 +78,7 @@ SIGNATURES = {
                          ctypes.POINTER(hs_result), ctypes.POINTER(_d)]),
     "hs_solve_mixed": (_i, [_vp, _vp, _vp, _d, _i, ctypes.POINTER(hs_opts), _vp, _sz, _vp,
                             ctypes.POINTER(hs_result), ctypes.POINTER(_d)]),
+    "hs_diffusion_grad_logk": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "hs_cg_static": (_i, [_vp, _i, _vp, _vp, _d, _i, ctypes.POINTER(hs_opts), _vp,
                           ctypes.POINTER(hs_result), ctypes.POINTER(_d)]),
     "hs_last_error": (ctypes.c_char_p, []),

@@ -129,14 +129,29 @@ __device__ __forceinline__ void gs_tile(const GsArgs<T>& a, T* sm, int tile, boo
   const int i0 = I * TX, j0 = J * TY, k0 = K * TZ;
   const T* bsrc = (OPK == OP_VARK) ? a.b : a.bD;
 
-  // load tile + one-node halo (zero outside the grid)
-  for (int e = threadIdx.x; e < SX * SY * SZ; e += blockDim.x) {
-    int ii = e % SX, jj = (e / SX) % SY, kk = e / (SX * SY);
-    int gi = i0 + ii - 1, gj = j0 + jj - 1, gk = k0 + kk - ZOFF;
-    T v = T(0);
-    if (gi >= 0 && gi < g.nx && gj >= 0 && gj < g.ny && gk >= 0 && gk < g.nz)
-      v = __ldcg(a.x + (long long)gk * g.plane + (long long)gj * g.nx + gi);
-    sm[e] = v;
+  // load tile + one-node halo (zero outside the grid); each thread issues
+  // LU independent loads before storing any of them, so a tile costs a few
+  // memory round trips instead of one per element
+  constexpr int TOT = SX * SY * SZ;
+  constexpr int LU = 16;
+  for (int base = threadIdx.x; base < TOT; base += LU * 128) {
+    T v[LU];
+#pragma unroll
+    for (int u = 0; u < LU; u++) {
+      const int e = base + u * 128;
+      v[u] = T(0);
+      if (e < TOT) {
+        const int ii = e % SX, jj = (e / SX) % SY, kk = e / (SX * SY);
+        const int gi = i0 + ii - 1, gj = j0 + jj - 1, gk = k0 + kk - ZOFF;
+        if (gi >= 0 && gi < g.nx && gj >= 0 && gj < g.ny && gk >= 0 && gk < g.nz)
+          v[u] = __ldcg(a.x + (long long)gk * g.plane + (long long)gj * g.nx + gi);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < LU; u++) {
+      const int e = base + u * 128;
+      if (e < TOT) sm[e] = v[u];
+    }
   }
   __syncthreads();
 

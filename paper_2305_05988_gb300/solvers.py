@@ -265,3 +265,63 @@ def bicgstab(A: Operator, b, x0=None, tol: float = 1e-10, maxit: int = 10000, hi
              restart_eps: float = 1e-5, **kw):
     """BiCGStab with Algorithm 2's normalised shadow residual and restart."""
     return _solve(_lib.HS_SOLVER_BICGSTAB, A, b, x0, tol, maxit, history, restart_eps=restart_eps, **kw)
+
+
+def grad_logk(A: Operator, u: torch.Tensor, lam: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """dL/dlog k per cell from the forward solution u and the adjoint lam (float64)."""
+    if A.kind != "diffusion":
+        raise ValueError("grad_logk needs a diffusion operator")
+    for t, n in ((u, "u"), (lam, "lam")):
+        A._vec(t, n)
+        if t.dtype != torch.float64:
+            raise TypeError("%s must be float64" % n)
+    g = torch.empty_like(u) if out is None else A._vec(out, "out")
+    with torch.cuda.device(u.device):
+        st = torch.cuda.current_stream(u.device).cuda_stream
+        check(_lib.load().hs_diffusion_grad_logk(A._op, ctypes.c_void_p(u.data_ptr()),
+                                                 ctypes.c_void_p(lam.data_ptr()), ctypes.c_void_p(g.data_ptr()),
+                                                 ctypes.c_void_p(st)), "hs_diffusion_grad_logk")
+    return g
+
+
+class DiffusionSolve(torch.autograd.Function):
+    """u = A(exp(logk))^{-1} f for the variable-coefficient diffusion operator,
+    differentiable in logk and f.  The backward pass solves the adjoint system
+    A lam = dL/du (A is symmetric) with the same solver as the forward pass and
+    returns dL/dlogk from the per-cell gradient kernel and dL/df = lam."""
+
+    @staticmethod
+    def forward(ctx, logk, f, shape, tol=1e-12, mixed=False, maxit=100000):
+        k = torch.exp(logk.detach()).contiguous()
+        A = Operator.diffusion(shape, k)
+        fd = f.detach().contiguous()
+        if mixed:
+            u, info = solve_mixed(A, fd, tol=tol, maxit=60, inner_maxit=maxit)
+        else:
+            u, info = cg(A, fd, tol=tol, maxit=maxit, history=False)
+        if info.status_code < 0 or info.status_code == _lib.HS_NOT_CONVERGED:
+            raise RuntimeError("forward diffusion solve failed: %s" % info.status)
+        ctx.A, ctx.tol, ctx.mixed, ctx.maxit = A, tol, mixed, maxit
+        ctx.save_for_backward(u)
+        ctx.info = info
+        return u
+
+    @staticmethod
+    def backward(ctx, grad_u):
+        (u,) = ctx.saved_tensors
+        A = ctx.A
+        rhs = grad_u.detach().contiguous().to(torch.float64)
+        if ctx.mixed:
+            lam, info = solve_mixed(A, rhs, tol=ctx.tol, maxit=60, inner_maxit=ctx.maxit)
+        else:
+            lam, info = cg(A, rhs, tol=ctx.tol, maxit=ctx.maxit, history=False)
+        if info.status_code < 0 or info.status_code == _lib.HS_NOT_CONVERGED:
+            raise RuntimeError("adjoint diffusion solve failed: %s" % info.status)
+        g = grad_logk(A, u, lam)
+        return g, lam, None, None, None, None
+
+
+def diffusion_solve(logk: torch.Tensor, f: torch.Tensor, shape, tol: float = 1e-12, mixed: bool = False,
+                    maxit: int = 100000) -> torch.Tensor:
+    """Differentiable solve of -div(exp(logk) grad u) = f (float64 CUDA tensors)."""
+    return DiffusionSolve.apply(logk, f, tuple(shape), tol, mixed, maxit)
