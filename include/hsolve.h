@@ -91,6 +91,8 @@ typedef struct {
     double inner_tol;       /* mixed precision: inner relative tolerance (1e-5) */
     int inner_solver;       /* mixed precision: HS_SOLVER_CG or _BICGSTAB (CG)  */
     int inner_maxit;        /* mixed precision: inner iteration cap (10000)     */
+    int use_graph;          /* batched solver: replay one captured CUDA graph
+                               (default 1; needs a non-default stream)          */
 } hs_opts;
 
 typedef struct {
@@ -236,6 +238,40 @@ hs_status hs_diffusion_grad_logk(const hs_op *A, const double *u, const double *
 #define HS_STATIC_SCRATCH_BYTES (16u << 20)
 hs_status hs_cg_static(const hs_op *A, hs_dtype dtype, const void *b, void *x, double tol, int maxit,
                        const hs_opts *opts, void *stream, hs_result *res, double *hist);
+
+/* ---- batched solves -------------------------------------------------------
+ * Many independent systems (grids of any size and dimension, CG or BiCGStab
+ * each) solved by ONE persistent cooperative kernel, replayed as a CUDA graph.
+ * Not in the paper (which solves one system per run); it keeps the GPU full
+ * when each system alone is too small to.  The library splits the grid into
+ * teams: a system whose estimated work (unknowns x iterations) exceeds the
+ * planned makespan gets a team of blocks of its own; the other systems form a
+ * queue, largest first, that every block drains one system at a time once
+ * its team job (if any) is done.
+ * Every system has its own convergence test, status and iteration count, and
+ * runs exactly the iteration of hs_cg / hs_bicgstab (FP64). */
+typedef struct hs_batch hs_batch;   /* opaque, library-owned */
+
+/* ops[s] (copied; a diffusion operator's k stays borrowed) and
+ * solvers[s] in {HS_SOLVER_CG (symmetric operators), HS_SOLVER_BICGSTAB}. */
+hs_status hs_batch_create(int nsys, const hs_op *const *ops, const int *solvers, hs_batch **out);
+void hs_batch_destroy(hs_batch *batch);
+/* Device workspace bytes for hs_batch_solve (plans the teams on first use). */
+hs_status hs_batch_workspace_size(hs_batch *batch, size_t *bytes);
+/* b[s], x[s]: host arrays of nsys FP64 device pointers (x: initial guess in,
+ * solution out).  res: host array of nsys results (true_rel_res = -1).
+ * Returns HS_OK unless a system timed out or the launch failed; per-system
+ * breakdowns and non-convergence are reported in res[s].status.  Calls on one
+ * batch object are serialised by the library; the captured graph is reused
+ * while ws and stream stay the same. */
+hs_status hs_batch_solve(hs_batch *batch, const double *const *b, double *const *x, double tol,
+                         int maxit, const hs_opts *opts, void *ws, size_t ws_bytes, void *stream,
+                         hs_result *res);
+/* Introspection: 1 if the last solve replayed a CUDA graph; the grid size;
+ * the team size (blocks) of every system. */
+int hs_batch_graph_used(const hs_batch *batch);
+int hs_batch_grid(const hs_batch *batch);
+hs_status hs_batch_team_sizes(const hs_batch *batch, int *teams);
 
 /* Thread-local message describing the last non-OK status (never NULL). */
 const char *hs_last_error(void);

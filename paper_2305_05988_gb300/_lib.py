@@ -39,7 +39,8 @@ class hs_opts(ctypes.Structure):
                 ("timeout_s", ctypes.c_double),
                 ("inner_tol", ctypes.c_double),
                 ("inner_solver", ctypes.c_int),
-                ("inner_maxit", ctypes.c_int)]
+                ("inner_maxit", ctypes.c_int),
+                ("use_graph", ctypes.c_int)]
 
 
 class hs_result(ctypes.Structure):
@@ -81,6 +82,14 @@ SIGNATURES = {
     "hs_diffusion_grad_logk": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "hs_cg_static": (_i, [_vp, _i, _vp, _vp, _d, _i, ctypes.POINTER(hs_opts), _vp,
                           ctypes.POINTER(hs_result), ctypes.POINTER(_d)]),
+    "hs_batch_create": (_i, [_i, ctypes.POINTER(_vp), ctypes.POINTER(_i), ctypes.POINTER(_vp)]),
+    "hs_batch_destroy": (None, [_vp]),
+    "hs_batch_workspace_size": (_i, [_vp, ctypes.POINTER(_sz)]),
+    "hs_batch_solve": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _d, _i, ctypes.POINTER(hs_opts), _vp, _sz,
+                            _vp, ctypes.POINTER(hs_result)]),
+    "hs_batch_graph_used": (_i, [_vp]),
+    "hs_batch_grid": (_i, [_vp]),
+    "hs_batch_team_sizes": (_i, [_vp, ctypes.POINTER(_i)]),
     "hs_last_error": (ctypes.c_char_p, []),
     "hs_version": (ctypes.c_char_p, []),
 }

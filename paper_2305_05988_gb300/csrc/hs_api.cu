@@ -73,6 +73,7 @@ static hs_opts default_opts() {
   o.inner_tol = 1e-5;
   o.inner_solver = HS_SOLVER_CG;
   o.inner_maxit = 10000;
+  o.use_graph = 1;
   return o;
 }
 

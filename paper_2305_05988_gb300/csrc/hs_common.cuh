@@ -134,29 +134,54 @@ struct Ctrl {
 
 static_assert(sizeof(Ctrl) <= 512, "Ctrl must fit its 512-byte slot");
 
-// Grid reduce-barrier.  Every block contributes NS partial sums (already
-// block-reduced, valid in thread 0), the last block to arrive sums all
-// partials in block-index order (so the result does not depend on arrival
-// order), publishes them in ctrl->scal and releases the others.  All threads
-// of all blocks return the same NS doubles in `out`.  Returns false if the
-// wait ran out (ctrl->status is then DS_TIMEOUT) or another block flagged an
-// error; the caller must then leave the kernel.
+// A team is the set of blocks that solve one system together: rank and size
+// within the team, and the team's own control block and partial-sum slots.
+// A standalone solve uses the whole grid as one team; the batched solver runs
+// many teams (one per large system, single-block teams for small ones) in
+// one cooperative launch.
+struct Team {
+  int rank;
+  int size;
+  Ctrl* ctrl;
+  double* partials;   // size * NS doubles
+  __device__ __forceinline__ long long tid() const { return (long long)rank * blockDim.x + threadIdx.x; }
+  __device__ __forceinline__ long long stride() const { return (long long)size * blockDim.x; }
+  __device__ __forceinline__ bool lead() const { return rank == 0 && threadIdx.x == 0; }
+};
+
+__device__ __forceinline__ Team grid_team(Ctrl* ctrl, double* partials) {
+  Team t;
+  t.rank = blockIdx.x;
+  t.size = gridDim.x;
+  t.ctrl = ctrl;
+  t.partials = partials;
+  return t;
+}
+
+// Team reduce-barrier.  Every block of the team contributes NS partial sums
+// (already block-reduced, valid in thread 0), the last block to arrive sums
+// all partials in rank order (so the result does not depend on arrival order),
+// publishes them in ctrl->scal and releases the others.  All threads of all
+// team blocks return the same NS doubles in `out`.  Returns false if the wait
+// ran out (ctrl->status is then DS_TIMEOUT) or another block flagged an error;
+// the caller must then stop working on this team's solve.
 //
-// Requires a cooperative launch (all blocks co-resident).  `partials` holds
-// gridDim.x * NS doubles; `sh` at least 32 * NS + 2 doubles of shared memory.
+// All blocks of the team must be co-resident (cooperative launch).  `sh` needs
+// 32 * NS doubles of shared memory.
 template <int NS>
-__device__ bool grid_reduce(Ctrl* ctrl, double* partials, const double (&mine)[NS],
-                            double (&out)[NS], double* sh) {
+__device__ bool team_reduce(const Team& tm, const double (&mine)[NS], double (&out)[NS], double* sh) {
   __shared__ int s_last;
   __shared__ int s_ok;
+  Ctrl* ctrl = tm.ctrl;
+  double* partials = tm.partials;
   const int tid = threadIdx.x;
   if (tid == 0) {
     unsigned g = ld_acquire(&ctrl->gen);
 #pragma unroll
-    for (int s = 0; s < NS; s++) partials[(size_t)blockIdx.x * NS + s] = mine[s];
+    for (int s = 0; s < NS; s++) partials[(size_t)tm.rank * NS + s] = mine[s];
     __threadfence();
     unsigned arrived = atomicAdd(&ctrl->count, 1u);
-    s_last = (arrived == gridDim.x - 1);
+    s_last = (arrived == (unsigned)tm.size - 1);
     s_ok = 1;
     if (!s_last) {
       unsigned long long t0 = global_ns();
@@ -182,7 +207,7 @@ __device__ bool grid_reduce(Ctrl* ctrl, double* partials, const double (&mine)[N
     double acc[NS];
 #pragma unroll
     for (int s = 0; s < NS; s++) acc[s] = 0.0;
-    for (int b = tid; b < (int)gridDim.x; b += blockDim.x) {
+    for (int b = tid; b < tm.size; b += blockDim.x) {
 #pragma unroll
       for (int s = 0; s < NS; s++) acc[s] += __ldcg(&partials[(size_t)b * NS + s]);
     }
@@ -209,10 +234,20 @@ __device__ bool grid_reduce(Ctrl* ctrl, double* partials, const double (&mine)[N
   return true;
 }
 
-// Plain grid barrier (no data).
-__device__ __forceinline__ bool grid_sync(Ctrl* ctrl, double* partials, double* sh) {
+// Whole-grid forms used by the standalone solver kernels.
+template <int NS>
+__device__ __forceinline__ bool grid_reduce(Ctrl* ctrl, double* partials, const double (&mine)[NS],
+                                            double (&out)[NS], double* sh) {
+  return team_reduce<NS>(grid_team(ctrl, partials), mine, out, sh);
+}
+
+// Plain barriers (no data).
+__device__ __forceinline__ bool team_sync(const Team& tm, double* sh) {
   double z[1] = {0.0}, o[1];
-  return grid_reduce<1>(ctrl, partials, z, o, sh);
+  return team_reduce<1>(tm, z, o, sh);
+}
+__device__ __forceinline__ bool grid_sync(Ctrl* ctrl, double* partials, double* sh) {
+  return team_sync(grid_team(ctrl, partials), sh);
 }
 
 }  // namespace hs

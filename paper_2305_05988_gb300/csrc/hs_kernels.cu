@@ -12,75 +12,9 @@
 #include <type_traits>
 
 #include "hs_internal.h"
+#include "hs_krylov.cuh"
 
 namespace hs {
-
-// Global index / stride helpers for grid-stride element loops.
-__device__ __forceinline__ long long gtid() { return (long long)blockIdx.x * blockDim.x + threadIdx.x; }
-__device__ __forceinline__ long long gstride() { return (long long)gridDim.x * blockDim.x; }
-
-template <typename T>
-__device__ __forceinline__ T ldcg(const T* p) {
-  return __ldcg(p);
-}
-
-__device__ __forceinline__ bool finite_d(double v) { return isfinite(v); }
-
-// Writes the final solver outcome (block 0, thread 0 only).
-__device__ __forceinline__ void finish(Ctrl* c, int status, int iters, double rel) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    c->iters = iters;
-    c->rel_res = rel;
-    atomicCAS(&c->status, 0, status);
-  }
-}
-
-// ===========================================================================
-// Common sinks
-// ===========================================================================
-
-// y = A x (scaled operator times sigma).
-template <typename T, int OPK, int NDIM>
-struct SpmvSink {
-  Coef<T> cf;
-  Geom g;
-  T sigma;
-  T* y;
-  using Raw = OpRaw<T, OPK>;
-  __device__ __forceinline__ Raw fetch(long long idx, int i, int j, int k) const {
-    return op_fetch<T, OPK, NDIM>(cf, g, idx, i, j, k);
-  }
-  __device__ __forceinline__ void operator()(long long idx, const Nbr<T>& nb, const Raw& o, int, int, int) {
-    T v = op_apply<T, OPK, NDIM>(cf, o, nb);
-    if (OPK != OP_VARK) v *= sigma;
-    y[idx] = v;
-  }
-};
-
-// r = b - A x, accumulating ||r||^2 and ||b||^2.
-template <typename T, int OPK, int NDIM>
-struct ResidualSink {
-  Coef<T> cf;
-  Geom g;
-  T sigma;
-  const T* b;
-  T* r;
-  double acc[2];
-  struct Raw {
-    OpRaw<T, OPK> o;
-    T b;
-  };
-  __device__ __forceinline__ Raw fetch(long long idx, int i, int j, int k) const {
-    return Raw{op_fetch<T, OPK, NDIM>(cf, g, idx, i, j, k), __ldg(b + idx)};
-  }
-  __device__ __forceinline__ void operator()(long long idx, const Nbr<T>& nb, const Raw& q, int, int, int) {
-    T v = op_apply<T, OPK, NDIM>(cf, q.o, nb);
-    T rv = (OPK == OP_VARK) ? q.b - v : fma(-sigma, v, q.b);
-    r[idx] = rv;
-    acc[0] += widen(rv) * widen(rv);
-    acc[1] += widen(q.b) * widen(q.b);
-  }
-};
 
 // ===========================================================================
 // SpMV and residual (one work item per block)
@@ -171,12 +105,6 @@ __global__ void k_vark_setup(Geom g, int ndim, const K* __restrict__ kk, double 
     D[idx] = invert ? (T)(1.0 / d) : (T)d;
   }
 }
-
-// Elementwise passes process ILP elements per thread per round: all loads of
-// a round are issued before any arithmetic or store, so several memory
-// requests are in flight per thread.  The element -> thread assignment and
-// the per-thread accumulation order are fixed by the launch shape.
-constexpr int ILP = 4;
 
 // ===========================================================================
 // Jacobi (section 3.1), out of place, persistent.
@@ -292,463 +220,18 @@ __global__ void __launch_bounds__(512) k_jacobi(JacArgs<T> a) {
   finish(a.cm.ctrl, status, iters, rel);
 }
 
-// ===========================================================================
-// CG: classical Hestenes-Stiefel (section 3.2) in two fused passes.
-//   pass 1 (stencil):  p = r + beta p_old (on the fly, halo included),
-//                      w = A p / sigma, partial p.w
-//   pass 2 (elements): x += alpha p, r -= alpha A p, partial r.r
-// p is double-buffered so that halo reads of p_old never race with stores.
-// ===========================================================================
-
-template <typename T>
-struct CgArgs {
-  Geom g;
-  Tiling tl;
-  Coef<T> cf;
-  double sigma;   // A = sigma * (scaled operator)
-  const T* b;
-  T* x;
-  T* r;
-  T* p0;
-  T* p1;
-  T* w;
-  Common cm;
-  int maxit;
-  double tol;
-};
-
-// p = r + beta p_old (or p = r), stored for owned nodes.
-template <typename T>
-struct PUpdateSrc {
-  const T* r;
-  const T* pold;
-  T* pnew;
-  T beta;
-  bool first;
-  struct Raw {
-    T r, p;
-  };
-  __device__ __forceinline__ Raw fetch(long long idx) const {
-    Raw q;
-    q.r = __ldcg(r + idx);
-    q.p = first ? T(0) : __ldcg(pold + idx);
-    return q;
-  }
-  __device__ __forceinline__ T make(const Raw& q, long long idx, bool own) const {
-    T pv = first ? q.r : fma(beta, q.p, q.r);
-    if (own) pnew[idx] = pv;
-    return pv;
-  }
-};
-
-// w = A p / sigma, accumulating p.w.
-template <typename T, int OPK, int NDIM>
-struct ApDotSink {
-  Coef<T> cf;
-  Geom g;
-  T* w;
-  double acc[1];
-  using Raw = OpRaw<T, OPK>;
-  __device__ __forceinline__ Raw fetch(long long idx, int i, int j, int k) const {
-    return op_fetch<T, OPK, NDIM>(cf, g, idx, i, j, k);
-  }
-  __device__ __forceinline__ void operator()(long long idx, const Nbr<T>& nb, const Raw& o, int, int, int) {
-    T wv = op_apply<T, OPK, NDIM>(cf, o, nb);
-    w[idx] = wv;
-    acc[0] += widen(nb.c) * widen(wv);
-  }
-};
-
 template <typename T, int OPK, int NDIM>
 __global__ void __launch_bounds__(512) k_cg(CgArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double sh[32 * MAX_SCAL];
-  T* sm = reinterpret_cast<T*>(smraw);
-  const long long N = a.g.N;
-  const T sig = (T)a.sigma;
-
-  // r = b - A x ; ||r||^2, ||b||^2
-  ResidualSink<T, OPK, NDIM> rsink{a.cf, a.g, sig, a.b, a.r, {0.0, 0.0}};
-  {
-    LoadSrc<T, true> src{a.x};
-    for (int item = blockIdx.x; item < a.tl.items(); item += gridDim.x)
-      zmarch_item<T, NDIM>(a.g, a.tl, item, sm, src, rsink);
-  }
-  block_sum<2>(rsink.acc, sh);
-  double s2[2];
-  if (!grid_reduce<2>(a.cm.ctrl, a.cm.partials, rsink.acc, s2, sh)) return;
-  double rr = s2[0];
-  const double bb = s2[1];
-  if (bb == 0.0) {
-    for (long long i = gtid(); i < N; i += gstride()) a.x[i] = T(0);
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.cm.hist[0] = 0.0;
-    finish(a.cm.ctrl, DS_CONVERGED, 0, 0.0);
-    return;
-  }
-  double rel = sqrt(rr / bb);
-  if (blockIdx.x == 0 && threadIdx.x == 0) a.cm.hist[0] = rel;
-  if (rel <= a.tol || a.maxit == 0) {
-    finish(a.cm.ctrl, rel <= a.tol ? DS_CONVERGED : DS_MAXIT, 0, rel);
-    return;
-  }
-
-  double beta = 0.0;
-  bool first = true;
-  int it = 0, status = DS_MAXIT;
-  const long long st = gstride();
-  while (it < a.maxit) {
-    it++;
-    const T* pold = (it & 1) ? a.p0 : a.p1;
-    T* pnew = (it & 1) ? a.p1 : a.p0;
-    // ---- pass 1: p = r + beta p_old ; w = A p / sigma ; p.w
-    PUpdateSrc<T> src{a.r, pold, pnew, (T)beta, first};
-    ApDotSink<T, OPK, NDIM> sink{a.cf, a.g, a.w, {0.0}};
-    for (int item = blockIdx.x; item < a.tl.items(); item += gridDim.x)
-      zmarch_item<T, NDIM>(a.g, a.tl, item, sm, src, sink);
-    block_sum<1>(sink.acc, sh);
-    double pw[1];
-    if (!grid_reduce<1>(a.cm.ctrl, a.cm.partials, sink.acc, pw, sh)) return;
-    if (!(pw[0] > 0.0) || !finite_d(pw[0])) {
-      status = finite_d(pw[0]) ? DS_BREAKDOWN : DS_NONFINITE;
-      break;
-    }
-    const double ar = rr / pw[0];           // multiplies w = A p / sigma
-    const double axs = ar / a.sigma;        // multiplies p
-    const T tar = (T)ar, tax = (T)axs;
-    // ---- pass 2: x += alpha p ; r -= alpha A p ; r.r
-    double acc1[1] = {0.0};
-    long long i = gtid();
-    for (; i + (ILP - 1) * st < N; i += ILP * st) {
-      T pv[ILP], wv[ILP], xv[ILP], rv[ILP];
-#pragma unroll
-      for (int u = 0; u < ILP; u++) {
-        const long long q = i + u * st;
-        pv[u] = ldcg(pnew + q);
-        wv[u] = ldcg(a.w + q);
-        xv[u] = ldcg(a.x + q);
-        rv[u] = ldcg(a.r + q);
-      }
-#pragma unroll
-      for (int u = 0; u < ILP; u++) {
-        const long long q = i + u * st;
-        xv[u] = fma(tax, pv[u], xv[u]);
-        rv[u] = fma(-tar, wv[u], rv[u]);
-        a.x[q] = xv[u];
-        a.r[q] = rv[u];
-        acc1[0] += widen(rv[u]) * widen(rv[u]);
-      }
-    }
-    for (; i < N; i += st) {
-      T xv = fma(tax, ldcg(pnew + i), ldcg(a.x + i));
-      T rv = fma(-tar, ldcg(a.w + i), ldcg(a.r + i));
-      a.x[i] = xv;
-      a.r[i] = rv;
-      acc1[0] += widen(rv) * widen(rv);
-    }
-    block_sum<1>(acc1, sh);
-    double rn[1];
-    if (!grid_reduce<1>(a.cm.ctrl, a.cm.partials, acc1, rn, sh)) return;
-    rel = sqrt(rn[0] / bb);
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.cm.hist[it] = rel;
-    if (!finite_d(rel)) {
-      status = DS_NONFINITE;
-      break;
-    }
-    if (rel <= a.tol) {
-      status = DS_CONVERGED;
-      break;
-    }
-    beta = rn[0] / rr;
-    rr = rn[0];
-    first = false;
-  }
-  finish(a.cm.ctrl, status, it, rel);
+  cg_body<T, OPK, NDIM>(a, grid_team(a.cm.ctrl, a.cm.partials), reinterpret_cast<T*>(smraw), sh);
 }
-
-// ===========================================================================
-// BiCGStab with Algorithm 2's normalised shadow residual and restart rule,
-// three fused passes per iteration:
-//   pass 1 (stencil):  p = r + beta (p_old - omega v_old) (or p = r after a
-//                      start/restart, which also stores r' = r/||r||),
-//                      v = A p / sigma, partial v.r'
-//   pass 2 (stencil):  s = r - alpha A p (on the fly), t = A s / sigma,
-//                      partials s.s, t.s, t.t
-//   pass 3 (elements): x += alpha p + omega s, r = s - omega A s,
-//                      partials r.r', r.r
-// ===========================================================================
-
-template <typename T>
-struct BiArgs {
-  Geom g;
-  Tiling tl;
-  Coef<T> cf;
-  double sigma;
-  const T* b;
-  T* x;
-  T* r;
-  T* rs;
-  T* p0;
-  T* p1;
-  T* v0;
-  T* v1;
-  T* s;
-  T* t;
-  Common cm;
-  int maxit;
-  double tol;
-  double reps;
-};
-
-// p = r + beta (p_old - omega sigma v_old), or p = r on (re)start.
-template <typename T>
-struct BiPSrc {
-  const T* r;
-  const T* pold;
-  const T* vold;
-  T* pnew;
-  T beta, ws;
-  bool restart;
-  struct Raw {
-    T r, p, v;
-  };
-  __device__ __forceinline__ Raw fetch(long long idx) const {
-    Raw q;
-    q.r = __ldcg(r + idx);
-    if (restart) {
-      q.p = T(0);
-      q.v = T(0);
-    } else {
-      q.p = __ldcg(pold + idx);
-      q.v = __ldcg(vold + idx);
-    }
-    return q;
-  }
-  __device__ __forceinline__ T make(const Raw& q, long long idx, bool own) const {
-    T pv = restart ? q.r : fma(beta, fma(-ws, q.v, q.p), q.r);
-    if (own) pnew[idx] = pv;
-    return pv;
-  }
-};
-
-// v = A p / sigma; r' = r/||r|| stored on (re)start; partial v.r'.
-template <typename T, int OPK, int NDIM>
-struct BiVSink {
-  Coef<T> cf;
-  Geom g;
-  const T* r;
-  T* rs;
-  T* vnew;
-  T inv_rn;
-  bool restart;
-  double acc[1];
-  struct Raw {
-    OpRaw<T, OPK> o;
-    T q;   // r (restart) or r'
-  };
-  __device__ __forceinline__ Raw fetch(long long idx, int i, int j, int k) const {
-    return Raw{op_fetch<T, OPK, NDIM>(cf, g, idx, i, j, k), restart ? __ldcg(r + idx) : __ldcg(rs + idx)};
-  }
-  __device__ __forceinline__ void operator()(long long idx, const Nbr<T>& nb, const Raw& q, int, int, int) {
-    T vv = op_apply<T, OPK, NDIM>(cf, q.o, nb);
-    vnew[idx] = vv;
-    T rsv = q.q;
-    if (restart) {
-      rsv = q.q * inv_rn;
-      rs[idx] = rsv;
-    }
-    acc[0] += widen(vv) * widen(rsv);
-  }
-};
-
-// s = r - alpha sigma v, stored for owned nodes.
-template <typename T>
-struct BiSSrc {
-  const T* r;
-  const T* v;
-  T* s;
-  T as;
-  struct Raw {
-    T r, v;
-  };
-  __device__ __forceinline__ Raw fetch(long long idx) const { return Raw{__ldcg(r + idx), __ldcg(v + idx)}; }
-  __device__ __forceinline__ T make(const Raw& q, long long idx, bool own) const {
-    T sv = fma(-as, q.v, q.r);
-    if (own) s[idx] = sv;
-    return sv;
-  }
-};
-
-// t = A s / sigma; partials s.s, t.s, t.t.
-template <typename T, int OPK, int NDIM>
-struct BiTSink {
-  Coef<T> cf;
-  Geom g;
-  T* t;
-  double acc[3];
-  using Raw = OpRaw<T, OPK>;
-  __device__ __forceinline__ Raw fetch(long long idx, int i, int j, int k) const {
-    return op_fetch<T, OPK, NDIM>(cf, g, idx, i, j, k);
-  }
-  __device__ __forceinline__ void operator()(long long idx, const Nbr<T>& nb, const Raw& o, int, int, int) {
-    T tv = op_apply<T, OPK, NDIM>(cf, o, nb);
-    t[idx] = tv;
-    const double sv = widen(nb.c), td = widen(tv);
-    acc[0] += sv * sv;
-    acc[1] += td * sv;
-    acc[2] += td * td;
-  }
-};
 
 template <typename T, int OPK, int NDIM>
 __global__ void __launch_bounds__(512) k_bicgstab(BiArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double sh[32 * MAX_SCAL];
-  T* sm = reinterpret_cast<T*>(smraw);
-  const long long N = a.g.N;
-  const T sig = (T)a.sigma;
-
-  ResidualSink<T, OPK, NDIM> rsink{a.cf, a.g, sig, a.b, a.r, {0.0, 0.0}};
-  {
-    LoadSrc<T, true> src{a.x};
-    for (int item = blockIdx.x; item < a.tl.items(); item += gridDim.x)
-      zmarch_item<T, NDIM>(a.g, a.tl, item, sm, src, rsink);
-  }
-  block_sum<2>(rsink.acc, sh);
-  double s2[2];
-  if (!grid_reduce<2>(a.cm.ctrl, a.cm.partials, rsink.acc, s2, sh)) return;
-  double brr = s2[0];
-  const double bb = s2[1];
-  if (bb == 0.0) {
-    for (long long i = gtid(); i < N; i += gstride()) a.x[i] = T(0);
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.cm.hist[0] = 0.0;
-    finish(a.cm.ctrl, DS_CONVERGED, 0, 0.0);
-    return;
-  }
-  double rel = sqrt(brr / bb);
-  if (blockIdx.x == 0 && threadIdx.x == 0) a.cm.hist[0] = rel;
-  if (rel <= a.tol || a.maxit == 0) {
-    finish(a.cm.ctrl, rel <= a.tol ? DS_CONVERGED : DS_MAXIT, 0, rel);
-    return;
-  }
-
-  double alpha_n = sqrt(brr);   // r . r' with r' = r / ||r||
-  double inv_rn = 1.0 / sqrt(brr);
-  bool restart = true;          // p = r and r' = r/||r|| in the next pass 1
-  double beta = 0.0, omega = 0.0;
-  int it = 0, status = DS_MAXIT, restarts = 0;
-  const long long st = gstride();
-  while (it < a.maxit) {
-    it++;
-    const T* pold = (it & 1) ? a.p0 : a.p1;
-    T* pnew = (it & 1) ? a.p1 : a.p0;
-    const T* vold = (it & 1) ? a.v0 : a.v1;
-    T* vnew = (it & 1) ? a.v1 : a.v0;
-    // ---- pass 1
-    double ad[1];
-    {
-      BiPSrc<T> src{a.r, pold, vold, pnew, (T)beta, (T)(omega * a.sigma), restart};
-      BiVSink<T, OPK, NDIM> sink{a.cf, a.g, a.r, a.rs, vnew, (T)inv_rn, restart, {0.0}};
-      for (int item = blockIdx.x; item < a.tl.items(); item += gridDim.x)
-        zmarch_item<T, NDIM>(a.g, a.tl, item, sm, src, sink);
-      block_sum<1>(sink.acc, sh);
-      if (!grid_reduce<1>(a.cm.ctrl, a.cm.partials, sink.acc, ad, sh)) return;
-    }
-    const double alpha_d = a.sigma * ad[0];
-    if (alpha_d == 0.0 || !finite_d(alpha_d)) {
-      status = finite_d(alpha_d) ? DS_BREAKDOWN : DS_NONFINITE;
-      break;
-    }
-    const double alpha = alpha_n / alpha_d;
-    // ---- pass 2
-    double st3[3];
-    {
-      BiSSrc<T> src{a.r, vnew, a.s, (T)(alpha * a.sigma)};
-      BiTSink<T, OPK, NDIM> sink{a.cf, a.g, a.t, {0.0, 0.0, 0.0}};
-      for (int item = blockIdx.x; item < a.tl.items(); item += gridDim.x)
-        zmarch_item<T, NDIM>(a.g, a.tl, item, sm, src, sink);
-      block_sum<3>(sink.acc, sh);
-      if (!grid_reduce<3>(a.cm.ctrl, a.cm.partials, sink.acc, st3, sh)) return;
-    }
-    const double srel = sqrt(st3[0] / bb);
-    if (srel <= a.tol) {
-      const T ta = (T)alpha;
-      for (long long i = gtid(); i < N; i += st) a.x[i] = fma(ta, ldcg(pnew + i), ldcg(a.x + i));
-      if (blockIdx.x == 0 && threadIdx.x == 0) a.cm.hist[it] = srel;
-      rel = srel;
-      status = DS_CONVERGED;
-      break;
-    }
-    const double ts = a.sigma * st3[1], tt = a.sigma * a.sigma * st3[2];
-    if (tt == 0.0 || !finite_d(tt) || !finite_d(ts)) {
-      status = finite_d(tt) && finite_d(ts) ? DS_BREAKDOWN : DS_NONFINITE;
-      break;
-    }
-    omega = ts / tt;
-    if (omega == 0.0) {
-      status = DS_BREAKDOWN;
-      break;
-    }
-    // ---- pass 3
-    const T ta = (T)alpha, tom = (T)omega, toms = (T)(omega * a.sigma);
-    double acc4[2] = {0.0, 0.0};
-    long long i = gtid();
-    for (; i + (ILP - 1) * st < N; i += ILP * st) {
-      T sv[ILP], pv[ILP], xv[ILP], tv[ILP], rsv[ILP];
-#pragma unroll
-      for (int u = 0; u < ILP; u++) {
-        const long long q = i + u * st;
-        sv[u] = ldcg(a.s + q);
-        pv[u] = ldcg(pnew + q);
-        xv[u] = ldcg(a.x + q);
-        tv[u] = ldcg(a.t + q);
-        rsv[u] = ldcg(a.rs + q);
-      }
-#pragma unroll
-      for (int u = 0; u < ILP; u++) {
-        const long long q = i + u * st;
-        T xn = fma(tom, sv[u], fma(ta, pv[u], xv[u]));
-        T rn = fma(-toms, tv[u], sv[u]);
-        a.x[q] = xn;
-        a.r[q] = rn;
-        acc4[0] += widen(rn) * widen(rsv[u]);
-        acc4[1] += widen(rn) * widen(rn);
-      }
-    }
-    for (; i < N; i += st) {
-      T sv = ldcg(a.s + i);
-      T xn = fma(tom, sv, fma(ta, ldcg(pnew + i), ldcg(a.x + i)));
-      T rn = fma(-toms, ldcg(a.t + i), sv);
-      a.x[i] = xn;
-      a.r[i] = rn;
-      acc4[0] += widen(rn) * widen(ldcg(a.rs + i));
-      acc4[1] += widen(rn) * widen(rn);
-    }
-    block_sum<2>(acc4, sh);
-    double rn2[2];
-    if (!grid_reduce<2>(a.cm.ctrl, a.cm.partials, acc4, rn2, sh)) return;
-    rel = sqrt(rn2[1] / bb);
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.cm.hist[it] = rel;
-    if (!finite_d(rel) || !finite_d(rn2[0])) {
-      status = DS_NONFINITE;
-      break;
-    }
-    if (rel <= a.tol) {
-      status = DS_CONVERGED;
-      break;
-    }
-    if (a.reps > 0.0 && sqrt(fabs(rn2[0])) < a.reps) {
-      restart = true;
-      alpha_n = sqrt(rn2[1]);
-      inv_rn = 1.0 / sqrt(rn2[1]);
-      restarts++;
-    } else {
-      restart = false;
-      beta = rn2[0] / (alpha_d * omega);
-      alpha_n = rn2[0];
-    }
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) a.cm.ctrl->restarts = restarts;
-  finish(a.cm.ctrl, status, it, rel);
+  bicgstab_body<T, OPK, NDIM>(a, grid_team(a.cm.ctrl, a.cm.partials), reinterpret_cast<T*>(smraw), sh);
 }
 
 // ===========================================================================
@@ -828,23 +311,6 @@ ConstRow const_row(const hs_op* A) {
   return c;
 }
 
-// Scaled coefficients: divide by sigma = -xu so that xu becomes exactly -1.
-template <typename T>
-static Coef<T> scaled_coef(const hs_op* A, double* sigma) {
-  Coef<T> cf = {};
-  ConstRow c = const_row(A);
-  double s = -c.xu;
-  *sigma = s;
-  cf.d = (T)(c.d / s);
-  cf.xl = (T)(c.xl / s);
-  cf.xu = (T)(-1.0);
-  cf.yl = (T)(c.yl / s);
-  cf.yu = (T)(c.yu / s);
-  cf.zl = (T)(c.zl / s);
-  cf.zu = (T)(c.zu / s);
-  return cf;
-}
-
 // Jacobi coefficients g = -a/a_ii.
 template <typename T>
 static Coef<T> jacobi_coef(const hs_op* A, T* invd, double* d2) {
@@ -899,17 +365,6 @@ hs_status setup_vark(const hs_op* A, hs_dtype dt, void* D, void* ax, void* ay, v
   return e == cudaSuccess ? HS_OK : cuda_fail(e, "variable-coefficient setup launch");
 }
 
-static int rows_per_tile(const Geom& g) {
-  // 2-D grids are small: more, shorter tiles; 3-D: 8 rows (256 threads).
-  if (g.nz == 1) return g.ny >= 64 ? 8 : 4;
-  return 8;
-}
-
-template <typename T>
-static size_t slab_bytes(int by) {
-  return (size_t)2 * (by + 2) * (BX + 2) * sizeof(T);
-}
-
 // ---- dispatch over (element type, operator kind, dimensionality) ---------
 template <typename T_, int OPK_, int NDIM_>
 struct Tag {
@@ -941,22 +396,6 @@ static hs_status dispatch(hs_dtype dt, int opk, int ndim, F&& f) {
 #undef HS_CASE
   set_error("unsupported operator / dtype combination");
   return HS_ERR_INVALID;
-}
-
-// Operator coefficients for stencil kernels (scaled form, or var-k arrays).
-template <typename T>
-static Coef<T> op_coef(const hs_op* A, const void* D, const void* ax, const void* ay, const void* az,
-                       double* sigma) {
-  if (A->kind == KIND_DIFFUSION) {
-    Coef<T> cf = {};
-    cf.D = (const T*)D;
-    cf.ax = (const T*)ax;
-    cf.ay = (const T*)ay;
-    cf.az = (const T*)az;
-    *sigma = 1.0;
-    return cf;
-  }
-  return scaled_coef<T>(A, sigma);
 }
 
 // Variable-coefficient SpMV without a workspace: face couplings are formed

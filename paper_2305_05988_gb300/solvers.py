@@ -161,12 +161,13 @@ def make_opts(**kw) -> _lib.hs_opts:
     o.inner_tol = 1e-5
     o.inner_solver = _lib.HS_SOLVER_CG
     o.inner_maxit = 10000
+    o.use_graph = 1
     for k, v in kw.items():
         if k == "gs_mode" and isinstance(v, str):
             v = _GS_MODES[v]
         if k == "inner_solver" and isinstance(v, str):
             v = {"cg": _lib.HS_SOLVER_CG, "bicgstab": _lib.HS_SOLVER_BICGSTAB}[v]
-        if k == "true_residual":
+        if k in ("true_residual", "use_graph"):
             v = int(bool(v))
         if not hasattr(o, k):
             raise TypeError("unknown solver option %r" % k)
@@ -325,3 +326,76 @@ def diffusion_solve(logk: torch.Tensor, f: torch.Tensor, shape, tol: float = 1e-
                     maxit: int = 100000) -> torch.Tensor:
     """Differentiable solve of -div(exp(logk) grad u) = f (float64 CUDA tensors)."""
     return DiffusionSolve.apply(logk, f, tuple(shape), tol, mixed, maxit)
+
+
+class Batch:
+    """Many independent systems solved by one persistent kernel (CUDA graph).
+
+    ops: list of Operators; solvers: list of "cg" / "bicgstab" (one per system).
+    """
+
+    def __init__(self, ops, solvers):
+        lib = _lib.load()
+        if len(ops) != len(solvers) or not ops:
+            raise ValueError("need one solver per operator")
+        self.ops = list(ops)
+        self.n = len(ops)
+        code = {"cg": _lib.HS_SOLVER_CG, "bicgstab": _lib.HS_SOLVER_BICGSTAB}
+        arr_ops = (ctypes.c_void_p * self.n)(*[o._op.value for o in self.ops])
+        arr_sol = (ctypes.c_int * self.n)(*[code[s] for s in solvers])
+        self._b = ctypes.c_void_p()
+        check(lib.hs_batch_create(self.n, arr_ops, arr_sol, ctypes.byref(self._b)), "hs_batch_create")
+        self._ws = None
+
+    def __del__(self):
+        try:
+            if self._b is not None and self._b.value:
+                _lib.load().hs_batch_destroy(self._b)
+                self._b = None
+        except Exception:
+            pass
+
+    def workspace(self, device) -> torch.Tensor:
+        size = ctypes.c_size_t()
+        with torch.cuda.device(device):
+            check(_lib.load().hs_batch_workspace_size(self._b, ctypes.byref(size)), "hs_batch_workspace_size")
+        if self._ws is None or self._ws.numel() < size.value or self._ws.device != torch.device(device):
+            self._ws = torch.empty(max(size.value, 256), dtype=torch.uint8, device=device)
+        return self._ws
+
+    @property
+    def teams(self):
+        t = (ctypes.c_int * self.n)()
+        check(_lib.load().hs_batch_team_sizes(self._b, t), "hs_batch_team_sizes")
+        return list(t)
+
+    @property
+    def graph_used(self) -> bool:
+        return bool(_lib.load().hs_batch_graph_used(self._b))
+
+    def solve(self, bs, xs=None, tol: float = 1e-8, maxit: int = 20000, stream=None, **kw):
+        """Solve A_s x_s = b_s for every system; returns (xs, infos)."""
+        if len(bs) != self.n:
+            raise ValueError("need one right-hand side per system")
+        for A, b in zip(self.ops, bs):
+            A._vec(b, "b")
+            if b.dtype != torch.float64:
+                raise TypeError("batched solves take float64 vectors")
+        xs = [torch.zeros_like(b) for b in bs] if xs is None else xs
+        for A, x in zip(self.ops, xs):
+            A._vec(x, "x")
+        dev = bs[0].device
+        opts = make_opts(**kw)
+        res = (_lib.hs_result * self.n)()
+        pb = (ctypes.c_void_p * self.n)(*[b.data_ptr() for b in bs])
+        px = (ctypes.c_void_p * self.n)(*[x.data_ptr() for x in xs])
+        with torch.cuda.device(dev):
+            ws = self.workspace(dev)
+            st = (stream or torch.cuda.current_stream(dev)).cuda_stream
+            status = _lib.load().hs_batch_solve(self._b, pb, px, float(tol), int(maxit), ctypes.byref(opts),
+                                                ctypes.c_void_p(ws.data_ptr()), ws.numel(), ctypes.c_void_p(st), res)
+        if status in (_lib.HS_ERR_INVALID, _lib.HS_ERR_CUDA, _lib.HS_ERR_WORKSPACE):
+            raise _lib.HsError(status, "hs_batch_solve")
+        infos = [SolveInfo(iters=r.iters, status=_lib.STATUS_NAMES.get(r.status, str(r.status)), status_code=r.status,
+                           rel_res=r.rel_res, true_rel_res=r.true_rel_res, restarts=r.restarts) for r in res]
+        return xs, infos
