@@ -80,6 +80,7 @@ def parse():
     p.add_argument("--timeout-s", type=float, default=2.0, help="bound on device-side waits")
     p.add_argument("--mixed-n", type=int, default=512, help="grid side of the mixed-precision comparison (0: skip)")
     p.add_argument("--adjoint-n", type=int, default=256, help="grid side of the adjoint-gradient timing (0: skip)")
+    p.add_argument("--batch-n", type=int, default=512, help="systems in the batched comparison (0: skip)")
     return p.parse_args()
 
 
@@ -411,6 +412,8 @@ def run_ours(args, rank, world, dist):
         extras["mixed_vs_fp64"] = mixed_comparison(args.mixed_n, dev, tmo)
     if rank == 0 and args.adjoint_n > 0:
         extras["adjoint"] = adjoint_timing(args.adjoint_n, dev, tmo)
+    if rank == 0 and args.batch_n > 0:
+        extras["batched"] = batch_comparison(args.batch_n, dev, tmo)
 
     # kernels launched per step: spmv 1; jacobi, cg, bicgstab: control init +
     # persistent solver + residual + finalize = 4 each; gauss-seidel: solver +
@@ -498,6 +501,59 @@ def adjoint_timing(n, dev, tmo):
                                              "loss": L.item(),
                                              "grad_logk_norm": torch.linalg.norm(logk.grad).item()}
     del logk, f, k2, u_obs
+    torch.cuda.empty_cache()
+    return out
+
+
+def batch_comparison(nsys, dev, tmo):
+    """The batched workload: nsys independent systems (2-D or 3-D, sides
+    log-uniform in [16, 256]; even systems CG on the Laplacian, odd systems
+    BiCGStab on upwind convection-diffusion with Peclet in [0.1, 1]) solved to
+    1e-8 by one persistent kernel replayed as a CUDA graph, against solving them
+    one after another with the standalone solvers."""
+    import torch
+
+    import paper_2305_05988_gb300 as hs
+    from paper_2305_05988_gb300 import inputs
+    systems = inputs.batch_systems(nsys, seed=0)
+    ops, bs, sol = [], [], []
+    for s in systems:
+        if s.solver == "cg":
+            ops.append(hs.Operator.laplacian(s.shape))
+        else:
+            ops.append(hs.Operator.upwind(s.shape, inputs.upwind_beta(s.shape, s.peclet)))
+        bs.append(torch.from_numpy(inputs.uniform_pm1(0, inputs.STREAM_BATCH_RHS + s.index, s.N)).to(dev))
+        sol.append(s.solver)
+    unknowns = sum(s.N for s in systems)
+    st = torch.cuda.Stream(dev)
+    out = {"workload": "%d systems, sides log-uniform in [16, 256], 2-D/3-D, CG (Laplacian) / BiCGStab "
+                       "(upwind, Pe in [0.1, 1]), tol 1e-8, FP64" % nsys, "unknowns": unknowns}
+    t0 = time.perf_counter()
+    batch = hs.Batch(ops, sol, autotune=True)
+    out["autotune_s"] = round(time.perf_counter() - t0, 2)
+    with torch.cuda.stream(st):
+        xs = [torch.zeros_like(b) for b in bs]
+        batch.solve(bs, xs, tol=1e-8, timeout_s=max(tmo, 20.0))   # warm-up: captures the graph
+        for x in xs:
+            x.zero_()
+        st.synchronize()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(st)
+        xs, infos = batch.solve(bs, xs, tol=1e-8, timeout_s=max(tmo, 20.0))
+        e1.record(st)
+        seq_iters = 0
+        for A, b, s in zip(ops, bs, sol):
+            fn = hs.cg if s == "cg" else hs.bicgstab
+            _, info = fn(A, b, tol=1e-8, history=False, true_residual=False, timeout_s=max(tmo, 10.0))
+            seq_iters += info.iters
+        e2.record(st)
+        st.synchronize()
+    tb, ts = e0.elapsed_time(e1), e1.elapsed_time(e2)
+    out["batched"] = {"ms": round(tb, 2), "graph": batch.graph_used, "iters_total": sum(i.iters for i in infos),
+                      "converged": sum(i.status == "OK" for i in infos), "teams_gt1": sum(t > 1 for t in batch.teams)}
+    out["sequential"] = {"ms": round(ts, 2), "iters_total": seq_iters}
+    out["speedup"] = round(ts / tb, 3)
+    del batch, xs, bs, ops
     torch.cuda.empty_cache()
     return out
 

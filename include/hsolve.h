@@ -93,6 +93,13 @@ typedef struct {
     int inner_maxit;        /* mixed precision: inner iteration cap (10000)     */
     int use_graph;          /* batched solver: replay one captured CUDA graph
                                (default 1; needs a non-default stream)          */
+    int tile_rows;          /* stencil tiles of the Jacobi / CG / BiCGStab /
+                               mixed solvers: rows of 32 nodes per tile = warps
+                               per block, 4, 8 or 16; 0 = built-in heuristic   */
+    int tile_planes;        /* z planes per work item of those tiles; 0 = the
+                               built-in cost model                             */
+    int max_blocks;         /* cap on the persistent grid (blocks); 0 = all
+                               co-resident blocks                               */
 } hs_opts;
 
 typedef struct {
@@ -267,6 +274,10 @@ hs_status hs_batch_workspace_size(hs_batch *batch, size_t *bytes);
 hs_status hs_batch_solve(hs_batch *batch, const double *const *b, double *const *x, double tol,
                          int maxit, const hs_opts *opts, void *ws, size_t ws_bytes, void *stream,
                          hs_result *res);
+/* Per-system z planes per work item (e.g. from the autotuner; 0 = cost
+ * model).  planes: host array of nsys ints.  Re-plans the batch, so call it
+ * before hs_batch_workspace_size. */
+hs_status hs_batch_set_tile_planes(hs_batch *batch, const int *planes);
 /* Introspection: 1 if the last solve replayed a CUDA graph; the grid size;
  * the team size (blocks) of every system. */
 int hs_batch_graph_used(const hs_batch *batch);

@@ -40,7 +40,10 @@ class hs_opts(ctypes.Structure):
                 ("inner_tol", ctypes.c_double),
                 ("inner_solver", ctypes.c_int),
                 ("inner_maxit", ctypes.c_int),
-                ("use_graph", ctypes.c_int)]
+                ("use_graph", ctypes.c_int),
+                ("tile_rows", ctypes.c_int),
+                ("tile_planes", ctypes.c_int),
+                ("max_blocks", ctypes.c_int)]
 
 
 class hs_result(ctypes.Structure):
@@ -87,6 +90,7 @@ SIGNATURES = {
     "hs_batch_workspace_size": (_i, [_vp, ctypes.POINTER(_sz)]),
     "hs_batch_solve": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _d, _i, ctypes.POINTER(hs_opts), _vp, _sz,
                             _vp, ctypes.POINTER(hs_result)]),
+    "hs_batch_set_tile_planes": (_i, [_vp, ctypes.POINTER(_i)]),
     "hs_batch_graph_used": (_i, [_vp]),
     "hs_batch_grid": (_i, [_vp]),
     "hs_batch_team_sizes": (_i, [_vp, ctypes.POINTER(_i)]),

@@ -106,6 +106,8 @@ static bool merge_opts(const hs_opts* in, hs_opts* out) {
     return false;
   }
   if (out->inner_maxit < 1 || out->inner_maxit > 100000000) out->inner_maxit = 10000;
+  if (out->tile_planes < 0) out->tile_planes = 0;
+  if (out->max_blocks < 0) out->max_blocks = 0;
   return true;
 }
 

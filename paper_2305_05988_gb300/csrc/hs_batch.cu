@@ -163,6 +163,7 @@ struct hs_batch {
   std::vector<int> job_off;
   std::vector<hs::BatchJob> jobs;
   std::vector<int> queue;             // single-block systems, largest first
+  std::vector<int> tile_planes;       // per system, 0 = cost model
   std::vector<size_t> sys_off;        // workspace offset of each system
   size_t tables_bytes = 0;
   size_t ws_total = 0;
@@ -267,7 +268,7 @@ static void make_plan(hs_batch* B, int grid, double tol) {
       p.team = 1;
       B->queue.push_back(s);   // largest first
     }
-    p.tl = choose_tiling(p.g, BATCH_BY, p.team, true);
+    p.tl = choose_tiling(p.g, BATCH_BY, p.team, true, B->tile_planes.empty() ? 0 : B->tile_planes[s]);
   }
   B->job_off.assign(grid + 1, 0);
   B->jobs.clear();
@@ -579,6 +580,22 @@ extern "C" hs_status hs_batch_solve(hs_batch* B, const double* const* b, double*
   if (worst == HS_ERR_TIMEOUT) set_error("a device-side wait ran out in the batched solve");
   if (worst == HS_ERR_CUDA) set_error("a system of the batch ended without a status");
   return worst;
+}
+
+extern "C" hs_status hs_batch_set_tile_planes(hs_batch* B, const int* planes) {
+  if (!B || !planes) {
+    set_error("NULL argument");
+    return HS_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> lock(B->mu);
+  B->tile_planes.assign(planes, planes + B->nsys);
+  for (int& v : B->tile_planes) v = std::max(0, v);
+  B->grid = 0;   // re-plan on next use
+  if (B->exec) {
+    cudaGraphExecDestroy(B->exec);
+    B->exec = nullptr;
+  }
+  return HS_OK;
 }
 
 extern "C" int hs_batch_graph_used(const hs_batch* B) { return B ? B->graph_used : 0; }

@@ -261,7 +261,7 @@ int sm_count() {
   return g_sm_count;
 }
 
-Tiling choose_tiling(const Geom& g, int by, int grid, bool src_expensive) {
+Tiling choose_tiling(const Geom& g, int by, int grid, bool src_expensive, int planes) {
   Tiling t;
   t.by = by;
   t.tiles_x = (g.nx + BX - 1) / BX;
@@ -270,6 +270,11 @@ Tiling choose_tiling(const Geom& g, int by, int grid, bool src_expensive) {
   if (g.nz == 1) {
     t.chunks = 1;
     t.lz = 1;
+    return t;
+  }
+  if (planes > 0) {
+    t.lz = std::min(g.nz, planes);
+    t.chunks = (g.nz + t.lz - 1) / t.lz;
     return t;
   }
   if (grid <= 0) {
@@ -541,7 +546,7 @@ static hs_status residual_norms(const hs_op* A, hs_dtype dt, const void* D, cons
 // ---- persistent launch planning ------------------------------------------------
 template <typename K>
 static hs_status plan_persistent(K kernel, int block, size_t smem, const Geom& g, int by, bool src_expensive,
-                                 int* grid_out, Tiling* tl_out) {
+                                 int* grid_out, Tiling* tl_out, const hs_opts& o) {
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem);
   if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
@@ -550,9 +555,10 @@ static hs_status plan_persistent(K kernel, int block, size_t smem, const Geom& g
     return HS_ERR_CUDA;
   }
   int grid = std::min(per_sm * sm_count(), MAX_BLOCKS);
-  Tiling tl = choose_tiling(g, by, grid, src_expensive);
+  if (o.max_blocks > 0) grid = std::min(grid, o.max_blocks);
+  Tiling tl = choose_tiling(g, by, grid, src_expensive, o.tile_planes);
   grid = std::max(1, std::min(grid, tl.items()));
-  *tl_out = choose_tiling(g, by, grid, src_expensive);
+  *tl_out = choose_tiling(g, by, grid, src_expensive, o.tile_planes);
   *grid_out = grid;
   return HS_OK;
 }
@@ -676,10 +682,10 @@ hs_status run_jacobi(const SolveArgs& sa, hs_result* res, double* hist) {
     a.maxit = sa.maxit;
     a.tol = sa.tol;
     a.fuse = sa.tol > 0.0 ? 1 : 0;
-    int by = rows_per_tile(g);
+    int by = rows_for(g, sa.o);
     size_t smem = slab_bytes<T>(by);
     int grid;
-    s = plan_persistent(k_jacobi<T, OPK, NDIM>, 32 * by, smem, g, by, false, &grid, &a.tl);
+    s = plan_persistent(k_jacobi<T, OPK, NDIM>, 32 * by, smem, g, by, false, &grid, &a.tl, sa.o);
     if (s != HS_OK) return s;
     void* args[] = {&a};
     s = launch_coop((const void*)k_jacobi<T, OPK, NDIM>, grid, 32 * by, args, smem, sa.stream);
@@ -712,10 +718,10 @@ static hs_status cg_core(const hs_op* A, const Coef<T>& cf, double sigma, const 
   a.tol = tol;
   hs_status s = init_ctrl(cm, o, st);
   if (s != HS_OK) return s;
-  int by = rows_per_tile(a.g);
+  int by = rows_for(a.g, o);
   size_t smem = slab_bytes<T>(by);
   int grid;
-  s = plan_persistent(k_cg<T, OPK, NDIM>, 32 * by, smem, a.g, by, true, &grid, &a.tl);
+  s = plan_persistent(k_cg<T, OPK, NDIM>, 32 * by, smem, a.g, by, true, &grid, &a.tl, o);
   if (s != HS_OK) return s;
   void* args[] = {&a};
   return launch_coop((const void*)k_cg<T, OPK, NDIM>, grid, 32 * by, args, smem, st);
@@ -744,10 +750,10 @@ static hs_status bicgstab_core(const hs_op* A, const Coef<T>& cf, double sigma, 
   a.reps = o.restart_eps;
   hs_status s = init_ctrl(cm, o, st);
   if (s != HS_OK) return s;
-  int by = rows_per_tile(a.g);
+  int by = rows_for(a.g, o);
   size_t smem = slab_bytes<T>(by);
   int grid;
-  s = plan_persistent(k_bicgstab<T, OPK, NDIM>, 32 * by, smem, a.g, by, true, &grid, &a.tl);
+  s = plan_persistent(k_bicgstab<T, OPK, NDIM>, 32 * by, smem, a.g, by, true, &grid, &a.tl, o);
   if (s != HS_OK) return s;
   void* args[] = {&a};
   return launch_coop((const void*)k_bicgstab<T, OPK, NDIM>, grid, 32 * by, args, smem, st);

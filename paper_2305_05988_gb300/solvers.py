@@ -334,7 +334,7 @@ class Batch:
     ops: list of Operators; solvers: list of "cg" / "bicgstab" (one per system).
     """
 
-    def __init__(self, ops, solvers):
+    def __init__(self, ops, solvers, autotune: bool = False):
         lib = _lib.load()
         if len(ops) != len(solvers) or not ops:
             raise ValueError("need one solver per operator")
@@ -346,6 +346,12 @@ class Batch:
         self._b = ctypes.c_void_p()
         check(lib.hs_batch_create(self.n, arr_ops, arr_sol, ctypes.byref(self._b)), "hs_batch_create")
         self._ws = None
+        self.tile_planes = None
+        if autotune:
+            from .autotune import batch_tile_planes
+            self.tile_planes = batch_tile_planes(self.ops, list(solvers))
+            arr = (ctypes.c_int * self.n)(*self.tile_planes)
+            check(lib.hs_batch_set_tile_planes(self._b, arr), "hs_batch_set_tile_planes")
 
     def __del__(self):
         try:
