@@ -49,6 +49,9 @@ struct BatchJob {
 
 constexpr int BATCH_THREADS = 256;   // 8 rows per tile
 constexpr int BATCH_BY = BATCH_THREADS / 32;
+// The batch kernel holds every iteration body at once, so it runs them
+// with one column per lane to keep its register count (and occupancy) down.
+constexpr int BATCH_CX = 1;
 
 __device__ __forceinline__ Ctrl* sys_ctrl(const BatchSys& d) { return d.kind < BK_BI_SYM2 ? d.cg.cm.ctrl : d.bi.cm.ctrl; }
 __device__ __forceinline__ double* sys_partials(const BatchSys& d) {
@@ -96,16 +99,16 @@ __device__ __forceinline__ void batch_job(const BatchSys* __restrict__ sys, int 
   tm.ctrl = sys_ctrl(d);
   tm.partials = sys_partials(d);
   switch (d.kind) {
-    case BK_CG_SYM2: cg_body<double, OP_SYM, 2>(d.cg, tm, sm, sh); break;
-    case BK_CG_SYM3: cg_body<double, OP_SYM, 3>(d.cg, tm, sm, sh); break;
-    case BK_CG_VARK2: cg_body<double, OP_VARK, 2>(d.cg, tm, sm, sh); break;
-    case BK_CG_VARK3: cg_body<double, OP_VARK, 3>(d.cg, tm, sm, sh); break;
-    case BK_BI_SYM2: bicgstab_body<double, OP_SYM, 2>(d.bi, tm, sm, sh); break;
-    case BK_BI_SYM3: bicgstab_body<double, OP_SYM, 3>(d.bi, tm, sm, sh); break;
-    case BK_BI_NONSYM2: bicgstab_body<double, OP_NONSYM, 2>(d.bi, tm, sm, sh); break;
-    case BK_BI_NONSYM3: bicgstab_body<double, OP_NONSYM, 3>(d.bi, tm, sm, sh); break;
-    case BK_BI_VARK2: bicgstab_body<double, OP_VARK, 2>(d.bi, tm, sm, sh); break;
-    default: bicgstab_body<double, OP_VARK, 3>(d.bi, tm, sm, sh); break;
+    case BK_CG_SYM2: cg_body<double, OP_SYM, 2, BATCH_CX>(d.cg, tm, sm, sh); break;
+    case BK_CG_SYM3: cg_body<double, OP_SYM, 3, BATCH_CX>(d.cg, tm, sm, sh); break;
+    case BK_CG_VARK2: cg_body<double, OP_VARK, 2, BATCH_CX>(d.cg, tm, sm, sh); break;
+    case BK_CG_VARK3: cg_body<double, OP_VARK, 3, BATCH_CX>(d.cg, tm, sm, sh); break;
+    case BK_BI_SYM2: bicgstab_body<double, OP_SYM, 2, BATCH_CX>(d.bi, tm, sm, sh); break;
+    case BK_BI_SYM3: bicgstab_body<double, OP_SYM, 3, BATCH_CX>(d.bi, tm, sm, sh); break;
+    case BK_BI_NONSYM2: bicgstab_body<double, OP_NONSYM, 2, BATCH_CX>(d.bi, tm, sm, sh); break;
+    case BK_BI_NONSYM3: bicgstab_body<double, OP_NONSYM, 3, BATCH_CX>(d.bi, tm, sm, sh); break;
+    case BK_BI_VARK2: bicgstab_body<double, OP_VARK, 2, BATCH_CX>(d.bi, tm, sm, sh); break;
+    default: bicgstab_body<double, OP_VARK, 3, BATCH_CX>(d.bi, tm, sm, sh); break;
   }
   __syncthreads();
 }
@@ -190,7 +193,9 @@ static int batch_kind(const hs_op* A, int solver) {
   return d3 ? BK_BI_VARK3 : BK_BI_VARK2;
 }
 
-static size_t batch_smem() { return slab_bytes<double>(BATCH_BY); }
+static size_t batch_smem() { return slab_bytes<double>(BATCH_BY, BATCH_CX); }
+
+static int cx_of(int) { return BATCH_CX; }
 
 static int batch_grid() {
   int per_sm = 0;
@@ -231,7 +236,7 @@ static void make_plan(hs_batch* B, int grid, double tol) {
     wmax = std::max(wmax, p.work);
   }
   auto team_cap = [&](const BatchPlanSys& p) {
-    Tiling t1 = choose_tiling(p.g, BATCH_BY, 0, true);
+    Tiling t1 = choose_tiling(p.g, BATCH_BY, 0, true, 0, cx_of(p.solver));
     return std::max(1, t1.tiles_x * t1.tiles_y * std::max(1, p.g.nz / 4));
   };
   auto blocks_needed = [&](double T) {
@@ -268,7 +273,8 @@ static void make_plan(hs_batch* B, int grid, double tol) {
       p.team = 1;
       B->queue.push_back(s);   // largest first
     }
-    p.tl = choose_tiling(p.g, BATCH_BY, p.team, true, B->tile_planes.empty() ? 0 : B->tile_planes[s]);
+    p.tl = choose_tiling(p.g, BATCH_BY, p.team, true, B->tile_planes.empty() ? 0 : B->tile_planes[s],
+                         cx_of(p.solver));
   }
   B->job_off.assign(grid + 1, 0);
   B->jobs.clear();

@@ -107,7 +107,8 @@ __device__ bool gs_residual(const GsArgs<T>& a, T* sm, double* sh, double bb, do
   const T* bsrc = (OPK == OP_VARK) ? a.b : a.bD;
   LoadSrc<T, true> src{a.x};
   GsResSink<T, OPK, NDIM> sink{a.cf, a.g, bsrc, {0.0}};
-  for (int item = blockIdx.x; item < a.tl.items(); item += gridDim.x) zmarch_item<T, NDIM>(a.g, a.tl, item, sm, src, sink);
+  for (int item = blockIdx.x; item < a.tl.items(); item += gridDim.x)
+    zmarch_item<T, NDIM, 1>(a.g, a.tl, item, sm, src, sink);
   block_sum<1>(sink.acc, sh);
   double rr[1];
   if (!grid_reduce<1>(a.cm.ctrl, a.cm.partials, sink.acc, rr, sh)) return false;
@@ -471,7 +472,7 @@ static hs_status gs_run_t(const SolveArgs& sa, hs_result* res, double* hist) {
     return HS_ERR_CUDA;
   }
   int grid = std::min(per_sm * sm_count(), MAX_BLOCKS);
-  a.tl = choose_tiling(g, THREADS / 32, grid, false);
+  a.tl = choose_tiling(g, THREADS / 32, grid, false, 0, 1);
   void* args[] = {&a};
   e = cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(THREADS), args, smem, sa.stream);
   if (e != cudaSuccess) return cuda_fail(e, "cooperative launch");

@@ -61,7 +61,7 @@ ConstRow const_row(const hs_op* A);
 
 // Chooses a tiling (rows per tile, z chunk length) for `grid` persistent
 // blocks, or for a one-item-per-block launch when grid == 0.
-Tiling choose_tiling(const Geom& g, int by, int grid, bool src_expensive, int planes = 0);
+Tiling choose_tiling(const Geom& g, int by, int grid, bool src_expensive, int planes = 0, int cx = 1);
 
 // Workspace carving: every section is 256-byte aligned.
 struct Carve {

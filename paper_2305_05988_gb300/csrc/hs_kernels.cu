@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(512) k_spmv(Geom g, Tiling tl, Coef<T> cf, T s
   T* sm = reinterpret_cast<T*>(smraw);
   LoadSrc<T, false> src{x};
   SpmvSink<T, OPK, NDIM> sink{cf, g, sigma, y};
-  for (int item = blockIdx.x; item < tl.items(); item += gridDim.x) zmarch_item<T, NDIM>(g, tl, item, sm, src, sink);
+  for (int item = blockIdx.x; item < tl.items(); item += gridDim.x) zmarch_item<T, NDIM, CX_ST>(g, tl, item, sm, src, sink);
 }
 
 template <typename T, int OPK, int NDIM>
@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(512) k_residual(Geom g, Tiling tl, Coef<T> cf,
   T* sm = reinterpret_cast<T*>(smraw);
   LoadSrc<T, false> src{x};
   ResidualSink<T, OPK, NDIM> sink{cf, g, sigma, b, r, {0.0, 0.0}};
-  for (int item = blockIdx.x; item < tl.items(); item += gridDim.x) zmarch_item<T, NDIM>(g, tl, item, sm, src, sink);
+  for (int item = blockIdx.x; item < tl.items(); item += gridDim.x) zmarch_item<T, NDIM, CX_ST>(g, tl, item, sm, src, sink);
   block_sum<2>(sink.acc, sh);
   if (partials && threadIdx.x == 0) {
     partials[2 * blockIdx.x] = sink.acc[0];
@@ -188,8 +188,8 @@ __global__ void __launch_bounds__(512) k_jacobi(JacArgs<T> a) {
     }
     LoadSrc<T, true> src{xs};
     JacobiSink<T, OPK, NDIM> sink{a.cf, a.g, bsrc, xd, a.fuse, {0.0}};
-    for (int item = blockIdx.x; item < a.tl.items(); item += gridDim.x)
-      zmarch_item<T, NDIM>(a.g, a.tl, item, sm, src, sink);
+    for (int pos = blockIdx.x; pos < a.tl.items(); pos += gridDim.x)
+      zmarch_item<T, NDIM, (cx_jac<T, OPK>())>(a.g, a.tl, pos, sm, src, sink);
     if (a.fuse) {
       block_sum<1>(sink.acc, sh);
       double rr[1];
@@ -261,10 +261,11 @@ int sm_count() {
   return g_sm_count;
 }
 
-Tiling choose_tiling(const Geom& g, int by, int grid, bool src_expensive, int planes) {
+Tiling choose_tiling(const Geom& g, int by, int grid, bool src_expensive, int planes, int cx) {
   Tiling t;
   t.by = by;
-  t.tiles_x = (g.nx + BX - 1) / BX;
+  t.cx = cx;
+  t.tiles_x = (g.nx + BX * cx - 1) / (BX * cx);
   t.tiles_y = (g.ny + by - 1) / by;
   const int txy = t.tiles_x * t.tiles_y;
   if (g.nz == 1) {
@@ -445,7 +446,7 @@ __global__ void __launch_bounds__(512) k_spmv_vark_direct(Geom g, Tiling tl, con
   T* sm = reinterpret_cast<T*>(smraw);
   LoadSrc<T, false> src{x};
   VarkDirectSink<T, K, NDIM> sink{g, kk, ihx, ihy, ihz, y};
-  for (int item = blockIdx.x; item < tl.items(); item += gridDim.x) zmarch_item<T, NDIM>(g, tl, item, sm, src, sink);
+  for (int item = blockIdx.x; item < tl.items(); item += gridDim.x) zmarch_item<T, NDIM, CX_ST>(g, tl, item, sm, src, sink);
 }
 
 // r = b - y (elementwise), used by the residual of diffusion operators.
@@ -458,14 +459,14 @@ template <typename T, int NDIM>
 static hs_status spmv_vark_direct(const hs_op* A, const void* x, void* y, cudaStream_t st) {
   Geom g = geom_of(A);
   int by = rows_per_tile(g);
-  Tiling tl = choose_tiling(g, by, 0, false);
+  Tiling tl = choose_tiling(g, by, 0, false, 0, CX_ST);
   double ih[3];
   for (int d = 0; d < 3; d++) ih[d] = d < A->ndim ? 1.0 / (A->h[d] * A->h[d]) : 0.0;
   if (A->kdt == HS_F64)
-    k_spmv_vark_direct<T, double, NDIM><<<tl.items(), 32 * by, slab_bytes<T>(by), st>>>(
+    k_spmv_vark_direct<T, double, NDIM><<<tl.items(), 32 * by, slab_bytes<T>(by, CX_ST), st>>>(
         g, tl, (const double*)A->k, ih[0], ih[1], ih[2], (const T*)x, (T*)y);
   else
-    k_spmv_vark_direct<T, float, NDIM><<<tl.items(), 32 * by, slab_bytes<T>(by), st>>>(
+    k_spmv_vark_direct<T, float, NDIM><<<tl.items(), 32 * by, slab_bytes<T>(by, CX_ST), st>>>(
         g, tl, (const float*)A->k, ih[0], ih[1], ih[2], (const T*)x, (T*)y);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? HS_OK : cuda_fail(e, "spmv launch");
@@ -481,8 +482,8 @@ hs_status run_spmv(const hs_op* A, hs_dtype dt, const void* x, void* y, cudaStre
     double sigma;
     Coef<T> cf = op_coef<T>(A, nullptr, nullptr, nullptr, nullptr, &sigma);
     int by = rows_per_tile(g);
-    Tiling tl = choose_tiling(g, by, 0, false);
-    k_spmv<T, OPK, NDIM><<<tl.items(), 32 * by, slab_bytes<T>(by), st>>>(g, tl, cf, (T)sigma, (const T*)x, (T*)y);
+    Tiling tl = choose_tiling(g, by, 0, false, 0, CX_ST);
+    k_spmv<T, OPK, NDIM><<<tl.items(), 32 * by, slab_bytes<T>(by, CX_ST), st>>>(g, tl, cf, (T)sigma, (const T*)x, (T*)y);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? HS_OK : cuda_fail(e, "spmv launch");
   });
@@ -510,8 +511,8 @@ hs_status run_residual_plain(const hs_op* A, hs_dtype dt, const void* b, const v
     double sigma;
     Coef<T> cf = op_coef<T>(A, nullptr, nullptr, nullptr, nullptr, &sigma);
     int by = rows_per_tile(g);
-    Tiling tl = choose_tiling(g, by, 0, false);
-    k_residual<T, OPK, NDIM><<<tl.items(), 32 * by, slab_bytes<T>(by), st>>>(g, tl, cf, (T)sigma, (const T*)b,
+    Tiling tl = choose_tiling(g, by, 0, false, 0, CX_ST);
+    k_residual<T, OPK, NDIM><<<tl.items(), 32 * by, slab_bytes<T>(by, CX_ST), st>>>(g, tl, cf, (T)sigma, (const T*)b,
                                                                                (const T*)x, (T*)r, nullptr);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? HS_OK : cuda_fail(e, "residual launch");
@@ -531,9 +532,9 @@ static hs_status residual_norms(const hs_op* A, hs_dtype dt, const void* D, cons
     double sigma;
     Coef<T> cf = op_coef<T>(A, D, ax, ay, az, &sigma);
     int by = rows_per_tile(g);
-    Tiling tl = choose_tiling(g, by, 0, false);
+    Tiling tl = choose_tiling(g, by, 0, false, 0, CX_ST);
     int grid = std::min(tl.items(), MAX_BLOCKS * MAX_SCAL / 2);
-    k_residual<T, OPK, NDIM><<<grid, 32 * by, slab_bytes<T>(by), st>>>(g, tl, cf, (T)sigma, (const T*)b,
+    k_residual<T, OPK, NDIM><<<grid, 32 * by, slab_bytes<T>(by, CX_ST), st>>>(g, tl, cf, (T)sigma, (const T*)b,
                                                                         (const T*)x, (T*)r, partials_dev);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "residual launch");
@@ -546,7 +547,7 @@ static hs_status residual_norms(const hs_op* A, hs_dtype dt, const void* D, cons
 // ---- persistent launch planning ------------------------------------------------
 template <typename K>
 static hs_status plan_persistent(K kernel, int block, size_t smem, const Geom& g, int by, bool src_expensive,
-                                 int* grid_out, Tiling* tl_out, const hs_opts& o) {
+                                 int* grid_out, Tiling* tl_out, const hs_opts& o, int cx) {
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem);
   if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
@@ -556,9 +557,9 @@ static hs_status plan_persistent(K kernel, int block, size_t smem, const Geom& g
   }
   int grid = std::min(per_sm * sm_count(), MAX_BLOCKS);
   if (o.max_blocks > 0) grid = std::min(grid, o.max_blocks);
-  Tiling tl = choose_tiling(g, by, grid, src_expensive, o.tile_planes);
+  Tiling tl = choose_tiling(g, by, grid, src_expensive, o.tile_planes, cx);
   grid = std::max(1, std::min(grid, tl.items()));
-  *tl_out = choose_tiling(g, by, grid, src_expensive, o.tile_planes);
+  *tl_out = choose_tiling(g, by, grid, src_expensive, o.tile_planes, cx);
   *grid_out = grid;
   return HS_OK;
 }
@@ -683,9 +684,10 @@ hs_status run_jacobi(const SolveArgs& sa, hs_result* res, double* hist) {
     a.tol = sa.tol;
     a.fuse = sa.tol > 0.0 ? 1 : 0;
     int by = rows_for(g, sa.o);
-    size_t smem = slab_bytes<T>(by);
+    constexpr int cx = cx_jac<T, OPK>();
+    size_t smem = slab_bytes<T>(by, cx);
     int grid;
-    s = plan_persistent(k_jacobi<T, OPK, NDIM>, 32 * by, smem, g, by, false, &grid, &a.tl, sa.o);
+    s = plan_persistent(k_jacobi<T, OPK, NDIM>, 32 * by, smem, g, by, false, &grid, &a.tl, sa.o, cx);
     if (s != HS_OK) return s;
     void* args[] = {&a};
     s = launch_coop((const void*)k_jacobi<T, OPK, NDIM>, grid, 32 * by, args, smem, sa.stream);
@@ -719,9 +721,10 @@ static hs_status cg_core(const hs_op* A, const Coef<T>& cf, double sigma, const 
   hs_status s = init_ctrl(cm, o, st);
   if (s != HS_OK) return s;
   int by = rows_for(a.g, o);
-  size_t smem = slab_bytes<T>(by);
+  constexpr int cx = cx_cg<T, OPK>();
+  size_t smem = slab_bytes<T>(by, cx);
   int grid;
-  s = plan_persistent(k_cg<T, OPK, NDIM>, 32 * by, smem, a.g, by, true, &grid, &a.tl, o);
+  s = plan_persistent(k_cg<T, OPK, NDIM>, 32 * by, smem, a.g, by, true, &grid, &a.tl, o, cx);
   if (s != HS_OK) return s;
   void* args[] = {&a};
   return launch_coop((const void*)k_cg<T, OPK, NDIM>, grid, 32 * by, args, smem, st);
@@ -751,9 +754,9 @@ static hs_status bicgstab_core(const hs_op* A, const Coef<T>& cf, double sigma, 
   hs_status s = init_ctrl(cm, o, st);
   if (s != HS_OK) return s;
   int by = rows_for(a.g, o);
-  size_t smem = slab_bytes<T>(by);
+  size_t smem = slab_bytes<T>(by, CX_BI);
   int grid;
-  s = plan_persistent(k_bicgstab<T, OPK, NDIM>, 32 * by, smem, a.g, by, true, &grid, &a.tl, o);
+  s = plan_persistent(k_bicgstab<T, OPK, NDIM>, 32 * by, smem, a.g, by, true, &grid, &a.tl, o, CX_BI);
   if (s != HS_OK) return s;
   void* args[] = {&a};
   return launch_coop((const void*)k_bicgstab<T, OPK, NDIM>, grid, 32 * by, args, smem, st);

@@ -9,6 +9,18 @@
 
 namespace hs {
 
+// Columns per lane of the tile engine for each kernel family (see
+// hs_stencil.cuh).  Measured on GB300: two columns per lane neither speeds up
+// the FP64-pipe-bound solver passes nor helps the HBM-bound FP32 ones (whose
+// occupancy drops with the extra registers), so the solvers use one; the
+// single-pass SpMV / residual kernels use two.
+constexpr int CX_ST = 2;    // SpMV / residual
+constexpr int CX_BI = 1;    // BiCGStab
+template <typename T, int OPK>
+__host__ __device__ constexpr int cx_jac() { return 1; }
+template <typename T, int OPK>
+__host__ __device__ constexpr int cx_cg() { return 1; }
+
 // Global index / stride helpers for grid-stride element loops.
 __device__ __forceinline__ long long gtid() { return (long long)blockIdx.x * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ long long gstride() { return (long long)gridDim.x * blockDim.x; }
@@ -160,7 +172,7 @@ struct ApDotSink {
 
 // The CG iteration run by one team of blocks (the whole grid for a standalone
 // solve, a subset of blocks in the batched solver).
-template <typename T, int OPK, int NDIM>
+template <typename T, int OPK, int NDIM, int CX = cx_cg<T, OPK>()>
 __device__ void cg_body(const CgArgs<T>& a, const Team& tm, T* sm, double* sh) {
   const long long N = a.g.N;
   const T sig = (T)a.sigma;
@@ -170,7 +182,7 @@ __device__ void cg_body(const CgArgs<T>& a, const Team& tm, T* sm, double* sh) {
   {
     LoadSrc<T, true> src{a.x};
     for (int item = tm.rank; item < a.tl.items(); item += tm.size)
-      zmarch_item<T, NDIM>(a.g, a.tl, item, sm, src, rsink);
+      zmarch_item<T, NDIM, CX>(a.g, a.tl, item, sm, src, rsink);
   }
   block_sum<2>(rsink.acc, sh);
   double s2[2];
@@ -202,7 +214,7 @@ __device__ void cg_body(const CgArgs<T>& a, const Team& tm, T* sm, double* sh) {
     PUpdateSrc<T> src{a.r, pold, pnew, (T)beta, first};
     ApDotSink<T, OPK, NDIM> sink{a.cf, a.g, a.w, {0.0}};
     for (int item = tm.rank; item < a.tl.items(); item += tm.size)
-      zmarch_item<T, NDIM>(a.g, a.tl, item, sm, src, sink);
+      zmarch_item<T, NDIM, CX>(a.g, a.tl, item, sm, src, sink);
     block_sum<1>(sink.acc, sh);
     double pw[1];
     if (!team_reduce<1>(tm, sink.acc, pw, sh)) return;
@@ -398,7 +410,7 @@ struct BiTSink {
 };
 
 // The BiCGStab iteration run by one team of blocks.
-template <typename T, int OPK, int NDIM>
+template <typename T, int OPK, int NDIM, int CX = CX_BI>
 __device__ void bicgstab_body(const BiArgs<T>& a, const Team& tm, T* sm, double* sh) {
   const long long N = a.g.N;
   const T sig = (T)a.sigma;
@@ -407,7 +419,7 @@ __device__ void bicgstab_body(const BiArgs<T>& a, const Team& tm, T* sm, double*
   {
     LoadSrc<T, true> src{a.x};
     for (int item = tm.rank; item < a.tl.items(); item += tm.size)
-      zmarch_item<T, NDIM>(a.g, a.tl, item, sm, src, rsink);
+      zmarch_item<T, NDIM, CX>(a.g, a.tl, item, sm, src, rsink);
   }
   block_sum<2>(rsink.acc, sh);
   double s2[2];
@@ -445,7 +457,7 @@ __device__ void bicgstab_body(const BiArgs<T>& a, const Team& tm, T* sm, double*
       BiPSrc<T> src{a.r, pold, vold, pnew, (T)beta, (T)(omega * a.sigma), restart};
       BiVSink<T, OPK, NDIM> sink{a.cf, a.g, a.r, a.rs, vnew, (T)inv_rn, restart, {0.0}};
       for (int item = tm.rank; item < a.tl.items(); item += tm.size)
-        zmarch_item<T, NDIM>(a.g, a.tl, item, sm, src, sink);
+        zmarch_item<T, NDIM, CX>(a.g, a.tl, item, sm, src, sink);
       block_sum<1>(sink.acc, sh);
       if (!team_reduce<1>(tm, sink.acc, ad, sh)) return;
     }
@@ -461,7 +473,7 @@ __device__ void bicgstab_body(const BiArgs<T>& a, const Team& tm, T* sm, double*
       BiSSrc<T> src{a.r, vnew, a.s, (T)(alpha * a.sigma)};
       BiTSink<T, OPK, NDIM> sink{a.cf, a.g, a.t, {0.0, 0.0, 0.0}};
       for (int item = tm.rank; item < a.tl.items(); item += tm.size)
-        zmarch_item<T, NDIM>(a.g, a.tl, item, sm, src, sink);
+        zmarch_item<T, NDIM, CX>(a.g, a.tl, item, sm, src, sink);
       block_sum<3>(sink.acc, sh);
       if (!team_reduce<3>(tm, sink.acc, st3, sh)) return;
     }
@@ -511,12 +523,13 @@ __device__ void bicgstab_body(const BiArgs<T>& a, const Team& tm, T* sm, double*
       }
     }
     for (; i < N; i += st) {
-      T sv = ldcg(a.s + i);
-      T xn = fma(tom, sv, fma(ta, ldcg(pnew + i), ldcg(a.x + i)));
-      T rn = fma(-toms, ldcg(a.t + i), sv);
-      a.x[i] = xn;
-      a.r[i] = rn;
-      acc4[0] += widen(rn) * widen(ldcg(a.rs + i));
+      const long long q = i;
+      T sv = ldcg(a.s + q);
+      T xn = fma(tom, sv, fma(ta, ldcg(pnew + q), ldcg(a.x + q)));
+      T rn = fma(-toms, ldcg(a.t + q), sv);
+      a.x[q] = xn;
+      a.r[q] = rn;
+      acc4[0] += widen(rn) * widen(ldcg(a.rs + q));
       acc4[1] += widen(rn) * widen(rn);
     }
     block_sum<2>(acc4, sh);
@@ -582,8 +595,8 @@ inline int rows_for(const Geom& g, const hs_opts& o) {
 }
 
 template <typename T>
-inline size_t slab_bytes(int by) {
-  return (size_t)2 * (by + 2) * (BX + 2) * sizeof(T);
+inline size_t slab_bytes(int by, int cx) {
+  return (size_t)2 * (by + 2) * (BX * cx + 2) * sizeof(T);
 }
 
 // Operator coefficients for stencil kernels (scaled form, or var-k arrays).

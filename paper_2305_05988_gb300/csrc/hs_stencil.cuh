@@ -1,11 +1,12 @@
 // hs_stencil.cuh -- the z-marching tile engine used by every stencil pass.
 //
-// A work item is an xy tile of BX x BY nodes (BX = 32, one warp per row) and
-// a range [z0, z1) of planes.  The block marches up the planes: each thread
-// keeps the values of its own column at planes k-1, k, k+1 in registers,
-// while the plane k itself (tile plus a one-node halo) sits in a
-// double-buffered shared-memory slab that supplies the W/E/S/N neighbours.
-// One __syncthreads per plane.
+// A work item is an xy tile of (32 CX) x BY nodes (one warp per row, each
+// lane owning CX columns 32 apart) and a range [z0, z1) of planes.  The block
+// marches up the planes: each thread keeps the values of its own columns at
+// planes k-1, k, k+1 in registers, while the plane k itself (tile plus a
+// one-node halo) sits in a double-buffered shared-memory slab that supplies
+// the W/E/S/N neighbours.  One __syncthreads per plane; with CX = 2 every
+// thread carries two independent stencil chains per barrier.
 //
 // The stencil INPUT value at a node is produced by a functor `src` (a plain
 // load for SpMV/Jacobi, or an on-the-fly vector update such as
@@ -23,6 +24,7 @@ constexpr int BX = 32;
 struct Tiling {
   int by;        // rows per tile (3..16), blockDim.x = 32 * by
   int tiles_x, tiles_y, chunks, lz;
+  int cx;        // columns per lane (1 or 2): tile width 32 * cx
   __host__ __device__ int items() const { return tiles_x * tiles_y * chunks; }
 };
 
@@ -35,16 +37,16 @@ __device__ __forceinline__ void decode_item(const Tiling& t, const Geom& g, int 
   int r = item - c * txy;
   int ty = r / t.tiles_x;
   int tx = r - ty * t.tiles_x;
-  i0 = tx * BX;
+  i0 = tx * BX * t.cx;
   j0 = ty * t.by;
   z0 = c * t.lz;
   z1 = min(g.nz, z0 + t.lz);
 }
 
-// Shared slab: 2 planes of (by + 2) x (BX + 2) values.
-template <typename T>
+// Shared slab: 2 planes of (by + 2) x (32 CX + 2) values.
+template <typename T, int CX>
 __device__ __forceinline__ T& slab(T* sm, int by, int buf, int row, int col) {
-  return sm[(buf * (by + 2) + row) * (BX + 2) + col];
+  return sm[(buf * (by + 2) + row) * (BX * CX + 2) + col];
 }
 
 // Neighbour values of the current node handed to the stencil functor.
@@ -67,97 +69,156 @@ struct Nbr {
 // latency is hidden behind a whole plane of work instead of sitting in front
 // of the barrier.
 //
-// Halo points are produced by whole warps: warp 0 the row below the tile,
-// warp 1 the row above, warp 2 the two side columns (lanes 0..by-1 left,
-// 16..16+by-1 right).  Requires 3 <= by <= 16.
-template <typename T, int NDIM, class Src, class Sink>
+// Halo nodes are produced by whole warps: warp 0 the row below the tile (CX
+// nodes per lane), warp 1 the row above, warp 2 the two side columns (lanes
+// 0..by-1 left, 16..16+by-1 right).  Requires 3 <= by <= 16 and tl.cx == CX.
+template <typename T, int NDIM, int CX, class Src, class Sink>
 __device__ __forceinline__ void zmarch_item(const Geom& g, const Tiling& tl, int item, T* sm, const Src& src,
                                             Sink& sink) {
   using SR = typename Src::Raw;
   using KR = typename Sink::Raw;
+  constexpr int TW = BX * CX;
   int i0, j0, z0, z1;
   decode_item(tl, g, item, i0, j0, z0, z1);
   const int by = tl.by;
   const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
-  const int i = i0 + lx, j = j0 + ly;
-  const bool inside = (i < g.nx) && (j < g.ny);
-  const long long col = (long long)j * g.nx + i;
+  const int j = j0 + ly;
   const long long P = g.plane;
+  int ii[CX];
+  bool inside[CX];
+  long long col[CX];
+#pragma unroll
+  for (int c = 0; c < CX; c++) {
+    ii[c] = i0 + lx + BX * c;
+    inside[c] = (ii[c] < g.nx) && (j < g.ny);
+    col[c] = (long long)j * g.nx + ii[c];
+  }
 
-  // the halo node this thread produces (warps 0..2 only)
-  int hrow = -1, hcp = 0, hi = 0, hj = 0;
-  if (ly == 0) {
-    hi = i0 + lx; hj = j0 - 1; hrow = 0; hcp = lx + 1;
-  } else if (ly == 1) {
-    hi = i0 + lx; hj = j0 + by; hrow = by + 1; hcp = lx + 1;
-  } else if (ly == 2) {
-    if (lx < by) {
-      hi = i0 - 1; hj = j0 + lx; hrow = lx + 1; hcp = 0;
-    } else if (lx >= 16 && lx < 16 + by) {
-      hi = i0 + BX; hj = j0 + lx - 16; hrow = lx - 15; hcp = BX + 1;
+  // halo nodes this thread produces (warps 0..2 only)
+  constexpr int NH = CX;
+  int hrow[NH], hcp[NH];
+  bool hin[NH];
+  long long hcol[NH];
+#pragma unroll
+  for (int c = 0; c < NH; c++) {
+    hrow[c] = -1;
+    hcp[c] = 0;
+    hin[c] = false;
+    hcol[c] = 0;
+    int hi = 0, hj = 0;
+    if (ly == 0) {
+      hi = i0 + lx + BX * c; hj = j0 - 1; hrow[c] = 0; hcp[c] = lx + BX * c + 1;
+    } else if (ly == 1) {
+      hi = i0 + lx + BX * c; hj = j0 + by; hrow[c] = by + 1; hcp[c] = lx + BX * c + 1;
+    } else if (ly == 2 && c == 0) {
+      if (lx < by) {
+        hi = i0 - 1; hj = j0 + lx; hrow[c] = lx + 1; hcp[c] = 0;
+      } else if (lx >= 16 && lx < 16 + by) {
+        hi = i0 + TW; hj = j0 + lx - 16; hrow[c] = lx - 15; hcp[c] = TW + 1;
+      }
+    }
+    if (hrow[c] >= 0 && hi >= 0 && hi < g.nx && hj >= 0 && hj < g.ny) {
+      hin[c] = true;
+      hcol[c] = (long long)hj * g.nx + hi;
     }
   }
-  const bool hany = hrow >= 0;
-  const bool hin = hany && hi >= 0 && hi < g.nx && hj >= 0 && hj < g.ny;
-  const long long hcol = hin ? (long long)hj * g.nx + hi : 0;
 
-  T vb = T(0), vc = T(0), vt = T(0);
-  SR rown{}, rhal{};   // raw src values of plane k+1
-  KR kown{};           // raw sink values of plane k
+  T vb[CX], vc[CX], vt[CX];
+  SR rown[CX], rhal[NH];   // raw src values of plane k+1
+  KR kown[CX];             // raw sink values of plane k
+#pragma unroll
+  for (int c = 0; c < CX; c++) {
+    vb[c] = T(0);
+    vc[c] = T(0);
+    vt[c] = T(0);
+    rown[c] = SR{};
+    rhal[c] = SR{};
+    kown[c] = KR{};
+  }
   {
-    if (NDIM == 3 && inside && z0 > 0) {
-      SR rb = src.fetch(col + (long long)(z0 - 1) * P);
-      vb = src.make(rb, col + (long long)(z0 - 1) * P, false);
+    SR r0[CX], h0[NH];
+#pragma unroll
+    for (int c = 0; c < CX; c++) {
+      r0[c] = SR{};
+      h0[c] = SR{};
+      if (NDIM == 3 && inside[c] && z0 > 0) {
+        SR rb = src.fetch(col[c] + (long long)(z0 - 1) * P);
+        vb[c] = src.make(rb, col[c] + (long long)(z0 - 1) * P, false);
+      }
+      if (inside[c]) r0[c] = src.fetch(col[c] + (long long)z0 * P);
+      if (hin[c]) h0[c] = src.fetch(hcol[c] + (long long)z0 * P);
+      if (inside[c]) kown[c] = sink.fetch(col[c] + (long long)z0 * P, ii[c], j, z0);
+      if (NDIM == 3 && z0 + 1 < g.nz) {
+        if (inside[c]) rown[c] = src.fetch(col[c] + (long long)(z0 + 1) * P);
+        if (hin[c] && z0 + 1 < z1) rhal[c] = src.fetch(hcol[c] + (long long)(z0 + 1) * P);
+      }
     }
-    SR r0{}, h0{};
-    if (inside) r0 = src.fetch(col + (long long)z0 * P);
-    if (hin) h0 = src.fetch(hcol + (long long)z0 * P);
-    if (inside) kown = sink.fetch(col + (long long)z0 * P, i, j, z0);
-    if (NDIM == 3 && z0 + 1 < g.nz) {
-      if (inside) rown = src.fetch(col + (long long)(z0 + 1) * P);
-      if (hin && z0 + 1 < z1) rhal = src.fetch(hcol + (long long)(z0 + 1) * P);
+#pragma unroll
+    for (int c = 0; c < CX; c++) {
+      vc[c] = inside[c] ? src.make(r0[c], col[c] + (long long)z0 * P, true) : T(0);
+      slab<T, CX>(sm, by, 0, ly + 1, lx + BX * c + 1) = vc[c];
+      if (hrow[c] >= 0)
+        slab<T, CX>(sm, by, 0, hrow[c], hcp[c]) = hin[c] ? src.make(h0[c], hcol[c] + (long long)z0 * P, false) : T(0);
     }
-    vc = inside ? src.make(r0, col + (long long)z0 * P, true) : T(0);
-    slab(sm, by, 0, ly + 1, lx + 1) = vc;
-    if (hany) slab(sm, by, 0, hrow, hcp) = hin ? src.make(h0, hcol + (long long)z0 * P, false) : T(0);
   }
   __syncthreads();
 
   for (int k = z0; k < z1; k++) {
     const int buf = (k - z0) & 1;
-    SR rown2{}, rhal2{};
-    KR kown2{};
+    SR rown2[CX], rhal2[NH];
+    KR kown2[CX];
+#pragma unroll
+    for (int c = 0; c < CX; c++) {
+      rown2[c] = SR{};
+      rhal2[c] = SR{};
+      kown2[c] = KR{};
+    }
     if (NDIM == 3) {
-      if (inside && k + 2 < g.nz && k + 2 <= z1) rown2 = src.fetch(col + (long long)(k + 2) * P);
-      if (hin && k + 2 < z1) rhal2 = src.fetch(hcol + (long long)(k + 2) * P);
-      if (inside && k + 1 < z1) kown2 = sink.fetch(col + (long long)(k + 1) * P, i, j, k + 1);
-      vt = T(0);
-      if (k + 1 < g.nz) {
-        const bool own_next = (k + 1 < z1);
-        if (inside) vt = src.make(rown, col + (long long)(k + 1) * P, own_next);
-        if (own_next) {
-          slab(sm, by, buf ^ 1, ly + 1, lx + 1) = vt;
-          if (hany) slab(sm, by, buf ^ 1, hrow, hcp) = hin ? src.make(rhal, hcol + (long long)(k + 1) * P, false) : T(0);
+#pragma unroll
+      for (int c = 0; c < CX; c++) {
+        if (inside[c] && k + 2 < g.nz && k + 2 <= z1) rown2[c] = src.fetch(col[c] + (long long)(k + 2) * P);
+        if (hin[c] && k + 2 < z1) rhal2[c] = src.fetch(hcol[c] + (long long)(k + 2) * P);
+        if (inside[c] && k + 1 < z1) kown2[c] = sink.fetch(col[c] + (long long)(k + 1) * P, ii[c], j, k + 1);
+      }
+#pragma unroll
+      for (int c = 0; c < CX; c++) {
+        vt[c] = T(0);
+        if (k + 1 < g.nz) {
+          const bool own_next = (k + 1 < z1);
+          if (inside[c]) vt[c] = src.make(rown[c], col[c] + (long long)(k + 1) * P, own_next);
+          if (own_next) {
+            slab<T, CX>(sm, by, buf ^ 1, ly + 1, lx + BX * c + 1) = vt[c];
+            if (hrow[c] >= 0)
+              slab<T, CX>(sm, by, buf ^ 1, hrow[c], hcp[c]) =
+                  hin[c] ? src.make(rhal[c], hcol[c] + (long long)(k + 1) * P, false) : T(0);
+          }
         }
       }
     }
-    if (inside) {
-      Nbr<T> nb;
-      nb.c = vc;
-      nb.w = slab(sm, by, buf, ly + 1, lx);
-      nb.e = slab(sm, by, buf, ly + 1, lx + 2);
-      nb.s = slab(sm, by, buf, ly, lx + 1);
-      nb.n = slab(sm, by, buf, ly + 2, lx + 1);
-      nb.b = vb;
-      nb.t = vt;
-      sink(col + (long long)k * P, nb, kown, i, j, k);
+#pragma unroll
+    for (int c = 0; c < CX; c++) {
+      if (inside[c]) {
+        const int sx = lx + BX * c + 1;
+        Nbr<T> nb;
+        nb.c = vc[c];
+        nb.w = slab<T, CX>(sm, by, buf, ly + 1, sx - 1);
+        nb.e = slab<T, CX>(sm, by, buf, ly + 1, sx + 1);
+        nb.s = slab<T, CX>(sm, by, buf, ly, sx);
+        nb.n = slab<T, CX>(sm, by, buf, ly + 2, sx);
+        nb.b = vb[c];
+        nb.t = vt[c];
+        sink(col[c] + (long long)k * P, nb, kown[c], ii[c], j, k);
+      }
     }
     __syncthreads();
-    vb = vc;
-    vc = vt;
-    rown = rown2;
-    rhal = rhal2;
-    kown = kown2;
+#pragma unroll
+    for (int c = 0; c < CX; c++) {
+      vb[c] = vc[c];
+      vc[c] = vt[c];
+      rown[c] = rown2[c];
+      rhal[c] = rhal2[c];
+      kown[c] = kown2[c];
+    }
   }
 }
 

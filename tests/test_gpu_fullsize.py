@@ -1,0 +1,184 @@
+"""Parity at the benchmark's full sizes, in the launch configuration bench.py
+times (default options, x0 = 0, the same seeded inputs).
+
+Where the oracle cannot repeat the whole run, the test checks what it can
+compute in seconds: one full SpMV, the LAST sweep of Jacobi / Gauss-Seidel
+(the oracle sweeps the GPU's previous iterate), closed forms that hold at any
+size, residuals certified by the oracle's own SpMV, iteration counts against
+counts the oracle produced once (tests/golden/poisson3d_256_counts.json, written
+by tests/golden/make_poisson3d_counts.py), and sampled systems of the batch.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2305_05988_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2305_05988_gb300 as hs  # noqa: E402
+
+N3 = (256, 256, 256)
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "poisson3d_256_counts.json")
+
+
+@pytest.fixture(scope="module")
+def rhs():
+    b = inputs.rhs_uniform(N3, 0)
+    return b, torch.from_numpy(b).cuda()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_spmv_full_size(rhs):
+    b, bt = rhs
+    for A_o, A_g in ((oracle.Operator(N3), hs.Operator.laplacian(N3)),
+                     (oracle.Operator(N3, oracle.UPWIND, inputs.upwind_beta(N3, 0.5)),
+                      hs.Operator.upwind(N3, inputs.upwind_beta(N3, 0.5)))):
+        assert rel(A_g.spmv(bt).cpu().numpy(), A_o.spmv(b)) <= 1e-13
+
+
+def test_jacobi_last_sweep_full_size(rhs):
+    b, bt = rhs
+    A_o, A_g = oracle.Operator(N3), hs.Operator.laplacian(N3)
+    x199, _ = hs.jacobi(A_g, bt, maxit=199)
+    x200, info = hs.jacobi(A_g, bt, maxit=200)          # the bench's call
+    assert info.iters == 200 and info.status == "OK"
+    ref, _, _, _ = oracle.jacobi(A_o, b, x199.cpu().numpy(), maxit=1)
+    assert rel(x200.cpu().numpy(), ref) <= 1e-13
+
+
+def test_jacobi_closed_form_full_size():
+    # b = lambda v for the lowest mode: x_k = (1 - mu^k) v at any size
+    n = 256
+    h = 1.0 / (n + 1)
+    s = np.sin(math.pi * (np.arange(n) + 1.0) * h)
+    v = np.multiply.outer(np.multiply.outer(s, s), s).reshape(-1)
+    lam = 3 * 4.0 / h**2 * math.sin(math.pi * h / 2) ** 2
+    mu = math.cos(math.pi * h)
+    x, info = hs.jacobi(hs.Operator.laplacian(N3), torch.from_numpy(lam * v).cuda(), maxit=200)
+    ref = (1.0 - mu**200) * v
+    # per sweep: 2d + 2 roundings of the update plus the rounding of the
+    # pre-scaled coefficients a/a_ii and b/a_ii (same sign every sweep)
+    assert rel(x.cpu().numpy(), ref) <= 200 * (2 * 3 + 2 + 4) * 2.0**-53
+
+
+def test_gauss_seidel_last_sweep_full_size(rhs):
+    b, bt = rhs
+    A_o, A_g = oracle.Operator(N3), hs.Operator.laplacian(N3)
+    x199, _ = hs.gauss_seidel(A_g, bt, maxit=199)
+    x200, info = hs.gauss_seidel(A_g, bt, maxit=200)    # the bench's call
+    assert info.iters == 200 and info.status == "OK"
+    ref = oracle.gs_sweep(A_o, b, x199.cpu().numpy())
+    assert rel(x200.cpu().numpy(), ref) <= 1e-13
+
+
+@pytest.mark.parametrize("solver", ["cg", "bicgstab"])
+def test_krylov_full_size_against_golden_counts(rhs, solver):
+    if not os.path.exists(GOLDEN):
+        pytest.skip("golden counts not generated")
+    golden = json.load(open(GOLDEN))
+    if solver not in golden:
+        pytest.skip("golden count for %s not generated" % solver)
+    g = golden[solver]
+    b, bt = rhs
+    if solver == "cg":
+        A_o, A_g = oracle.Operator(N3), hs.Operator.laplacian(N3)
+        x, info = hs.cg(A_g, bt, tol=1e-10, maxit=20000)
+    else:
+        beta = inputs.upwind_beta(N3, 0.5)
+        A_o, A_g = oracle.Operator(N3, oracle.UPWIND, beta), hs.Operator.upwind(N3, beta)
+        x, info = hs.bicgstab(A_g, bt, tol=1e-10, maxit=20000)
+    assert info.status == "OK"
+    assert abs(info.iters - g["iters"]) <= 2, (info.iters, g)
+    assert A_o.relres(b, x.cpu().numpy()) <= 1e-10 * (1 + 1e-3)
+
+
+def test_mixed_512_certified_by_oracle():
+    shape = (512, 512, 512)
+    k = np.exp(inputs.log_k(shape, 1.0, 0))
+    b = inputs.rhs_uniform(shape, 0)
+    kt = torch.from_numpy(k).cuda()
+    A_g = hs.Operator.diffusion(shape, kt)
+    x, info = hs.solve_mixed(A_g, torch.from_numpy(b).cuda(), tol=1e-10, maxit=40, inner_tol=1e-4,
+                             inner_maxit=200000, timeout_s=20.0)
+    assert info.status == "OK"
+    A_o = oracle.Operator(shape, oracle.DIFFUSION, k=k)
+    assert A_o.relres(b, x.cpu().numpy()) <= 1e-10 * (1 + 1e-3)
+
+
+def test_adjoint_full_size():
+    shape = N3
+    N = int(np.prod(shape))
+    logk = inputs.log_k(shape, 0.5, 0)
+    f = inputs.rhs_uniform(shape, 0)
+    k = np.exp(logk)
+    kt = torch.from_numpy(k).cuda()
+    A_g = hs.Operator.diffusion(shape, kt)
+    ft = torch.from_numpy(f).cuda()
+    u, _ = hs.cg(A_g, ft, tol=1e-12, maxit=20000)
+    k2 = torch.from_numpy(np.exp(inputs.log_k(shape, 0.5, 0, inputs.STREAM_K2))).cuda()
+    u_obs, _ = hs.cg(hs.Operator.diffusion(shape, k2), ft, tol=1e-12, maxit=20000)
+    lam, _ = hs.cg(A_g, (2 * (u - u_obs)).contiguous(), tol=1e-12, maxit=20000)
+    g = hs.grad_logk(A_g, u, lam).cpu().numpy()
+    # the kernel against the oracle's gradient formula on the same fields
+    g_o = oracle.grad_logk(oracle.Operator(shape, oracle.DIFFUSION, k=k), u.cpu().numpy(), lam.cpu().numpy())
+    assert rel(g, g_o) <= 1e-12
+    # central differences of L on a few random cells (seeded).  Written without
+    # cancellation: with A(theta) u = f, the perturbed solution is u + du where
+    # A(theta+-) du = -(A(theta+-) - A(theta)) u (a right-hand side that lives
+    # next to the perturbed cell), and L(u + du) - L(u) = du . (du + 2 (u - u_obs)).
+    cells = (inputs.uniform(0, inputs.STREAM_FD, 4) * N).astype(np.int64)
+    delta = 1e-4
+    lk = torch.from_numpy(logk).cuda()
+    Au = A_g.spmv(u)
+    d_obs = 2 * (u - u_obs)
+
+    def dloss(lkt):
+        A_p = hs.Operator.diffusion(shape, torch.exp(lkt).contiguous())
+        r = (Au - A_p.spmv(u)).contiguous()
+        du, info = hs.cg(A_p, r, tol=1e-12, maxit=20000)
+        assert info.status == "OK"
+        return torch.sum(du * (du + d_obs)).item()
+
+    fd = []
+    for c in cells:
+        lp, lm = lk.clone(), lk.clone()
+        lp[c] += delta
+        lm[c] -= delta
+        fd.append((dloss(lp) - dloss(lm)) / (2 * delta))
+    fd = np.array(fd)
+    assert np.linalg.norm(g[cells] - fd) <= 1e-6 * np.linalg.norm(fd), (g[cells], fd)
+
+
+def test_batched_512_sampled_against_oracle():
+    systems = inputs.batch_systems(512, seed=0)
+    ops, bs, sol = [], [], []
+    for s in systems:
+        if s.solver == "cg":
+            ops.append(hs.Operator.laplacian(s.shape))
+        else:
+            ops.append(hs.Operator.upwind(s.shape, inputs.upwind_beta(s.shape, s.peclet)))
+        bs.append(torch.from_numpy(inputs.uniform_pm1(0, inputs.STREAM_BATCH_RHS + s.index, s.N)).cuda())
+        sol.append(s.solver)
+    batch = hs.Batch(ops, sol)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        xs, infos = batch.solve(bs, tol=1e-8, timeout_s=20.0)
+    st.synchronize()
+    assert all(i.status == "OK" for i in infos)
+    picks = np.unique((inputs.uniform(1, inputs.STREAM_FD, 24) * 512).astype(int))
+    for p in picks:
+        s = systems[p]
+        if s.solver == "cg":
+            A_o = oracle.Operator(s.shape)
+        else:
+            A_o = oracle.Operator(s.shape, oracle.UPWIND, inputs.upwind_beta(s.shape, s.peclet))
+        assert A_o.relres(bs[p].cpu().numpy(), xs[p].cpu().numpy()) <= 1e-8 * 1.5, (p, s)
