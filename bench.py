@@ -81,6 +81,8 @@ def parse():
     p.add_argument("--mixed-n", type=int, default=512, help="grid side of the mixed-precision comparison (0: skip)")
     p.add_argument("--adjoint-n", type=int, default=256, help="grid side of the adjoint-gradient timing (0: skip)")
     p.add_argument("--batch-n", type=int, default=512, help="systems in the batched comparison (0: skip)")
+    p.add_argument("--batch-vark", action="store_true",
+                   help="batched comparison: CG systems on variable-k diffusion (log k ~ N(0, 1))")
     return p.parse_args()
 
 
@@ -413,7 +415,7 @@ def run_ours(args, rank, world, dist):
     if rank == 0 and args.adjoint_n > 0:
         extras["adjoint"] = adjoint_timing(args.adjoint_n, dev, tmo)
     if rank == 0 and args.batch_n > 0:
-        extras["batched"] = batch_comparison(args.batch_n, dev, tmo)
+        extras["batched"] = batch_comparison(args.batch_n, dev, tmo, args.batch_vark)
 
     # kernels launched per step: spmv 1; jacobi, cg, bicgstab: control init +
     # persistent solver + residual + finalize = 4 each; gauss-seidel: solver +
@@ -505,20 +507,26 @@ def adjoint_timing(n, dev, tmo):
     return out
 
 
-def batch_comparison(nsys, dev, tmo):
+def batch_comparison(nsys, dev, tmo, vark=False):
     """The batched workload: nsys independent systems (2-D or 3-D, sides
-    log-uniform in [16, 256]; even systems CG on the Laplacian, odd systems
-    BiCGStab on upwind convection-diffusion with Peclet in [0.1, 1]) solved to
-    1e-8 by one persistent kernel replayed as a CUDA graph, against solving them
-    one after another with the standalone solvers."""
+    log-uniform in [16, 256]; even systems CG on the symmetric diffusion
+    operator (k = 1, or log k ~ N(0, 1) with vark), odd systems BiCGStab on
+    upwind convection-diffusion with Peclet in [0.1, 1]) solved to 1e-8 by one
+    persistent kernel replayed as a CUDA graph: in FP64, and in mixed precision
+    (FP64 refinement, FP32 inner CG / BiCGStab to 1e-4), against solving them
+    one after another with the standalone FP64 solvers."""
     import torch
 
     import paper_2305_05988_gb300 as hs
     from paper_2305_05988_gb300 import inputs
     systems = inputs.batch_systems(nsys, seed=0)
-    ops, bs, sol = [], [], []
+    ops, bs, sol, ks = [], [], [], []
     for s in systems:
-        if s.solver == "cg":
+        if s.solver == "cg" and vark:
+            k = torch.from_numpy(np.exp(inputs.log_k(s.shape, 1.0, s.index))).to(dev)
+            ks.append(k)
+            ops.append(hs.Operator.diffusion(s.shape, k))
+        elif s.solver == "cg":
             ops.append(hs.Operator.laplacian(s.shape))
         else:
             ops.append(hs.Operator.upwind(s.shape, inputs.upwind_beta(s.shape, s.peclet)))
@@ -526,8 +534,9 @@ def batch_comparison(nsys, dev, tmo):
         sol.append(s.solver)
     unknowns = sum(s.N for s in systems)
     st = torch.cuda.Stream(dev)
-    out = {"workload": "%d systems, sides log-uniform in [16, 256], 2-D/3-D, CG (Laplacian) / BiCGStab "
-                       "(upwind, Pe in [0.1, 1]), tol 1e-8, FP64" % nsys, "unknowns": unknowns}
+    out = {"workload": "%d systems, sides log-uniform in [16, 256], 2-D/3-D, CG (%s) / BiCGStab "
+                       "(upwind, Pe in [0.1, 1]), tol 1e-8" % (nsys, "diffusion, log k ~ N(0,1)" if vark else "Laplacian"),
+           "unknowns": unknowns}
     t0 = time.perf_counter()
     batch = hs.Batch(ops, sol, autotune=True)
     out["autotune_s"] = round(time.perf_counter() - t0, 2)
@@ -553,7 +562,29 @@ def batch_comparison(nsys, dev, tmo):
                       "converged": sum(i.status == "OK" for i in infos), "teams_gt1": sum(t > 1 for t in batch.teams)}
     out["sequential"] = {"ms": round(ts, 2), "iters_total": seq_iters}
     out["speedup"] = round(ts / tb, 3)
-    del batch, xs, bs, ops
+    del batch
+    # mixed precision: the same systems, FP64 refinement with FP32 inner solves
+    mb = hs.Batch(ops, ["mixed"] * len(ops), autotune=True)
+    with torch.cuda.stream(st):
+        for x in xs:
+            x.zero_()
+        mb.solve(bs, xs, tol=1e-8, maxit=20, inner_tol=1e-4, inner_maxit=100000, timeout_s=max(tmo, 20.0))
+        for x in xs:
+            x.zero_()
+        st.synchronize()
+        e0.record(st)
+        xs, minfo = mb.solve(bs, xs, tol=1e-8, maxit=20, inner_tol=1e-4, inner_maxit=100000,
+                             timeout_s=max(tmo, 20.0))
+        e1.record(st)
+        st.synchronize()
+    tm = e0.elapsed_time(e1)
+    out["batched_mixed"] = {"ms": round(tm, 2), "graph": mb.graph_used,
+                            "outer_total": sum(i.outer for i in minfo),
+                            "inner_iters_total": sum(i.inner_iters for i in minfo),
+                            "converged": sum(i.status == "OK" for i in minfo),
+                            "max_rel_res": max(i.rel_res for i in minfo)}
+    out["speedup_mixed_vs_sequential"] = round(ts / tm, 3)
+    del mb, xs, bs, ops, ks
     torch.cuda.empty_cache()
     return out
 

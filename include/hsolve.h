@@ -256,17 +256,29 @@ hs_status hs_cg_static(const hs_op *A, hs_dtype dtype, const void *b, void *x, d
  * queue, largest first, that every block drains one system at a time once
  * its team job (if any) is done.
  * Every system has its own convergence test, status and iteration count, and
- * runs exactly the iteration of hs_cg / hs_bicgstab (FP64). */
+ * runs exactly the iteration of hs_cg / hs_bicgstab (FP64).
+ * A batch whose systems all name HS_SOLVER_MIXED runs FP64 iterative
+ * refinement per system (the scheme of hs_solve_mixed) inside one kernel:
+ * the FP64 residual b - A x is scaled by a power of two and rounded to FP32,
+ * the correction equation is solved in FP32 (CG for symmetric operators,
+ * BiCGStab for the upwind operator) to opts.inner_tol / opts.inner_maxit,
+ * and x += correction in FP64, until the FP64 relative residual <= tol or
+ * maxit refinement steps. */
 typedef struct hs_batch hs_batch;   /* opaque, library-owned */
 
 /* ops[s] (copied; a diffusion operator's k stays borrowed) and
- * solvers[s] in {HS_SOLVER_CG (symmetric operators), HS_SOLVER_BICGSTAB}. */
+ * solvers[s] in {HS_SOLVER_CG (symmetric operators), HS_SOLVER_BICGSTAB}, or
+ * HS_SOLVER_MIXED for every system.  HS_ERR_INVALID for a NULL operator, an
+ * unknown solver, CG on the upwind operator, or MIXED for only some systems. */
 hs_status hs_batch_create(int nsys, const hs_op *const *ops, const int *solvers, hs_batch **out);
 void hs_batch_destroy(hs_batch *batch);
 /* Device workspace bytes for hs_batch_solve (plans the teams on first use). */
 hs_status hs_batch_workspace_size(hs_batch *batch, size_t *bytes);
 /* b[s], x[s]: host arrays of nsys FP64 device pointers (x: initial guess in,
- * solution out).  res: host array of nsys results (true_rel_res = -1).
+ * solution out).  res: host array of nsys results (true_rel_res = -1 for FP64
+ * systems; for mixed systems iters = outer = refinement steps, inner_iters =
+ * their inner iterations, rel_res = true_rel_res = the FP64 relative residual,
+ * restarts = inner BiCGStab restarts).
  * Returns HS_OK unless a system timed out or the launch failed; per-system
  * breakdowns and non-convergence are reported in res[s].status.  Calls on one
  * batch object are serialised by the library; the captured graph is reused

@@ -159,6 +159,8 @@ def batch_tile_planes(ops: Sequence[Operator], solvers: Sequence[str], tune_miss
     out = []
     done = {}
     for A, s in zip(ops, solvers):
+        if s == "mixed":   # tuned as its inner solver
+            s = "bicgstab" if A.kind == "upwind" else "cg"
         if size_bucket(A.shape) > SMALL_BUCKET:
             out.append(0)
             continue

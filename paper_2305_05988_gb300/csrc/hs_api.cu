@@ -77,7 +77,7 @@ static hs_opts default_opts() {
   return o;
 }
 
-static bool merge_opts(const hs_opts* in, hs_opts* out) {
+bool merge_opts(const hs_opts* in, hs_opts* out) {
   *out = default_opts();
   if (!in) return true;
   if (in->struct_size < sizeof(size_t) || in->struct_size > 4096) {
@@ -113,8 +113,6 @@ static bool merge_opts(const hs_opts* in, hs_opts* out) {
 
 static bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
-static hs_opts default_opts();
-static bool merge_opts(const hs_opts* in, hs_opts* out);
 
 static size_t ws_need(const hs_op* A, hs_solver s, hs_dtype dt, const hs_opts& o, int maxit) {
   if (s == HS_SOLVER_MIXED) return mixed_ws_bytes(A, o, maxit);

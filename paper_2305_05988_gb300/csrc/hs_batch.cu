@@ -9,6 +9,9 @@
 // largest first, that every block drains one system at a time once its team
 // job (if any) is done.  A team's blocks therefore never wait for a block that
 // is busy with another system, and converged systems stop taking block time.
+//
+// A batch whose systems all name HS_SOLVER_MIXED runs the mixed-precision
+// kernel of hs_batch_mixed.cu instead (same plan, tables and graph cache).
 #include <algorithm>
 #include <cmath>
 #include <cstddef>
@@ -18,7 +21,7 @@
 #include <numeric>
 #include <vector>
 
-#include "hs_krylov.cuh"
+#include "hs_batch.cuh"
 
 namespace hs {
 
@@ -43,15 +46,6 @@ struct BatchSys {
 };
 static_assert(sizeof(BatchSys) % 8 == 0, "descriptor must be copied in 8-byte words");
 
-struct BatchJob {
-  int sys, rank, size, pad;
-};
-
-constexpr int BATCH_THREADS = 256;   // 8 rows per tile
-constexpr int BATCH_BY = BATCH_THREADS / 32;
-// The batch kernel holds every iteration body at once, so it runs them
-// with one column per lane to keep its register count (and occupancy) down.
-constexpr int BATCH_CX = 1;
 
 __device__ __forceinline__ Ctrl* sys_ctrl(const BatchSys& d) { return d.kind < BK_BI_SYM2 ? d.cg.cm.ctrl : d.bi.cm.ctrl; }
 __device__ __forceinline__ double* sys_partials(const BatchSys& d) {
@@ -76,10 +70,13 @@ __global__ void k_batch_init(const BatchSys* __restrict__ sys, int nsys, unsigne
 __global__ void k_batch_gather(const BatchSys* __restrict__ sys, int nsys, double* __restrict__ out) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsys; s += gridDim.x * blockDim.x) {
     const Ctrl* c = sys_ctrl(sys[s]);
-    out[4 * s + 0] = (double)c->status;
-    out[4 * s + 1] = (double)c->iters;
-    out[4 * s + 2] = c->rel_res;
-    out[4 * s + 3] = (double)c->restarts;
+    double* o = out + (size_t)BATCH_OUT * s;
+    o[0] = (double)c->status;
+    o[1] = (double)c->iters;
+    o[2] = c->rel_res;
+    o[3] = (double)c->restarts;
+    o[4] = 0.0;
+    o[5] = 0.0;
   }
 }
 
@@ -99,16 +96,16 @@ __device__ __forceinline__ void batch_job(const BatchSys* __restrict__ sys, int 
   tm.ctrl = sys_ctrl(d);
   tm.partials = sys_partials(d);
   switch (d.kind) {
-    case BK_CG_SYM2: cg_body<double, OP_SYM, 2, BATCH_CX>(d.cg, tm, sm, sh); break;
-    case BK_CG_SYM3: cg_body<double, OP_SYM, 3, BATCH_CX>(d.cg, tm, sm, sh); break;
-    case BK_CG_VARK2: cg_body<double, OP_VARK, 2, BATCH_CX>(d.cg, tm, sm, sh); break;
-    case BK_CG_VARK3: cg_body<double, OP_VARK, 3, BATCH_CX>(d.cg, tm, sm, sh); break;
-    case BK_BI_SYM2: bicgstab_body<double, OP_SYM, 2, BATCH_CX>(d.bi, tm, sm, sh); break;
-    case BK_BI_SYM3: bicgstab_body<double, OP_SYM, 3, BATCH_CX>(d.bi, tm, sm, sh); break;
-    case BK_BI_NONSYM2: bicgstab_body<double, OP_NONSYM, 2, BATCH_CX>(d.bi, tm, sm, sh); break;
-    case BK_BI_NONSYM3: bicgstab_body<double, OP_NONSYM, 3, BATCH_CX>(d.bi, tm, sm, sh); break;
-    case BK_BI_VARK2: bicgstab_body<double, OP_VARK, 2, BATCH_CX>(d.bi, tm, sm, sh); break;
-    default: bicgstab_body<double, OP_VARK, 3, BATCH_CX>(d.bi, tm, sm, sh); break;
+    case BK_CG_SYM2: team_finish(tm, cg_body<double, OP_SYM, 2, BATCH_CX>(d.cg, tm, sm, sh)); break;
+    case BK_CG_SYM3: team_finish(tm, cg_body<double, OP_SYM, 3, BATCH_CX>(d.cg, tm, sm, sh)); break;
+    case BK_CG_VARK2: team_finish(tm, cg_body<double, OP_VARK, 2, BATCH_CX>(d.cg, tm, sm, sh)); break;
+    case BK_CG_VARK3: team_finish(tm, cg_body<double, OP_VARK, 3, BATCH_CX>(d.cg, tm, sm, sh)); break;
+    case BK_BI_SYM2: team_finish(tm, bicgstab_body<double, OP_SYM, 2, BATCH_CX>(d.bi, tm, sm, sh)); break;
+    case BK_BI_SYM3: team_finish(tm, bicgstab_body<double, OP_SYM, 3, BATCH_CX>(d.bi, tm, sm, sh)); break;
+    case BK_BI_NONSYM2: team_finish(tm, bicgstab_body<double, OP_NONSYM, 2, BATCH_CX>(d.bi, tm, sm, sh)); break;
+    case BK_BI_NONSYM3: team_finish(tm, bicgstab_body<double, OP_NONSYM, 3, BATCH_CX>(d.bi, tm, sm, sh)); break;
+    case BK_BI_VARK2: team_finish(tm, bicgstab_body<double, OP_VARK, 2, BATCH_CX>(d.bi, tm, sm, sh)); break;
+    default: team_finish(tm, bicgstab_body<double, OP_VARK, 3, BATCH_CX>(d.bi, tm, sm, sh)); break;
   }
   __syncthreads();
 }
@@ -160,6 +157,7 @@ struct hs_batch {
   int nsys;
   std::vector<hs_op> ops;             // copies of the operators (k stays borrowed)
   std::vector<int> solvers;
+  bool mixed = false;                 // every system uses FP64 refinement with an FP32 inner solve
   // plan (depends on the grid size of the batched kernel)
   int grid = 0;
   std::vector<hs::BatchPlanSys> plan;
@@ -180,9 +178,22 @@ struct hs_batch {
 
 namespace hs {
 
+// Inner solver of a mixed-precision system: CG for the symmetric operators,
+// BiCGStab for the upwind one.
+static int mixed_inner(const hs_op* A) { return opkind_of(A) == OP_NONSYM ? HS_SOLVER_BICGSTAB : HS_SOLVER_CG; }
+
 static int batch_kind(const hs_op* A, int solver) {
   const bool d3 = A->ndim >= 3;
   const int opk = opkind_of(A);
+  if (solver == HS_SOLVER_MIXED) {
+    if (mixed_inner(A) == HS_SOLVER_CG) {
+      if (opk == OP_SYM) return d3 ? MK_CG_SYM3 : MK_CG_SYM2;
+      return d3 ? MK_CG_VARK3 : MK_CG_VARK2;
+    }
+    if (opk == OP_SYM) return d3 ? MK_BI_SYM3 : MK_BI_SYM2;
+    if (opk == OP_NONSYM) return d3 ? MK_BI_NONSYM3 : MK_BI_NONSYM2;
+    return d3 ? MK_BI_VARK3 : MK_BI_VARK2;
+  }
   if (solver == HS_SOLVER_CG) {
     if (opk == OP_SYM) return d3 ? BK_CG_SYM3 : BK_CG_SYM2;
     if (opk == OP_VARK) return d3 ? BK_CG_VARK3 : BK_CG_VARK2;
@@ -197,23 +208,30 @@ static size_t batch_smem() { return slab_bytes<double>(BATCH_BY, BATCH_CX); }
 
 static int cx_of(int) { return BATCH_CX; }
 
-static int batch_grid() {
+static int batch_grid(bool mixed) {
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, BATCH_THREADS, batch_smem()) != cudaSuccess ||
-      per_sm < 1)
-    return 0;
+  if (mixed) {
+    per_sm = batch_mx_blocks_per_sm(BATCH_THREADS, batch_smem());
+  } else if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, BATCH_THREADS, batch_smem()) !=
+             cudaSuccess) {
+    per_sm = 0;
+  }
+  if (per_sm < 1) return 0;
   return std::min(per_sm * sm_count(), MAX_BLOCKS);
 }
 
 // Estimated solver work: unknowns x iterations x relative cost per
 // iteration.  Iterations of CG on these operators grow like the grid side:
 // about (n + 1) ln(2/tol) / (2 pi); BiCGStab needs ~0.65 as many iterations
-// at ~2.2 times the cost.
+// at ~2.2 times the cost.  A mixed-precision system does about as many
+// inner iterations in all, at about half the cost each (FP32 arithmetic and
+// half the bytes).
 static double est_work(const hs_op* A, int solver, double tol) {
   double nmax = 1;
   for (int d = 0; d < A->ndim; d++) nmax = std::max(nmax, (double)A->n[d]);
   const double N = (double)(A->n[0] * A->n[1] * A->n[2]);
   const double it = std::max(2.0, (nmax + 1.0) * std::log(2.0 / std::max(tol, 1e-300)) / (2.0 * M_PI));
+  if (solver == HS_SOLVER_MIXED) return 0.5 * est_work(A, mixed_inner(A), tol);
   return solver == HS_SOLVER_CG ? N * it : N * 0.65 * it * 2.2;
 }
 
@@ -290,24 +308,36 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Workspace: descriptor table, job tables, results, then per system a control
 // block, its team's partial sums and its solver vectors (+ coefficients).
+static size_t desc_bytes(const hs_batch* B) { return B->mixed ? sizeof(MxSys) : sizeof(BatchSys); }
+
+// Vectors of a system: FP64 solver vectors, or for a mixed system the FP32
+// residual and correction plus the inner solver's FP32 vectors.
+static int sys_vectors(const hs_batch* B, int s) {
+  const int solver = B->mixed ? mixed_inner(&B->ops[s]) : B->plan[s].solver;
+  return (solver == HS_SOLVER_CG ? 4 : 8) + (B->mixed ? 2 : 0);
+}
+
 static void layout(hs_batch* B) {
   const int n = B->nsys;
   size_t off = 0;
-  off += align256(sizeof(BatchSys) * n);
+  off += align256(desc_bytes(B) * n);
   off += align256(sizeof(int) * (B->grid + 1));
   off += align256(sizeof(BatchJob) * std::max<size_t>(1, B->jobs.size()));
-  off += align256(sizeof(double) * 4 * n);
+  off += align256(sizeof(double) * BATCH_OUT * n);
   off += align256(sizeof(int) * (n + 1));   // queue + head
   B->tables_bytes = off;
   B->sys_off.assign(n, 0);
   for (int s = 0; s < n; s++) {
     const BatchPlanSys& p = B->plan[s];
     B->sys_off[s] = off;
-    off += 512;
+    off += B->mixed ? 1024 : 512;           // control block(s)
     off += align256(sizeof(double) * MAX_SCAL * p.team);
-    const size_t vec = align256(sizeof(double) * (size_t)p.g.N);
-    off += vec * (p.solver == HS_SOLVER_CG ? 4 : 8);
-    if (B->ops[s].kind == KIND_DIFFUSION) off += 4 * vec;
+    const size_t el = B->mixed ? sizeof(float) : sizeof(double);
+    off += align256(el * (size_t)p.g.N) * sys_vectors(B, s);
+    if (B->ops[s].kind == KIND_DIFFUSION) {
+      off += 4 * align256(sizeof(double) * (size_t)p.g.N);
+      if (B->mixed) off += 4 * align256(sizeof(float) * (size_t)p.g.N);
+    }
   }
   B->ws_total = off;
 }
@@ -317,7 +347,7 @@ static void layout(hs_batch* B) {
 // logarithmic factor).
 static hs_status ensure_plan(hs_batch* B) {
   if (B->grid > 0) return HS_OK;
-  int grid = batch_grid();
+  int grid = batch_grid(B->mixed);
   if (grid < 1) {
     set_error("batched kernel cannot be resident");
     return HS_ERR_CUDA;
@@ -327,6 +357,96 @@ static hs_status ensure_plan(hs_batch* B) {
   if (B->exec) {
     cudaGraphExecDestroy(B->exec);
     B->exec = nullptr;
+  }
+  return HS_OK;
+}
+
+// Descriptor of mixed-precision system s for one call: carves its control
+// blocks and vectors from the workspace and sets up its coefficients.
+static hs_status fill_mixed(hs_batch* B, int s, const double* b, double* x, double tol, int maxit, const hs_opts& o,
+                            char* base, cudaStream_t stm, MxSys* out) {
+  const hs_op* A = &B->ops[s];
+  const BatchPlanSys& p = B->plan[s];
+  Carve c{base + B->sys_off[s], 0, (size_t)-1, true};
+  Common cm;
+  cm.ctrl = c.take<Ctrl>(1);
+  c.take<char>(512 - ((sizeof(Ctrl) + 255) & ~(size_t)255));
+  Ctrl* inner = c.take<Ctrl>(1);
+  c.take<char>(512 - ((sizeof(Ctrl) + 255) & ~(size_t)255));
+  cm.partials = c.take<double>((size_t)MAX_SCAL * p.team);
+  cm.hist = nullptr;
+  const int nv = sys_vectors(B, s);
+  float* v[10] = {nullptr};
+  for (int q = 0; q < nv; q++) v[q] = c.take<float>(p.g.N);
+  double *D = nullptr, *ax = nullptr, *ay = nullptr, *az = nullptr;
+  float *D32 = nullptr, *ax32 = nullptr, *ay32 = nullptr, *az32 = nullptr;
+  if (A->kind == KIND_DIFFUSION) {
+    D = c.take<double>(p.g.N);
+    ax = c.take<double>(p.g.N);
+    ay = c.take<double>(p.g.N);
+    az = c.take<double>(p.g.N);
+    D32 = c.take<float>(p.g.N);
+    ax32 = c.take<float>(p.g.N);
+    ay32 = c.take<float>(p.g.N);
+    az32 = c.take<float>(p.g.N);
+    hs_status s2 = setup_vark(A, HS_F64, D, ax, ay, az, false, stm);
+    if (s2 == HS_OK) s2 = setup_vark(A, HS_F32, D32, ax32, ay32, az32, false, stm);
+    if (s2 != HS_OK) return s2;
+  }
+  MxSys& d = *out;
+  memset(&d, 0, sizeof(d));
+  d.kind = p.kind;
+  d.max_outer = maxit;
+  d.tol = tol;
+  d.restart_eps = o.restart_eps;
+  d.g = p.g;
+  d.tl = p.tl;
+  d.cf = op_coef<double>(A, D, ax, ay, az, &d.sigma);
+  d.b = b;
+  d.x = x;
+  d.r32 = v[0];
+  d.d32 = v[1];
+  d.cm = cm;
+  d.inner_ctrl = inner;
+  Common ci = cm;
+  ci.ctrl = inner;
+  double sig32 = 1.0;
+  const Coef<float> cf32 = op_coef<float>(A, D32, ax32, ay32, az32, &sig32);
+  if (mixed_inner(A) == HS_SOLVER_CG) {
+    CgArgs<float>& a = d.cg;
+    a.g = p.g;
+    a.tl = p.tl;
+    a.cf = cf32;
+    a.sigma = sig32;
+    a.b = d.r32;
+    a.x = d.d32;
+    a.r = v[2];
+    a.p0 = v[3];
+    a.p1 = v[4];
+    a.w = v[5];
+    a.cm = ci;
+    a.maxit = o.inner_maxit;
+    a.tol = o.inner_tol;
+  } else {
+    BiArgs<float>& a = d.bi;
+    a.g = p.g;
+    a.tl = p.tl;
+    a.cf = cf32;
+    a.sigma = sig32;
+    a.b = d.r32;
+    a.x = d.d32;
+    a.r = v[2];
+    a.rs = v[3];
+    a.p0 = v[4];
+    a.p1 = v[5];
+    a.v0 = v[6];
+    a.v1 = v[7];
+    a.s = v[8];
+    a.t = v[9];
+    a.cm = ci;
+    a.maxit = o.inner_maxit;
+    a.tol = o.inner_tol;
+    a.reps = o.restart_eps;   // rescaled on the device for each correction solve
   }
   return HS_OK;
 }
@@ -353,9 +473,15 @@ extern "C" hs_status hs_batch_create(int nsys, const hs_op* const* ops, const in
   B->nsys = nsys;
   B->ops.resize(nsys);
   B->solvers.resize(nsys);
+  B->mixed = solvers[0] == HS_SOLVER_MIXED;
   for (int s = 0; s < nsys; s++) {
-    if (!ops[s] || (solvers[s] != HS_SOLVER_CG && solvers[s] != HS_SOLVER_BICGSTAB)) {
-      set_error("system %d: operator missing or solver not CG / BiCGStab", s);
+    if (!ops[s] || (solvers[s] != HS_SOLVER_CG && solvers[s] != HS_SOLVER_BICGSTAB && solvers[s] != HS_SOLVER_MIXED)) {
+      set_error("system %d: operator missing or solver not CG / BiCGStab / mixed", s);
+      delete B;
+      return HS_ERR_INVALID;
+    }
+    if ((solvers[s] == HS_SOLVER_MIXED) != B->mixed) {
+      set_error("system %d: a batch is either all mixed precision or all FP64", s);
       delete B;
       return HS_ERR_INVALID;
     }
@@ -406,31 +532,34 @@ extern "C" hs_status hs_batch_solve(hs_batch* B, const double* const* b, double*
     set_error("batch workspace missing, misaligned or too small (%zu < %zu)", ws_bytes, B->ws_total);
     return HS_ERR_WORKSPACE;
   }
-  double timeout_s = 2.0;
-  int use_graph = 1;
-  if (opts) {
-    if (opts->struct_size >= offsetof(hs_opts, timeout_s) + sizeof(double) && opts->timeout_s > 0)
-      timeout_s = opts->timeout_s;
-    if (opts->struct_size >= offsetof(hs_opts, use_graph) + sizeof(int)) use_graph = opts->use_graph;
-  }
+  hs_opts o;
+  if (!merge_opts(opts, &o)) return HS_ERR_INVALID;
+  const double timeout_s = o.timeout_s;
+  const int use_graph = o.use_graph;
   cudaStream_t stm = (cudaStream_t)stream;
   const int n = B->nsys;
   char* base = (char*)ws;
-  BatchSys* d_sys = (BatchSys*)base;
-  int* d_joboff = (int*)(base + align256(sizeof(BatchSys) * n));
+  void* d_sys = base;
+  int* d_joboff = (int*)(base + align256(desc_bytes(B) * n));
   BatchJob* d_jobs = (BatchJob*)((char*)d_joboff + align256(sizeof(int) * (B->grid + 1)));
   double* d_out = (double*)((char*)d_jobs + align256(sizeof(BatchJob) * std::max<size_t>(1, B->jobs.size())));
-  int* d_head = (int*)((char*)d_out + align256(sizeof(double) * 4 * n));
+  int* d_head = (int*)((char*)d_out + align256(sizeof(double) * BATCH_OUT * n));
   int* d_queue = d_head + 1;
   const int nqueue = (int)B->queue.size();
   // descriptors for this call (b, x pointers may change between calls)
-  std::vector<BatchSys> hsys(n);
+  std::vector<BatchSys> hsys(B->mixed ? 0 : n);
+  std::vector<MxSys> hmx(B->mixed ? n : 0);
   for (int s = 0; s < n; s++) {
     const hs_op* A = &B->ops[s];
     const BatchPlanSys& p = B->plan[s];
     if (!b[s] || !x[s] || ((uintptr_t)b[s] % 16) || ((uintptr_t)x[s] % 16)) {
       set_error("system %d: b and x must be 16-byte aligned device pointers", s);
       return HS_ERR_INVALID;
+    }
+    if (B->mixed) {
+      hs_status sm = fill_mixed(B, s, b[s], x[s], tol, maxit, o, base, stm, &hmx[s]);
+      if (sm != HS_OK) return sm;
+      continue;
     }
     Carve c{base + B->sys_off[s], 0, (size_t)-1, true};
     Common cm;
@@ -489,11 +618,11 @@ extern "C" hs_status hs_batch_solve(hs_batch* B, const double* const* b, double*
       a.cm = cm;
       a.maxit = maxit;
       a.tol = tol;
-      a.reps = (opts && opts->struct_size >= offsetof(hs_opts, restart_eps) + sizeof(double)) ? opts->restart_eps
-                                                                                                 : 1e-5;
+      a.reps = o.restart_eps;
     }
   }
-  cudaError_t e = cudaMemcpyAsync(d_sys, hsys.data(), sizeof(BatchSys) * n, cudaMemcpyHostToDevice, stm);
+  cudaError_t e = B->mixed ? cudaMemcpyAsync(d_sys, hmx.data(), sizeof(MxSys) * n, cudaMemcpyHostToDevice, stm)
+                           : cudaMemcpyAsync(d_sys, hsys.data(), sizeof(BatchSys) * n, cudaMemcpyHostToDevice, stm);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_joboff, B->job_off.data(), sizeof(int) * (B->grid + 1), cudaMemcpyHostToDevice, stm);
   if (e == cudaSuccess && !B->jobs.empty())
@@ -507,7 +636,10 @@ extern "C" hs_status hs_batch_solve(hs_batch* B, const double* const* b, double*
   const int ib = std::max(1, std::min(64, (n + 255) / 256));
   const size_t smem = batch_smem();
   auto launch_all = [&](cudaStream_t s) -> cudaError_t {
-    k_batch_init<<<ib, 256, 0, s>>>(d_sys, n, tns, d_head);
+    if (B->mixed)
+      return batch_mx_launch(s, B->grid, smem, (const MxSys*)d_sys, n, tns, d_joboff, d_jobs, d_queue, nqueue, d_head,
+                             d_out);
+    k_batch_init<<<ib, 256, 0, s>>>((const BatchSys*)d_sys, n, tns, d_head);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(B->grid);
     cfg.blockDim = dim3(BATCH_THREADS);
@@ -521,7 +653,7 @@ extern "C" hs_status hs_batch_solve(hs_batch* B, const double* const* b, double*
     cudaError_t le = cudaLaunchKernelEx(&cfg, k_batch, (const BatchSys*)d_sys, (const int*)d_joboff,
                                         (const BatchJob*)d_jobs, (const int*)d_queue, nqueue, d_head);
     if (le != cudaSuccess) return le;
-    k_batch_gather<<<ib, 256, 0, s>>>(d_sys, n, d_out);
+    k_batch_gather<<<ib, 256, 0, s>>>((const BatchSys*)d_sys, n, d_out);
     return cudaGetLastError();
   };
   B->graph_used = 0;
@@ -560,19 +692,22 @@ extern "C" hs_status hs_batch_solve(hs_batch* B, const double* const* b, double*
     e = launch_all(stm);
     if (e != cudaSuccess) return cuda_fail(e, "batch launch");
   }
-  std::vector<double> outh((size_t)4 * n);
-  e = cudaMemcpyAsync(outh.data(), d_out, sizeof(double) * 4 * n, cudaMemcpyDeviceToHost, stm);
+  std::vector<double> outh((size_t)BATCH_OUT * n);
+  e = cudaMemcpyAsync(outh.data(), d_out, sizeof(double) * BATCH_OUT * n, cudaMemcpyDeviceToHost, stm);
   if (e == cudaSuccess) e = cudaStreamSynchronize(stm);
   if (e != cudaSuccess) return cuda_fail(e, "batched solve");
   hs_status worst = HS_OK;
   for (int s = 0; s < n; s++) {
-    const int dsx = (int)outh[4 * s];
+    const double* q = &outh[(size_t)BATCH_OUT * s];
+    const int dsx = (int)q[0];
     hs_result& r = res[s];
     memset(&r, 0, sizeof(r));
-    r.iters = (int)outh[4 * s + 1];
-    r.rel_res = outh[4 * s + 2];
-    r.true_rel_res = -1.0;
-    r.restarts = (int)outh[4 * s + 3];
+    r.iters = (int)q[1];
+    r.rel_res = q[2];
+    r.true_rel_res = B->mixed ? q[2] : -1.0;   // a mixed system's residual is the FP64 b - A x
+    r.restarts = (int)q[3];
+    r.outer = (int)q[4];
+    r.inner_iters = (long long)q[5];
     switch (dsx) {
       case DS_CONVERGED: r.status = HS_OK; break;
       case DS_MAXIT: r.status = HS_NOT_CONVERGED; break;

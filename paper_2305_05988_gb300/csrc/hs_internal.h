@@ -118,6 +118,9 @@ hs_status run_residual_plain(const hs_op* A, hs_dtype dt, const void* b, const v
 size_t vark_coef_bytes(const hs_op* A, hs_dtype dt);
 // Fills D (diagonal, or its inverse when invert_diag), ax, ay, az in dtype dt
 // from the operator's k.
+// Options with defaults filled in and validated (false: invalid, error set).
+bool merge_opts(const hs_opts* in, hs_opts* out);
+
 hs_status setup_vark(const hs_op* A, hs_dtype dt, void* D, void* ax, void* ay, void* az, bool invert_diag,
                      cudaStream_t st);
 

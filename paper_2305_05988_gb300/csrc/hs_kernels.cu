@@ -224,14 +224,16 @@ template <typename T, int OPK, int NDIM>
 __global__ void __launch_bounds__(512) k_cg(CgArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double sh[32 * MAX_SCAL];
-  cg_body<T, OPK, NDIM>(a, grid_team(a.cm.ctrl, a.cm.partials), reinterpret_cast<T*>(smraw), sh);
+  const Team tm = grid_team(a.cm.ctrl, a.cm.partials);
+  team_finish(tm, cg_body<T, OPK, NDIM>(a, tm, reinterpret_cast<T*>(smraw), sh));
 }
 
 template <typename T, int OPK, int NDIM>
 __global__ void __launch_bounds__(512) k_bicgstab(BiArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double sh[32 * MAX_SCAL];
-  bicgstab_body<T, OPK, NDIM>(a, grid_team(a.cm.ctrl, a.cm.partials), reinterpret_cast<T*>(smraw), sh);
+  const Team tm = grid_team(a.cm.ctrl, a.cm.partials);
+  team_finish(tm, bicgstab_body<T, OPK, NDIM>(a, tm, reinterpret_cast<T*>(smraw), sh));
 }
 
 // ===========================================================================

@@ -41,6 +41,18 @@ __device__ __forceinline__ void finish(Ctrl* c, int status, int iters, double re
   }
 }
 
+// Outcome of an iteration body, identical in every block of the team (all
+// blocks take their decisions from the same reduced scalars).  ok = false:
+// a team barrier was abandoned (timeout or an error status already posted),
+// the body returned early and the control block holds the status.
+struct BodyOut {
+  int status;
+  int iters;
+  double rel;
+  int restarts;
+  bool ok;
+};
+
 // Writes the final solver outcome of a team (its lead thread only).
 __device__ __forceinline__ void team_finish(const Team& tm, int status, int iters, double rel) {
   if (tm.lead()) {
@@ -48,6 +60,11 @@ __device__ __forceinline__ void team_finish(const Team& tm, int status, int iter
     tm.ctrl->rel_res = rel;
     atomicCAS(&tm.ctrl->status, 0, status);
   }
+}
+__device__ __forceinline__ void team_finish(const Team& tm, const BodyOut& o) {
+  if (!o.ok) return;
+  if (tm.lead()) tm.ctrl->restarts = o.restarts;
+  team_finish(tm, o.status, o.iters, o.rel);
 }
 
 // ===========================================================================
@@ -173,7 +190,7 @@ struct ApDotSink {
 // The CG iteration run by one team of blocks (the whole grid for a standalone
 // solve, a subset of blocks in the batched solver).
 template <typename T, int OPK, int NDIM, int CX = cx_cg<T, OPK>()>
-__device__ void cg_body(const CgArgs<T>& a, const Team& tm, T* sm, double* sh) {
+__device__ BodyOut cg_body(const CgArgs<T>& a, const Team& tm, T* sm, double* sh) {
   const long long N = a.g.N;
   const T sig = (T)a.sigma;
 
@@ -186,20 +203,18 @@ __device__ void cg_body(const CgArgs<T>& a, const Team& tm, T* sm, double* sh) {
   }
   block_sum<2>(rsink.acc, sh);
   double s2[2];
-  if (!team_reduce<2>(tm, rsink.acc, s2, sh)) return;
+  if (!team_reduce<2>(tm, rsink.acc, s2, sh)) return BodyOut{DS_TIMEOUT, 0, -1.0, 0, false};
   double rr = s2[0];
   const double bb = s2[1];
   if (bb == 0.0) {
     for (long long i = tm.tid(); i < N; i += tm.stride()) a.x[i] = T(0);
     if (tm.lead() && a.cm.hist) a.cm.hist[0] = 0.0;
-    team_finish(tm, DS_CONVERGED, 0, 0.0);
-    return;
+    return BodyOut{DS_CONVERGED, 0, 0.0, 0, true};
   }
   double rel = sqrt(rr / bb);
   if (tm.lead() && a.cm.hist) a.cm.hist[0] = rel;
   if (rel <= a.tol || a.maxit == 0) {
-    team_finish(tm, rel <= a.tol ? DS_CONVERGED : DS_MAXIT, 0, rel);
-    return;
+    return BodyOut{rel <= a.tol ? DS_CONVERGED : DS_MAXIT, 0, rel, 0, true};
   }
 
   double beta = 0.0;
@@ -217,7 +232,7 @@ __device__ void cg_body(const CgArgs<T>& a, const Team& tm, T* sm, double* sh) {
       zmarch_item<T, NDIM, CX>(a.g, a.tl, item, sm, src, sink);
     block_sum<1>(sink.acc, sh);
     double pw[1];
-    if (!team_reduce<1>(tm, sink.acc, pw, sh)) return;
+    if (!team_reduce<1>(tm, sink.acc, pw, sh)) return BodyOut{DS_TIMEOUT, it, rel, 0, false};
     if (!(pw[0] > 0.0) || !finite_d(pw[0])) {
       status = finite_d(pw[0]) ? DS_BREAKDOWN : DS_NONFINITE;
       break;
@@ -257,7 +272,7 @@ __device__ void cg_body(const CgArgs<T>& a, const Team& tm, T* sm, double* sh) {
     }
     block_sum<1>(acc1, sh);
     double rn[1];
-    if (!team_reduce<1>(tm, acc1, rn, sh)) return;
+    if (!team_reduce<1>(tm, acc1, rn, sh)) return BodyOut{DS_TIMEOUT, it, rel, 0, false};
     rel = sqrt(rn[0] / bb);
     if (tm.lead() && a.cm.hist) a.cm.hist[it] = rel;
     if (!finite_d(rel)) {
@@ -272,7 +287,7 @@ __device__ void cg_body(const CgArgs<T>& a, const Team& tm, T* sm, double* sh) {
     rr = rn[0];
     first = false;
   }
-  team_finish(tm, status, it, rel);
+  return BodyOut{status, it, rel, 0, true};
 }
 
 // ===========================================================================
@@ -411,7 +426,7 @@ struct BiTSink {
 
 // The BiCGStab iteration run by one team of blocks.
 template <typename T, int OPK, int NDIM, int CX = CX_BI>
-__device__ void bicgstab_body(const BiArgs<T>& a, const Team& tm, T* sm, double* sh) {
+__device__ BodyOut bicgstab_body(const BiArgs<T>& a, const Team& tm, T* sm, double* sh) {
   const long long N = a.g.N;
   const T sig = (T)a.sigma;
 
@@ -423,20 +438,18 @@ __device__ void bicgstab_body(const BiArgs<T>& a, const Team& tm, T* sm, double*
   }
   block_sum<2>(rsink.acc, sh);
   double s2[2];
-  if (!team_reduce<2>(tm, rsink.acc, s2, sh)) return;
+  if (!team_reduce<2>(tm, rsink.acc, s2, sh)) return BodyOut{DS_TIMEOUT, 0, -1.0, 0, false};
   double brr = s2[0];
   const double bb = s2[1];
   if (bb == 0.0) {
     for (long long i = tm.tid(); i < N; i += tm.stride()) a.x[i] = T(0);
     if (tm.lead() && a.cm.hist) a.cm.hist[0] = 0.0;
-    team_finish(tm, DS_CONVERGED, 0, 0.0);
-    return;
+    return BodyOut{DS_CONVERGED, 0, 0.0, 0, true};
   }
   double rel = sqrt(brr / bb);
   if (tm.lead() && a.cm.hist) a.cm.hist[0] = rel;
   if (rel <= a.tol || a.maxit == 0) {
-    team_finish(tm, rel <= a.tol ? DS_CONVERGED : DS_MAXIT, 0, rel);
-    return;
+    return BodyOut{rel <= a.tol ? DS_CONVERGED : DS_MAXIT, 0, rel, 0, true};
   }
 
   double alpha_n = sqrt(brr);   // r . r' with r' = r / ||r||
@@ -459,7 +472,7 @@ __device__ void bicgstab_body(const BiArgs<T>& a, const Team& tm, T* sm, double*
       for (int item = tm.rank; item < a.tl.items(); item += tm.size)
         zmarch_item<T, NDIM, CX>(a.g, a.tl, item, sm, src, sink);
       block_sum<1>(sink.acc, sh);
-      if (!team_reduce<1>(tm, sink.acc, ad, sh)) return;
+      if (!team_reduce<1>(tm, sink.acc, ad, sh)) return BodyOut{DS_TIMEOUT, it, rel, restarts, false};
     }
     const double alpha_d = a.sigma * ad[0];
     if (alpha_d == 0.0 || !finite_d(alpha_d)) {
@@ -475,7 +488,7 @@ __device__ void bicgstab_body(const BiArgs<T>& a, const Team& tm, T* sm, double*
       for (int item = tm.rank; item < a.tl.items(); item += tm.size)
         zmarch_item<T, NDIM, CX>(a.g, a.tl, item, sm, src, sink);
       block_sum<3>(sink.acc, sh);
-      if (!team_reduce<3>(tm, sink.acc, st3, sh)) return;
+      if (!team_reduce<3>(tm, sink.acc, st3, sh)) return BodyOut{DS_TIMEOUT, it, rel, restarts, false};
     }
     const double srel = sqrt(st3[0] / bb);
     if (srel <= a.tol) {
@@ -534,7 +547,7 @@ __device__ void bicgstab_body(const BiArgs<T>& a, const Team& tm, T* sm, double*
     }
     block_sum<2>(acc4, sh);
     double rn2[2];
-    if (!team_reduce<2>(tm, acc4, rn2, sh)) return;
+    if (!team_reduce<2>(tm, acc4, rn2, sh)) return BodyOut{DS_TIMEOUT, it, rel, restarts, false};
     rel = sqrt(rn2[1] / bb);
     if (tm.lead() && a.cm.hist) a.cm.hist[it] = rel;
     if (!finite_d(rel) || !finite_d(rn2[0])) {
@@ -556,8 +569,7 @@ __device__ void bicgstab_body(const BiArgs<T>& a, const Team& tm, T* sm, double*
       alpha_n = rn2[0];
     }
   }
-  if (tm.lead()) a.cm.ctrl->restarts = restarts;
-  team_finish(tm, status, it, rel);
+  return BodyOut{status, it, rel, restarts, true};
 }
 
 // ---------------------------------------------------------------------------

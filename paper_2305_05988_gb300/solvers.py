@@ -331,7 +331,11 @@ def diffusion_solve(logk: torch.Tensor, f: torch.Tensor, shape, tol: float = 1e-
 class Batch:
     """Many independent systems solved by one persistent kernel (CUDA graph).
 
-    ops: list of Operators; solvers: list of "cg" / "bicgstab" (one per system).
+    ops: list of Operators; solvers: list of "cg" / "bicgstab" (one per system),
+    or "mixed" for every system: FP64 iterative refinement per system with an
+    FP32 inner CG (symmetric operators) or BiCGStab (upwind operator); then
+    maxit bounds the refinement steps and inner_tol / inner_maxit the inner
+    solves.
     """
 
     def __init__(self, ops, solvers, autotune: bool = False):
@@ -340,7 +344,8 @@ class Batch:
             raise ValueError("need one solver per operator")
         self.ops = list(ops)
         self.n = len(ops)
-        code = {"cg": _lib.HS_SOLVER_CG, "bicgstab": _lib.HS_SOLVER_BICGSTAB}
+        code = {"cg": _lib.HS_SOLVER_CG, "bicgstab": _lib.HS_SOLVER_BICGSTAB, "mixed": _lib.HS_SOLVER_MIXED}
+        self.mixed = solvers[0] == "mixed"
         arr_ops = (ctypes.c_void_p * self.n)(*[o._op.value for o in self.ops])
         arr_sol = (ctypes.c_int * self.n)(*[code[s] for s in solvers])
         self._b = ctypes.c_void_p()
@@ -403,5 +408,6 @@ class Batch:
         if status in (_lib.HS_ERR_INVALID, _lib.HS_ERR_CUDA, _lib.HS_ERR_WORKSPACE):
             raise _lib.HsError(status, "hs_batch_solve")
         infos = [SolveInfo(iters=r.iters, status=_lib.STATUS_NAMES.get(r.status, str(r.status)), status_code=r.status,
-                           rel_res=r.rel_res, true_rel_res=r.true_rel_res, restarts=r.restarts) for r in res]
+                           rel_res=r.rel_res, true_rel_res=r.true_rel_res, restarts=r.restarts, outer=r.outer,
+                           inner_iters=r.inner_iters) for r in res]
         return xs, infos

@@ -129,3 +129,94 @@ def test_batch_zero_rhs_and_maxit():
     s.synchronize()
     assert infos[0].status == "OK" and infos[0].iters == 0 and torch.count_nonzero(xs[0]).item() == 0
     assert infos[1].status == "NOT_CONVERGED" and infos[1].iters == 3
+
+
+def build_mixed(systems, seed=0, vark_every=0):
+    """Like build(), with every `vark_every`-th CG system on a variable-k
+    diffusion operator (log k ~ N(0, 1))."""
+    ops_o, ops_g, bs, ks = [], [], [], []
+    for q, bsys in enumerate(systems):
+        shape = bsys.shape
+        if bsys.solver == "cg" and vark_every and q % vark_every == 0:
+            k = np.exp(inputs.log_k(shape, 1.0, seed + q))
+            ops_o.append(oracle.Operator(shape, oracle.DIFFUSION, k=k))
+            kt = dev(k)
+            ks.append(kt)
+            ops_g.append(hs.Operator.diffusion(shape, kt))
+        elif bsys.solver == "cg":
+            ops_o.append(oracle.Operator(shape))
+            ops_g.append(hs.Operator.laplacian(shape))
+        else:
+            beta = inputs.upwind_beta(shape, bsys.peclet)
+            ops_o.append(oracle.Operator(shape, oracle.UPWIND, beta))
+            ops_g.append(hs.Operator.upwind(shape, beta))
+        bs.append(inputs.uniform_pm1(seed, inputs.STREAM_BATCH_RHS + bsys.index, bsys.N))
+    return ops_o, ops_g, bs, ks
+
+
+def test_batch_mixed_precision_certified_by_oracle():
+    # FP64 refinement with FP32 inner solves reaches an FP64 residual of 1e-10
+    # (below what FP32 alone can represent); the oracle's FP64 SpMV certifies
+    # every system and its FP64 solution agrees to the conditioning bound
+    systems = small_batch(24, 36, seed=13)
+    ops_o, ops_g, bs, _ks = build_mixed(systems, vark_every=4)
+    batch = hs.Batch(ops_g, ["mixed"] * len(ops_g))
+    tol = 1e-10
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        xs, infos = batch.solve([dev(b) for b in bs], tol=tol, maxit=30, inner_tol=1e-4, inner_maxit=20000)
+    s.synchronize()
+    for k, (A_o, b, x, info, bsys) in enumerate(zip(ops_o, bs, xs, infos, systems)):
+        assert info.status == "OK", (k, bsys, info)
+        assert info.outer >= 2 and info.inner_iters > 0 and info.iters == info.outer, (k, info)
+        xh = x.cpu().numpy()
+        rr = A_o.relres(b, xh)
+        assert rr <= tol * (1 + 1e-3), (k, bsys, rr)
+        # the device's FP64 residual norm is the oracle's up to the rounding of b - A x
+        assert abs(info.rel_res - rr) <= 0.05 * rr + 1e-13, (k, info.rel_res, rr)
+        if bsys.solver == "cg":
+            x_o, _, _, _ = oracle.cg(A_o, b, tol=1e-13, maxit=20000)
+        else:
+            x_o, _, _, _, _ = oracle.bicgstab(A_o, b, tol=1e-13, maxit=20000)
+        # ||x - x*|| / ||x*|| <= cond(A) * ||r|| / ||b||; cond <= 4 (n+1)^2 / pi^2 for these grids
+        n = max(bsys.shape)
+        bound = 4.0 * (n + 1) ** 2 / np.pi ** 2 * 1e-10 * 10
+        assert np.linalg.norm(xh - x_o) <= bound * np.linalg.norm(x_o), (k, bsys)
+
+
+def test_batch_mixed_matches_standalone_mixed_counts():
+    # one system alone in a batch runs the standalone refinement's arithmetic
+    # up to the power-of-two residual scaling: same outer steps, inner counts
+    # within a few iterations
+    shape = (40, 36, 30)
+    A = hs.Operator.laplacian(shape)
+    b = dev(inputs.uniform_pm1(0, 77, int(np.prod(shape))))
+    batch = hs.Batch([A], ["mixed"])
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        xb, ib = batch.solve([b], tol=1e-10, maxit=20, inner_tol=1e-4)
+        xs, info = hs.solve_mixed(A, b, tol=1e-10, maxit=20, inner_tol=1e-4)
+    s.synchronize()
+    assert ib[0].status == "OK" and info.status == "OK"
+    assert ib[0].outer == info.outer
+    assert abs(ib[0].inner_iters - info.inner_iters) <= 3 * info.outer, (ib[0], info)
+    assert torch.linalg.norm(xb[0] - xs).item() <= 1e-8 * torch.linalg.norm(xs).item()
+
+
+def test_batch_mixed_poisoned_and_all_or_none():
+    systems = small_batch(12, 20, seed=17)
+    ops_o, ops_g, bs, _ = build_mixed(systems)
+    bad = 3
+    bs[bad] = bs[bad].copy()
+    bs[bad][5] = np.inf
+    batch = hs.Batch(ops_g, ["mixed"] * len(ops_g))
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        xs, infos = batch.solve([dev(b) for b in bs], tol=1e-10, maxit=30, inner_tol=1e-4)
+    s.synchronize()
+    assert infos[bad].status == "ERR_NONFINITE"
+    for k, (A_o, b, x, info) in enumerate(zip(ops_o, bs, xs, infos)):
+        if k != bad:
+            assert info.status == "OK" and A_o.relres(b, x.cpu().numpy()) <= 1e-10 * (1 + 1e-3)
+    with pytest.raises(hs.HsError):
+        hs.Batch(ops_g[:2], ["mixed", "cg"])

@@ -97,7 +97,10 @@ def test_krylov_full_size_against_golden_counts(rhs, solver):
         A_o, A_g = oracle.Operator(N3, oracle.UPWIND, beta), hs.Operator.upwind(N3, beta)
         x, info = hs.bicgstab(A_g, bt, tol=1e-10, maxit=20000)
     assert info.status == "OK"
-    assert abs(info.iters - g["iters"]) <= 2, (info.iters, g)
+    # +-2, or when the oracle restarted BiCGStab (absolute restart threshold:
+    # where restarts fire depends on rounding) 2 + 10 %, as in parity_util
+    slack = 2 + (math.ceil(0.10 * g["iters"]) if g.get("restarts", 0) > 0 else 0)
+    assert abs(info.iters - g["iters"]) <= slack, (info.iters, g)
     assert A_o.relres(b, x.cpu().numpy()) <= 1e-10 * (1 + 1e-3)
 
 
