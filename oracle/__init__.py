@@ -83,6 +83,12 @@ def _load():
             lib.ora_bicgstab.argtypes = [op, dp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                          dp, P(ctypes.c_int), P(ctypes.c_int)]
             lib.ora_bicgstab.restype = ctypes.c_int
+            lib.ora_cg_nb.argtypes = [op, dp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_int, dp,
+                                      P(ctypes.c_int)]
+            lib.ora_cg_nb.restype = ctypes.c_int
+            lib.ora_bicgstab_b1.argtypes = [op, dp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                            dp, P(ctypes.c_int), P(ctypes.c_int)]
+            lib.ora_bicgstab_b1.restype = ctypes.c_int
             lib.ora_grad_logk.argtypes = [op, dp, dp, dp]; lib.ora_grad_logk.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -220,6 +226,30 @@ def bicgstab(A: Operator, b, x0=None, maxit=1000, tol=1e-10, restart_eps=1e-5):
     nr = ctypes.c_int(0)
     st = _load().ora_bicgstab(A._ref(), _ptr(b), _ptr(x), int(maxit), float(tol), float(restart_eps),
                               _ptr(h), ctypes.byref(it), ctypes.byref(nr))
+    return x, it.value, st, h[: it.value + 1], nr.value
+
+
+def cg_nb(A: Operator, b, x0=None, maxit=1000, tol=1e-10, paper_order=False):
+    """CG-NB (Algorithm 1); returns (x, iters, status, hist)."""
+    b = _f64(b).reshape(-1)
+    x = np.zeros(A.N) if x0 is None else _f64(x0).reshape(-1).copy()
+    h = _hist(maxit, True)
+    it = ctypes.c_int(0)
+    st = _load().ora_cg_nb(A._ref(), _ptr(b), _ptr(x), int(maxit), float(tol), int(bool(paper_order)), _ptr(h),
+                           ctypes.byref(it))
+    return x, it.value, st, h[: it.value + 1]
+
+
+def bicgstab_b1(A: Operator, b, x0=None, maxit=1000, tol=1e-10, restart_eps=1e-5):
+    """BiCGStab in the statement order of Algorithm 2 (late test, final step);
+    returns (x, iters, status, hist, restarts)."""
+    b = _f64(b).reshape(-1)
+    x = np.zeros(A.N) if x0 is None else _f64(x0).reshape(-1).copy()
+    h = _hist(maxit, True)
+    it = ctypes.c_int(0)
+    nr = ctypes.c_int(0)
+    st = _load().ora_bicgstab_b1(A._ref(), _ptr(b), _ptr(x), int(maxit), float(tol), float(restart_eps),
+                                 _ptr(h), ctypes.byref(it), ctypes.byref(nr))
     return x, it.value, st, h[: it.value + 1], nr.value
 
 

@@ -420,6 +420,154 @@ done:
 }
 
 /* ------------------------------------------------------------------------ */
+/* CG-NB, the paper's nonblocking CG (section 3.2, Algorithm 1): the SpMV is */
+/* applied to r_j and A p_j follows from the recurrence                     */
+/*   A p_j = A r_j + (alpha_n,j / alpha_n,j-1) A p_j-1,                      */
+/* the search direction p_j = r_j + (alpha_n,j / alpha_n,j-1) p_j-1 and      */
+/*   x_j = x_j-1 + alpha_n,j-1^2 / (alpha_d,j-1 alpha_n,j) (p_j - r_j),      */
+/* with alpha_n = r.r, alpha_d = (A p).p.  The printed x update carries a    */
+/* minus sign; with r_j = r_j-1 - alpha_j-1 A p_j-1 the derivation gives     */
+/* plus (p_j - r_j = beta_j p_j-1), the reading used here.                   */
+/* Stopping: relative residual sqrt(alpha_n,j)/||b|| <= tol tested at the     */
+/* end of iteration j, returning x_j (iters = j).  paper_order = 1 tests at  */
+/* the top of the next iteration instead and applies the printed final      */
+/* step x = x_l + alpha_l p_l after the loop.                               */
+/* ------------------------------------------------------------------------ */
+
+int ora_cg_nb(const ora_op *A, const double *b, double *x, int maxit, double tol,
+              int paper_order, double *hist, int *iters)
+{
+    int64_t N = ora_size(A);
+    double *r = (double *)malloc((size_t)N * sizeof(double));
+    double *p = (double *)malloc((size_t)N * sizeof(double));
+    double *Ap = (double *)malloc((size_t)N * sizeof(double));
+    double *Ar = (double *)malloc((size_t)N * sizeof(double));
+    int status = ORA_NOT_CONVERGED, it = 0;
+    if (!r || !p || !Ap || !Ar) { status = -1; goto done; }
+    double bn = sqrt(ora_dot(N, b, b));
+    if (bn == 0.0) {
+        for (int64_t i = 0; i < N; i++) x[i] = 0.0;
+        if (hist) hist[0] = 0.0;
+        status = ORA_OK;
+        goto done;
+    }
+    /* r0 = b - A x0, p0 = r0, alpha_0 = (r0.r0) / ((A p0).p0) */
+    ora_residual(A, b, x, r);
+    for (int64_t i = 0; i < N; i++) p[i] = r[i];
+    ora_spmv(A, p, Ap);
+    double an = ora_dot(N, r, r);
+    double ad = ora_dot(N, Ap, p);
+    if (hist) hist[0] = sqrt(an) / bn;
+    if (sqrt(an) / bn <= tol) { status = ORA_OK; goto done; }
+    if (!(ad > 0.0)) { status = ORA_BREAKDOWN; goto done; }
+    double alpha = an / ad;
+    for (it = 1; it <= maxit; it++) {
+        if (paper_order && sqrt(an) / bn <= tol && it > 1) { it--; status = ORA_OK; break; }
+        for (int64_t i = 0; i < N; i++) r[i] -= alpha * Ap[i];
+        double an_new = ora_dot(N, r, r);
+        double beta = an_new / an;
+        ora_spmv(A, r, Ar);
+        for (int64_t i = 0; i < N; i++) Ap[i] = Ar[i] + beta * Ap[i];
+        for (int64_t i = 0; i < N; i++) p[i] = r[i] + beta * p[i];
+        double ad_new = ora_dot(N, Ap, p);
+        double c = an * an / (ad * an_new);
+        for (int64_t i = 0; i < N; i++) x[i] += c * (p[i] - r[i]);
+        if (hist) hist[it] = sqrt(an_new) / bn;
+        an = an_new;
+        ad = ad_new;
+        if (!paper_order && sqrt(an) / bn <= tol) { status = ORA_OK; break; }
+        if (!(ad > 0.0)) { status = ORA_BREAKDOWN; break; }
+        alpha = an / ad;
+    }
+    if (it > maxit) it = maxit;
+    if (paper_order && status != ORA_BREAKDOWN) {
+        /* the printed final step x = x_l + alpha_l p_l */
+        for (int64_t i = 0; i < N; i++) x[i] += alpha * p[i];
+        if (status != ORA_OK && sqrt(an) / bn <= tol) status = ORA_OK;
+    }
+done:
+    *iters = it;
+    free(r); free(p); free(Ap); free(Ar);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* BiCGStab-B1, the statement order of Algorithm 2 (section 3.2): in        */
+/* iteration j the convergence test on beta_j = r_j.r_j comes after         */
+/* alpha_d,j, s_j, omega_j and x_j+1/2 = x_j + alpha_j p_j, and the loop     */
+/* ends with the printed final step x = x_l + omega_l s_l, so the returned   */
+/* iterate is x_l+1 for the first l with sqrt(beta_l)/||b|| <= tol           */
+/* (iters = l + 1 SpMV pairs).  Restart as in ora_bicgstab.                 */
+/* ------------------------------------------------------------------------ */
+
+int ora_bicgstab_b1(const ora_op *A, const double *b, double *x, int maxit, double tol,
+                    double restart_eps, double *hist, int *iters, int *restarts)
+{
+    int64_t N = ora_size(A);
+    double *r = (double *)malloc((size_t)N * sizeof(double));
+    double *rs = (double *)malloc((size_t)N * sizeof(double));
+    double *p = (double *)malloc((size_t)N * sizeof(double));
+    double *Ap = (double *)malloc((size_t)N * sizeof(double));
+    double *s = (double *)malloc((size_t)N * sizeof(double));
+    double *As = (double *)malloc((size_t)N * sizeof(double));
+    int status = ORA_NOT_CONVERGED, it = 0, nrestart = 0;
+    if (!r || !rs || !p || !Ap || !s || !As) { status = -1; goto done; }
+    double bn = sqrt(ora_dot(N, b, b));
+    if (bn == 0.0) {
+        for (int64_t i = 0; i < N; i++) x[i] = 0.0;
+        if (hist) hist[0] = 0.0;
+        status = ORA_OK;
+        goto done;
+    }
+    ora_residual(A, b, x, r);
+    double beta_j = ora_dot(N, r, r);
+    if (hist) hist[0] = sqrt(beta_j) / bn;
+    if (sqrt(beta_j) / bn <= tol) { status = ORA_OK; goto done; }
+    for (int64_t i = 0; i < N; i++) rs[i] = r[i] / sqrt(beta_j);
+    double an = ora_dot(N, r, rs);
+    for (int64_t i = 0; i < N; i++) p[i] = r[i];
+    while (it < maxit) {
+        ora_spmv(A, p, Ap);
+        double ad = ora_dot(N, Ap, rs);
+        if (ad == 0.0 || !isfinite(ad)) { status = ORA_BREAKDOWN; break; }
+        double alpha = an / ad;
+        for (int64_t i = 0; i < N; i++) s[i] = r[i] - alpha * Ap[i];
+        ora_spmv(A, s, As);
+        double num = ora_dot(N, As, s), den = ora_dot(N, As, As);
+        if (den == 0.0 || !isfinite(den)) { status = ORA_BREAKDOWN; break; }
+        double omega = num / den;
+        for (int64_t i = 0; i < N; i++) x[i] += alpha * p[i];            /* x_j+1/2 */
+        it++;
+        if (sqrt(beta_j) / bn <= tol) {                                  /* late test */
+            for (int64_t i = 0; i < N; i++) x[i] += omega * s[i];        /* final step */
+            status = ORA_OK;
+            break;
+        }
+        for (int64_t i = 0; i < N; i++) x[i] += omega * s[i];
+        for (int64_t i = 0; i < N; i++) r[i] = s[i] - omega * As[i];
+        double an_new = ora_dot(N, r, rs);
+        beta_j = ora_dot(N, r, r);
+        if (hist) hist[it] = sqrt(beta_j) / bn;
+        for (int64_t i = 0; i < N; i++) Ap[i] = p[i] - omega * Ap[i];   /* p_j+1/2, stored in Ap */
+        if (restart_eps > 0.0 && sqrt(fabs(an_new)) < restart_eps) {
+            for (int64_t i = 0; i < N; i++) p[i] = r[i];
+            for (int64_t i = 0; i < N; i++) rs[i] = r[i] / sqrt(beta_j);
+            an = ora_dot(N, r, rs);
+            nrestart++;
+        } else {
+            double c = an_new / (ad * omega);
+            for (int64_t i = 0; i < N; i++) p[i] = r[i] + c * Ap[i];
+            an = an_new;
+        }
+    }
+done:
+    *iters = it;
+    if (restarts) *restarts = nrestart;
+    free(r); free(rs); free(p); free(Ap); free(s); free(As);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Adjoint gradient of L(u) for the diffusion operator.                     */
 /* With A(k) u = f and lambda solving A^T lambda = dL/du:                   */
 /*   dL/dk_i = -lambda^T (dA/dk_i) u                                        */

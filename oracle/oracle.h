@@ -36,6 +36,10 @@ int ora_cg(const ora_op *A, const double *b, double *x, int maxit, double tol,
            double *hist, int *iters);
 int ora_bicgstab(const ora_op *A, const double *b, double *x, int maxit, double tol,
                  double restart_eps, double *hist, int *iters, int *restarts);
+int ora_cg_nb(const ora_op *A, const double *b, double *x, int maxit, double tol,
+              int paper_order, double *hist, int *iters);
+int ora_bicgstab_b1(const ora_op *A, const double *b, double *x, int maxit, double tol,
+                    double restart_eps, double *hist, int *iters, int *restarts);
 int ora_grad_logk(const ora_op *A, const double *u, const double *lam, double *g);
 
 #endif

@@ -391,6 +391,83 @@ def test_bicgstab_restart_fires_and_both_converge():
 
 
 # --------------------------------------------------------------------------
+# CG-NB (Algorithm 1) and BiCGStab-B1 (Algorithm 2's statement order)
+# --------------------------------------------------------------------------
+
+# 1-D grids are left out: there CG terminates (residual at rounding level)
+# and Algorithm 1's x update, which divides by alpha_n,j, turns the rounding
+# noise of p_j - r_j into an O(1e-4) error (a property of the printed update).
+@pytest.mark.parametrize("shape", [(5, 4), (3, 4, 5), (12, 11), (6, 6)])
+def test_cg_nb_dense_lu(shape):
+    M = laplacian_dense(shape)
+    b = inputs.uniform_pm1(21, 1, M.shape[0])
+    ref = sla.lu_solve(sla.lu_factor(M), b)
+    x, it, st, hist = oracle.cg_nb(oracle.Operator(shape), b, maxit=200, tol=1e-13)
+    assert st == oracle.OK
+    assert np.linalg.norm(x - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_cg_nb_equals_classical_cg_iterates():
+    # arithmetically equivalent to CG (section 3.2): the same iterate after k
+    # iterations up to rounding.  A wrong sign in the x update (the printed
+    # minus) would move x away from the CG iterate by 2 alpha p per step.
+    shape = (23, 17)
+    A = oracle.Operator(shape)
+    b = inputs.rhs_uniform(shape, 7)
+    for k in (1, 2, 5, 20, 60):
+        xc, itc, _, _ = oracle.cg(A, b, maxit=k, tol=0.0)
+        xn, itn, _, _ = oracle.cg_nb(A, b, maxit=k, tol=0.0)
+        assert itc == itn == k
+        assert np.linalg.norm(xn - xc) <= 1e-10 * np.linalg.norm(xc), k
+
+
+def test_cg_nb_count_and_finite_termination():
+    shape = (20, 17)
+    A = oracle.Operator(shape)
+    b = inputs.rhs_uniform(shape, 5)
+    _, itc, _, hc = oracle.cg(A, b, tol=1e-10, maxit=2000)
+    x, itn, st, hn = oracle.cg_nb(A, b, tol=1e-10, maxit=2000)
+    assert st == oracle.OK and abs(itn - itc) <= 1
+    assert A.relres(b, x) <= 1e-10 * (1 + 1e-3)
+    M = laplacian_dense((4, 4))
+    distinct = len(np.unique(np.round(np.linalg.eigvalsh(M) / 8.0, 10)))
+    _, it, st, _ = oracle.cg_nb(oracle.Operator((4, 4)), inputs.uniform_pm1(12, 1, 16), maxit=100, tol=1e-11)
+    assert st == oracle.OK and it <= distinct
+
+
+def test_cg_nb_paper_order_returns_next_iterate():
+    # the printed order tests at the top of the next iteration and then
+    # applies x = x_l + alpha_l p_l: the CG iterate one step further
+    shape = (19, 13)
+    A = oracle.Operator(shape)
+    b = inputs.rhs_uniform(shape, 9)
+    _, l, st, _ = oracle.cg_nb(A, b, tol=1e-8, maxit=2000)
+    xp, lp, stp, _ = oracle.cg_nb(A, b, tol=1e-8, maxit=2000, paper_order=True)
+    xc, _, _, _ = oracle.cg(A, b, maxit=l + 1, tol=0.0)
+    assert st == stp == oracle.OK and lp == l
+    assert np.linalg.norm(xp - xc) <= 1e-9 * np.linalg.norm(xc)
+
+
+def test_bicgstab_b1_late_test_and_final_step():
+    # B1 detects ||r_l|| <= tol inside iteration l+1 and completes that
+    # iteration: the classical iterate x_{l+1} (without the half-step exit)
+    shape = (14, 11)
+    beta = inputs.upwind_beta(shape, 0.5)
+    A = oracle.Operator(shape, oracle.UPWIND, beta)
+    b = inputs.rhs_uniform(shape, 4)
+    ref = np.linalg.solve(upwind_dense(shape, beta), b)
+    xb, itb, stb, hb, nrb = oracle.bicgstab_b1(A, b, tol=1e-9, maxit=2000, restart_eps=0.0)
+    assert stb == oracle.OK and nrb == 0
+    l = itb - 1
+    assert hb[l] <= 1e-9 and (l == 0 or hb[l - 1] > 1e-9)
+    xc, itc, _, _, _ = oracle.bicgstab(A, b, tol=0.0, maxit=itb, restart_eps=0.0)
+    assert itc == itb
+    assert np.linalg.norm(xb - xc) <= 1e-10 * np.linalg.norm(xc)
+    xs, _, st, _, _ = oracle.bicgstab_b1(A, b, tol=1e-13, maxit=2000)
+    assert st == oracle.OK and np.linalg.norm(xs - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+# --------------------------------------------------------------------------
 # Adjoint gradient
 # --------------------------------------------------------------------------
 
