@@ -81,6 +81,9 @@ def parse():
     p.add_argument("--mixed-n", type=int, default=512, help="grid side of the mixed-precision comparison (0: skip)")
     p.add_argument("--adjoint-n", type=int, default=256, help="grid side of the adjoint-gradient timing (0: skip)")
     p.add_argument("--batch-n", type=int, default=512, help="systems in the batched comparison (0: skip)")
+    p.add_argument("--no-variants", action="store_true", help="skip the CG-NB / BiCGStab-B1 comparison")
+    p.add_argument("--hpcg-nz", type=int, default=6144,
+                   help="z extent of the HPCG 128 x 128 x nz timing (the paper's node: 6144; 0: skip)")
     p.add_argument("--batch-vark", action="store_true",
                    help="batched comparison: CG systems on variable-k diffusion (log k ~ N(0, 1))")
     return p.parse_args()
@@ -416,6 +419,10 @@ def run_ours(args, rank, world, dist):
         extras["adjoint"] = adjoint_timing(args.adjoint_n, dev, tmo)
     if rank == 0 and args.batch_n > 0:
         extras["batched"] = batch_comparison(args.batch_n, dev, tmo, args.batch_vark)
+    if rank == 0 and not args.no_variants:
+        extras["paper_variants"] = variant_comparison(n, dev, tmo)
+    if rank == 0 and args.hpcg_nz > 0:
+        extras["hpcg"] = hpcg_timing(args.hpcg_nz, dev, tmo)
 
     # kernels launched per step: spmv 1; jacobi, cg, bicgstab: control init +
     # persistent solver + residual + finalize = 4 each; gauss-seidel: solver +
@@ -435,6 +442,79 @@ def run_ours(args, rank, world, dist):
             "extras": extras,
         }
         print(json.dumps(line), flush=True)
+
+
+def hpcg_timing(nz, dev, tmo):
+    """The paper's own benchmark system (section 4.1) on the grid of one of its
+    nodes, 128 x 128 x nz (nz = 6144: 48 ranks of 128^3): HPCG's 7- and 27-point
+    matrices (diagonal 27, -1 per neighbour), b = A 1, x0 = 0, absolute
+    criterion ||r|| < 1e-6.  Time to criterion and per iteration for CG, CG-NB,
+    BiCGStab and Jacobi, with the paper's printed iteration counts beside ours
+    (its per-iteration times on a 48-core node are context, not a target)."""
+    import torch
+
+    import paper_2305_05988_gb300 as hs
+    shape = (128, 128, nz)
+    stream = torch.cuda.current_stream(dev)
+    paper = {"hpcg7": {"cg": 12, "bicgstab": 8, "jacobi": 18}, "hpcg27": {"cg": 72, "bicgstab": 45, "jacobi": 515}}
+    out = {"workload": "HPCG %dx%dx%d, b = A 1, x0 = 0, ||r|| < 1e-6" % shape}
+    for pts in (7, 27):
+        A = hs.Operator.hpcg(shape, pts)
+        b = A.spmv(torch.ones(A.N, dtype=torch.float64, device=dev))
+        tol = 1e-6 / torch.linalg.norm(b).item()
+        rec = {}
+        for name, fn in (("cg", hs.cg), ("cg_nb", hs.cg_nb), ("bicgstab", hs.bicgstab), ("jacobi", hs.jacobi)):
+            fn(A, b, tol=tol, maxit=5000, history=False, true_residual=False, timeout_s=max(tmo, 10.0))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            x, info = fn(A, b, tol=tol, maxit=5000, history=False, true_residual=False, timeout_s=max(tmo, 10.0))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            rec[name] = {"ms": round(ms, 3), "iters": info.iters, "paper_iters": paper["hpcg%d" % pts].get(name),
+                         "us_per_iter": round(1e3 * ms / max(info.iters, 1), 2), "status": info.status,
+                         "max_err_vs_ones": torch.max(torch.abs(x - 1.0)).item()}
+            del x
+        out["hpcg%d" % pts] = rec
+        del A, b
+    torch.cuda.empty_cache()
+    return out
+
+
+def variant_comparison(n, dev, tmo):
+    """The paper's proposed variants on the step's systems: CG-NB (Algorithm 1,
+    one fused pass and one grid reduction per iteration) against classical CG
+    on the Laplacian, and BiCGStab in Algorithm 2's order (B1) against the
+    classical order on the upwind operator; time to 1e-10 and per iteration."""
+    import torch
+
+    import paper_2305_05988_gb300 as hs
+    from paper_2305_05988_gb300 import inputs
+    shape = (n, n, n)
+    b = torch.from_numpy(inputs.rhs_uniform(shape, 0)).to(dev)
+    A = hs.Operator.laplacian(shape)
+    U = hs.Operator.upwind(shape, inputs.upwind_beta(shape, 0.5))
+    stream = torch.cuda.current_stream(dev)
+    out = {"workload": "%d^3: CG / CG-NB on the Laplacian, BiCGStab / B1 on upwind (Pe 0.5), tol 1e-10" % n}
+    runs = (("cg", hs.cg, A, {}), ("cg_nb", hs.cg_nb, A, {}), ("bicgstab", hs.bicgstab, U, {}),
+            ("bicgstab_b1", hs.bicgstab, U, {"paper_order": True}))
+    for name, fn, op, kw in runs:
+        fn(op, b, tol=1e-10, maxit=20000, history=False, true_residual=False, timeout_s=max(tmo, 10.0), **kw)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        x, info = fn(op, b, tol=1e-10, maxit=20000, history=False, true_residual=False,
+                     timeout_s=max(tmo, 10.0), **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[name] = {"ms": round(ms, 2), "iters": info.iters, "us_per_iter": round(1e3 * ms / max(info.iters, 1), 2),
+                     "status": info.status, "true_rel_res": op.residual(b, x).norm().item() / b.norm().item()}
+    out["cg_nb_speedup"] = round(out["cg"]["ms"] / out["cg_nb"]["ms"], 3)
+    del b, A, U
+    torch.cuda.empty_cache()
+    return out
 
 
 def mixed_comparison(n, dev, tmo):

@@ -63,7 +63,8 @@ typedef enum {
     HS_SOLVER_GAUSS_SEIDEL = 1,
     HS_SOLVER_CG = 2,
     HS_SOLVER_BICGSTAB = 3,
-    HS_SOLVER_MIXED = 4      /* hs_solve_mixed (dtype HS_F64) */
+    HS_SOLVER_MIXED = 4,     /* hs_solve_mixed (dtype HS_F64) */
+    HS_SOLVER_CG_NB = 5      /* hs_cg_nb */
 } hs_solver;
 
 typedef enum { HS_GS_FORWARD = 0, HS_GS_BACKWARD = 1, HS_GS_SYMMETRIC = 2 } hs_gs_mode;
@@ -100,6 +101,14 @@ typedef struct {
                                built-in cost model                             */
     int max_blocks;         /* cap on the persistent grid (blocks); 0 = all
                                co-resident blocks                               */
+    int paper_order;        /* 1: the statement order printed in Algorithms 1-2
+                               (convergence tested at the top of the next
+                               iteration / after omega, then the final step
+                               x = x_l + alpha_l p_l (CG-NB) or
+                               x = x_l + omega_l s_l (BiCGStab), which returns
+                               the iterate one step beyond the converged one);
+                               0 (default): test right after each residual
+                               update and return that iterate                   */
 } hs_opts;
 
 typedef struct {
@@ -123,6 +132,17 @@ void hs_grid_destroy(hs_grid *g);
 
 /* Operators keep a copy of the grid; the grid may be destroyed afterwards. */
 hs_status hs_op_laplacian(const hs_grid *g, hs_op **out);
+/* The benchmark system of section 4.1 (HPCG's generated matrix, unscaled):
+ * diagonal 27 and -1 for each of the 6 face neighbours (points = 7) or the 26
+ * neighbours of the 3x3x3 box (points = 27, 3-D grids only) inside the grid.
+ * The paper solves it with b = A 1 (exact solution x = 1) from x0 = 0 to an
+ * absolute residual of 1e-6.  The coefficients are the reading that fits the
+ * paper's printed iteration counts.  The 27-point operator supports SpMV,
+ * residual, Jacobi, CG, CG-NB, BiCGStab and mixed precision; lexicographic
+ * Gauss-Seidel and the batched solver return HS_ERR_INVALID for it.
+ * HS_ERR_INVALID: points not 7 or 27, a 27-point operator on a 1-/2-D grid. */
+hs_status hs_op_hpcg(const hs_grid *g, int points, hs_op **out);
+
 /* beta[d] >= 0 and finite for d < ndim (first-order upwind). */
 hs_status hs_op_convdiff_upwind(const hs_grid *g, const double beta[3], hs_op **out);
 /* k_dev: device array of N coefficients (> 0) of type kdt, BORROWED: it must
@@ -183,9 +203,23 @@ hs_status hs_cg(const hs_op *A, hs_dtype dtype, const void *b, void *x, double t
                 const hs_opts *opts, void *ws, size_t ws_bytes, void *stream, hs_result *res,
                 double *hist);
 
+/* CG-NB, the paper's nonblocking CG (section 3.2, Algorithm 1): the SpMV is
+ * applied to r_j and A p_j = A r_j + beta_j A p_j-1 follows by recurrence.
+ * One fused pass and ONE reduce-barrier per iteration: the denominator
+ * (A p_j).p_j is expanded as r_j.A r_j - beta_j (r_j.r_j) / alpha_j-1 (equal in
+ * exact arithmetic for symmetric A), so r.r and r.A r are reduced together.
+ * A must be symmetric positive definite.  x is updated as x_j-1 + alpha_j-1
+ * p_j-1 (Algorithm 1's x_j-1 + c (p_j - r_j) with c (p_j - r_j) = alpha_j-1
+ * p_j-1).  Workspace: hs_workspace_size(A, HS_SOLVER_CG_NB, ...). */
+hs_status hs_cg_nb(const hs_op *A, hs_dtype dtype, const void *b, void *x, double tol, int maxit,
+                   const hs_opts *opts, void *ws, size_t ws_bytes, void *stream, hs_result *res,
+                   double *hist);
+
 /* BiCGStab with the shadow residual r' = r0/||r0|| and the restart rule of
  * Algorithm 2 (restart when sqrt|alpha_n| < restart_eps: p = r, r' = r/||r||),
- * classical statement order (convergence tested after each residual update). */
+ * classical statement order (convergence tested after each residual update);
+ * opts.paper_order = 1 gives Algorithm 2's order (BiCGStab-B1: test on the
+ * previous residual after omega, then the final step x = x_l + omega_l s_l). */
 hs_status hs_bicgstab(const hs_op *A, hs_dtype dtype, const void *b, void *x, double tol,
                       int maxit, const hs_opts *opts, void *ws, size_t ws_bytes, void *stream,
                       hs_result *res, double *hist);

@@ -32,7 +32,7 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-LAPLACIAN, UPWIND, DIFFUSION = 0, 1, 2
+LAPLACIAN, UPWIND, DIFFUSION, HPCG7, HPCG27 = 0, 1, 2, 3, 4
 GS_FORWARD, GS_BACKWARD, GS_SYMMETRIC = 0, 1, 2
 OK, NOT_CONVERGED, BREAKDOWN = 0, 1, -3
 

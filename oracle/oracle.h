@@ -7,13 +7,14 @@
 #define ORACLE_H
 #include <stdint.h>
 
-enum { ORA_LAPLACIAN = 0, ORA_UPWIND = 1, ORA_DIFFUSION = 2 };
+enum { ORA_LAPLACIAN = 0, ORA_UPWIND = 1, ORA_DIFFUSION = 2, ORA_HPCG7 = 3, ORA_HPCG27 = 4 };
+enum { ORA_MAXNB = 26 };   /* off-diagonal entries per row, at most */
 enum { ORA_GS_FORWARD = 0, ORA_GS_BACKWARD = 1, ORA_GS_SYMMETRIC = 2 };
 enum { ORA_OK = 0, ORA_NOT_CONVERGED = 1, ORA_BREAKDOWN = -3 };
 
 typedef struct {
     int ndim;           /* 2 or 3 (1 allowed for tests)                 */
-    int kind;           /* ORA_LAPLACIAN / ORA_UPWIND / ORA_DIFFUSION   */
+    int kind;           /* ORA_LAPLACIAN / ORA_UPWIND / ORA_DIFFUSION / ORA_HPCG7 / ORA_HPCG27 */
     int64_t n[3];       /* interior nodes per dimension (unused = 1)    */
     double h[3];        /* mesh spacing 1/(n_d + 1)                     */
     double beta[3];     /* upwind velocity, beta_d >= 0                 */
@@ -21,7 +22,7 @@ typedef struct {
 } ora_op;
 
 int64_t ora_size(const ora_op *A);
-int ora_row(const ora_op *A, int64_t idx, double *diag, int64_t nb[6], double c[6]);
+int ora_row(const ora_op *A, int64_t idx, double *diag, int64_t nb[ORA_MAXNB], double c[ORA_MAXNB]);
 void ora_spmv(const ora_op *A, const double *x, double *y);
 int ora_dense(const ora_op *A, double *M, int64_t maxN);
 double ora_dot(int64_t N, const double *a, const double *b);

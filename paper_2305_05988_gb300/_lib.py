@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", -1: "ERR_INVALID", -2: "ERR_CUDA", 
                 -4: "ERR_NONFINITE", -5: "ERR_TIMEOUT", -6: "ERR_WORKSPACE"}
 
 HS_F64, HS_F32 = 0, 1
-HS_SOLVER_JACOBI, HS_SOLVER_GAUSS_SEIDEL, HS_SOLVER_CG, HS_SOLVER_BICGSTAB, HS_SOLVER_MIXED = 0, 1, 2, 3, 4
+HS_SOLVER_JACOBI, HS_SOLVER_GAUSS_SEIDEL, HS_SOLVER_CG, HS_SOLVER_BICGSTAB, HS_SOLVER_MIXED, HS_SOLVER_CG_NB = 0, 1, 2, 3, 4, 5
 HS_GS_FORWARD, HS_GS_BACKWARD, HS_GS_SYMMETRIC = 0, 1, 2
 HS_STATIC_SCRATCH_BYTES = 16 << 20   # include/hsolve.h
 
@@ -43,7 +43,8 @@ class hs_opts(ctypes.Structure):
                 ("use_graph", ctypes.c_int),
                 ("tile_rows", ctypes.c_int),
                 ("tile_planes", ctypes.c_int),
-                ("max_blocks", ctypes.c_int)]
+                ("max_blocks", ctypes.c_int),
+                ("paper_order", ctypes.c_int)]
 
 
 class hs_result(ctypes.Structure):
@@ -65,6 +66,7 @@ SIGNATURES = {
     "hs_grid_create": (_i, [_i, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_vp)]),
     "hs_grid_destroy": (None, [_vp]),
     "hs_op_laplacian": (_i, [_vp, ctypes.POINTER(_vp)]),
+    "hs_op_hpcg": (_i, [_vp, _i, ctypes.POINTER(_vp)]),
     "hs_op_convdiff_upwind": (_i, [_vp, ctypes.POINTER(_d), ctypes.POINTER(_vp)]),
     "hs_op_diffusion": (_i, [_vp, _i, _vp, ctypes.POINTER(_vp)]),
     "hs_op_destroy": (None, [_vp]),
@@ -77,6 +79,8 @@ SIGNATURES = {
     "hs_gauss_seidel": (_i, [_vp, _i, _vp, _vp, _d, _i, ctypes.POINTER(hs_opts), _vp, _sz, _vp,
                              ctypes.POINTER(hs_result), ctypes.POINTER(_d)]),
     "hs_cg": (_i, [_vp, _i, _vp, _vp, _d, _i, ctypes.POINTER(hs_opts), _vp, _sz, _vp,
+                   ctypes.POINTER(hs_result), ctypes.POINTER(_d)]),
+    "hs_cg_nb": (_i, [_vp, _i, _vp, _vp, _d, _i, ctypes.POINTER(hs_opts), _vp, _sz, _vp,
                    ctypes.POINTER(hs_result), ctypes.POINTER(_d)]),
     "hs_bicgstab": (_i, [_vp, _i, _vp, _vp, _d, _i, ctypes.POINTER(hs_opts), _vp, _sz, _vp,
                          ctypes.POINTER(hs_result), ctypes.POINTER(_d)]),

@@ -57,6 +57,7 @@ size_t ws_bytes_for(const hs_op* A, hs_solver s, hs_dtype dt, int maxit) {
     case HS_SOLVER_BICGSTAB: nvec = 8; break;
     case HS_SOLVER_GAUSS_SEIDEL: return common_bytes(maxit) + gs_ws_vectors(A, dt) + vark_coef_bytes(A, dt);
     case HS_SOLVER_MIXED: return 0;  // sized by mixed_ws_bytes with the options
+    case HS_SOLVER_CG_NB: nvec = 7; break;  // r, w, q ping-pong pairs and p
   }
   return common_bytes(maxit) + nvec * vec + vark_coef_bytes(A, dt);
 }
@@ -108,6 +109,7 @@ bool merge_opts(const hs_opts* in, hs_opts* out) {
   if (out->inner_maxit < 1 || out->inner_maxit > 100000000) out->inner_maxit = 10000;
   if (out->tile_planes < 0) out->tile_planes = 0;
   if (out->max_blocks < 0) out->max_blocks = 0;
+  out->paper_order = out->paper_order ? 1 : 0;
   return true;
 }
 
@@ -227,6 +229,12 @@ static hs_status make_op(const hs_grid* g, int kind, const double* beta, const v
 
 hs_status hs_op_laplacian(const hs_grid* g, hs_op** out) { return make_op(g, KIND_LAPLACIAN, nullptr, nullptr, 0, out); }
 
+hs_status hs_op_hpcg(const hs_grid* g, int points, hs_op** out) {
+  if (points != 7 && points != 27) { set_error("points must be 7 or 27"); return HS_ERR_INVALID; }
+  if (points == 27 && g && g->ndim != 3) { set_error("the 27-point system needs a 3-D grid"); return HS_ERR_INVALID; }
+  return make_op(g, points == 7 ? KIND_HPCG7 : KIND_HPCG27, nullptr, nullptr, 0, out);
+}
+
 hs_status hs_op_convdiff_upwind(const hs_grid* g, const double beta[3], hs_op** out) {
   if (!beta) { set_error("beta is NULL"); return HS_ERR_INVALID; }
   if (g)
@@ -269,7 +277,7 @@ hs_status hs_workspace_size(const hs_op* A, hs_solver solver, hs_dtype dtype, co
                             size_t* bytes) {
   if (!A || !bytes) { set_error("NULL argument"); return HS_ERR_INVALID; }
   if (dtype != HS_F64 && dtype != HS_F32) { set_error("bad dtype"); return HS_ERR_INVALID; }
-  if (solver < HS_SOLVER_JACOBI || solver > HS_SOLVER_MIXED) { set_error("bad solver"); return HS_ERR_INVALID; }
+  if (solver < HS_SOLVER_JACOBI || solver > HS_SOLVER_CG_NB) { set_error("bad solver"); return HS_ERR_INVALID; }
   if (solver == HS_SOLVER_MIXED && dtype != HS_F64) { set_error("mixed precision takes FP64 b and x"); return HS_ERR_INVALID; }
   if (maxit < 0) { set_error("maxit must be >= 0"); return HS_ERR_INVALID; }
   hs_opts o;
@@ -305,6 +313,17 @@ hs_status hs_cg(const hs_op* A, hs_dtype dtype, const void* b, void* x, double t
     return HS_ERR_INVALID;
   }
   return solve_common(run_cg, HS_SOLVER_CG, A, dtype, b, x, tol, maxit, opts, ws, ws_bytes, stream, res, hist);
+}
+
+hs_status hs_cg_nb(const hs_op* A, hs_dtype dtype, const void* b, void* x, double tol, int maxit,
+                   const hs_opts* opts, void* ws, size_t ws_bytes, void* stream, hs_result* res, double* hist) {
+  if (A && opkind_of(A) == OP_NONSYM) {
+    set_error("CG-NB needs a symmetric operator (Laplacian or diffusion)");
+    if (res) { fill_res(res); }
+    return HS_ERR_INVALID;
+  }
+  return solve_common(run_cg_nb, HS_SOLVER_CG_NB, A, dtype, b, x, tol, maxit, opts, ws, ws_bytes, stream, res,
+                      hist);
 }
 
 hs_status hs_bicgstab(const hs_op* A, hs_dtype dtype, const void* b, void* x, double tol, int maxit,

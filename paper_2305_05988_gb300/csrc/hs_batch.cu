@@ -480,6 +480,11 @@ extern "C" hs_status hs_batch_create(int nsys, const hs_op* const* ops, const in
       delete B;
       return HS_ERR_INVALID;
     }
+    if (opkind_of(ops[s]) == OP_BOX27) {
+      set_error("system %d: the batched solver takes 7-point operators", s);
+      delete B;
+      return HS_ERR_INVALID;
+    }
     if ((solvers[s] == HS_SOLVER_MIXED) != B->mixed) {
       set_error("system %d: a batch is either all mixed precision or all FP64", s);
       delete B;

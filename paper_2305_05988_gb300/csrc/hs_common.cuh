@@ -8,7 +8,9 @@
 namespace hs {
 
 // Operator kinds as compiled into kernels.
-enum OpKind : int { OP_SYM = 0, OP_NONSYM = 1, OP_VARK = 2 };
+// OP_BOX27: the HPCG 27-point system (diagonal 27, -1 on the 26 neighbours of
+// the 3x3x3 box), applied through separable box sums (3-D only).
+enum OpKind : int { OP_SYM = 0, OP_NONSYM = 1, OP_VARK = 2, OP_BOX27 = 3 };
 
 // Device status word values (mirrors hs_status where they overlap).
 enum DevStatus : int {

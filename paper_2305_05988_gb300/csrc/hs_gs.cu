@@ -33,14 +33,25 @@ namespace hs {
 
 template <int NDIM>
 struct GsTile;
+// Tile shapes (one thread per x-line: TY * TZ threads per block).  The 3-D
+// default 32 x 16 x 8 can be overridden at build time for measurements
+// (-DHS_GS_TY=.. -DHS_GS_TZ=..).
+#ifndef HS_GS_TY
+#define HS_GS_TY 16
+#endif
+#ifndef HS_GS_TZ
+#define HS_GS_TZ 8
+#endif
 template <>
 struct GsTile<3> {
-  static constexpr int TX = 32, TY = 16, TZ = 8;
+  static constexpr int TX = 32, TY = HS_GS_TY, TZ = HS_GS_TZ;
 };
 template <>
 struct GsTile<2> {
   static constexpr int TX = 32, TY = 128, TZ = 1;
 };
+template <int NDIM>
+constexpr int gs_threads() { return GsTile<NDIM>::TY * GsTile<NDIM>::TZ; }
 
 template <typename T>
 struct GsArgs {
@@ -117,6 +128,49 @@ __device__ bool gs_residual(const GsArgs<T>& a, T* sm, double* sh, double bb, do
   return true;
 }
 
+// Jacobi-form update x_i = D_i (b_i + sum_j a_ij x_j) split in two: gs_old
+// gathers the couplings to the neighbours not yet updated in this sweep (upper
+// neighbours of a forward sweep, lower ones of a backward sweep) into the
+// pre-scaled right-hand side, gs_new adds the already-updated neighbours (x
+// one first: it is ready earliest) and applies D_i (variable coefficients;
+// constant couplings come pre-divided by a_ii).
+template <typename T, int OPK, int NDIM>
+__device__ __forceinline__ T gs_old(const Coef<T>& cf, const OpRaw<T, OPK>& o, T bv, T vx, T vy, T vz, bool bw) {
+  T cx, cy, cz;
+  if constexpr (OPK == OP_VARK) {
+    cx = bw ? o.xl : o.xu;
+    cy = bw ? o.yl : o.yu;
+    cz = bw ? o.zl : o.zu;
+  } else {
+    cx = bw ? cf.xl : cf.xu;
+    cy = bw ? cf.yl : cf.yu;
+    cz = bw ? cf.zl : cf.zu;
+  }
+  T y = fma(cx, vx, bv);
+  y = fma(cy, vy, y);
+  if (NDIM == 3) y = fma(cz, vz, y);
+  return y;
+}
+
+template <typename T, int OPK, int NDIM>
+__device__ __forceinline__ T gs_new(const Coef<T>& cf, const OpRaw<T, OPK>& o, T yold, T vx, T vy, T vz, bool bw) {
+  T cx, cy, cz;
+  if constexpr (OPK == OP_VARK) {
+    cx = bw ? o.xu : o.xl;
+    cy = bw ? o.yu : o.yl;
+    cz = bw ? o.zu : o.zl;
+  } else {
+    cx = bw ? cf.xu : cf.xl;
+    cy = bw ? cf.yu : cf.yl;
+    cz = bw ? cf.zu : cf.zl;
+  }
+  T y = fma(cx, vx, yold);
+  y = fma(cy, vy, y);
+  if (NDIM == 3) y = fma(cz, vz, y);
+  if constexpr (OPK == OP_VARK) y = y * o.d;
+  return y;
+}
+
 // One tile of one sweep: load tile + halo, wavefront in shared memory, store.
 template <typename T, int OPK, int NDIM>
 __device__ __forceinline__ void gs_tile(const GsArgs<T>& a, T* sm, int tile, bool backward) {
@@ -135,11 +189,12 @@ __device__ __forceinline__ void gs_tile(const GsArgs<T>& a, T* sm, int tile, boo
   // memory round trips instead of one per element
   constexpr int TOT = SX * SY * SZ;
   constexpr int LU = 16;
-  for (int base = threadIdx.x; base < TOT; base += LU * 128) {
+  constexpr int NT = TY * TZ;
+  for (int base = threadIdx.x; base < TOT; base += LU * NT) {
     T v[LU];
 #pragma unroll
     for (int u = 0; u < LU; u++) {
-      const int e = base + u * 128;
+      const int e = base + u * NT;
       v[u] = T(0);
       if (e < TOT) {
         const int ii = e % SX, jj = (e / SX) % SY, kk = e / (SX * SY);
@@ -150,7 +205,7 @@ __device__ __forceinline__ void gs_tile(const GsArgs<T>& a, T* sm, int tile, boo
     }
 #pragma unroll
     for (int u = 0; u < LU; u++) {
-      const int e = base + u * 128;
+      const int e = base + u * NT;
       if (e < TOT) sm[e] = v[u];
     }
   }
@@ -168,17 +223,27 @@ __device__ __forceinline__ void gs_tile(const GsArgs<T>& a, T* sm, int tile, boo
   const int base = ((kl + ZOFF) * SY + (jl + 1)) * SX + 1;
   const long long gbase = (long long)gk * g.plane + (long long)gj * g.nx + i0;
   const int nsteps = TX + TY + TZ - 2;
-  // per-node operands of the next substep are loaded one substep ahead
+  // Offsets to the neighbours already updated in this sweep ("new" side:
+  // lower neighbours of a forward sweep) and to those not yet updated ("old"
+  // side).  The update of a node is split accordingly: the old-side terms
+  // are gathered one substep ahead, off the critical path; after the
+  // barrier only the new-side terms remain, the x one from a register.
+  const int nxo = backward ? 1 : -1;
+  const int nyo = backward ? SX : -SX;
+  const int nzo = backward ? SX * SY : -SX * SY;
   // local x index of this line at substep s, or -1 when the line is idle
 #define HS_IL_AT(S) ((((S) - d) < 0 || ((S) - d) >= TX) ? -1 : \
                      ((line_in && i0 + (backward ? TX - 1 - ((S) - d) : ((S) - d)) < g.nx) ? \
                       (backward ? TX - 1 - ((S) - d) : ((S) - d)) : -1))
   int il = HS_IL_AT(0);
-  T bcur = T(0);
+  T yold = T(0), wreg = T(0);
   OpRaw<T, OPK> ocur{};
   if (il >= 0) {
-    bcur = __ldcg(bsrc + gbase + il);
+    const int c = base + il;
+    const T bv = __ldcg(bsrc + gbase + il);
     ocur = op_fetch<T, OPK, NDIM>(a.cf, g, gbase + il, i0 + il, gj, gk);
+    yold = gs_old<T, OPK, NDIM>(a.cf, ocur, bv, sm[c - nxo], sm[c - nyo], NDIM == 3 ? sm[c - nzo] : T(0), backward);
+    wreg = sm[c + nxo];
   }
   for (int s = 0; s < nsteps; s++) {
     const int il_n = HS_IL_AT(s + 1);
@@ -190,24 +255,20 @@ __device__ __forceinline__ void gs_tile(const GsArgs<T>& a, T* sm, int tile, boo
     }
     if (il >= 0) {
       const int c = base + il;
-      Nbr<T> nb;
-      nb.c = sm[c];
-      nb.w = sm[c - 1];
-      nb.e = sm[c + 1];
-      nb.s = sm[c - SX];
-      nb.n = sm[c + SX];
-      if (NDIM == 3) {
-        nb.b = sm[c - SX * SY];
-        nb.t = sm[c + SX * SY];
-      } else {
-        nb.b = T(0);
-        nb.t = T(0);
-      }
-      sm[c] = jacobi_apply<T, OPK, NDIM>(a.cf, ocur, nb, bcur);
+      const T y = gs_new<T, OPK, NDIM>(a.cf, ocur, yold, wreg, sm[c + nyo], NDIM == 3 ? sm[c + nzo] : T(0), backward);
+      sm[c] = y;
+      wreg = y;
+    }
+    if (il_n >= 0) {
+      // the old-side cells of the next node are written at substep s + 2
+      // at the earliest, so they still hold the previous sweep's values
+      const int c = base + il_n;
+      if (il < 0) wreg = sm[c + nxo];   // first node of the line: x neighbour from the halo
+      yold = gs_old<T, OPK, NDIM>(a.cf, onext, bnext, sm[c - nxo], sm[c - nyo], NDIM == 3 ? sm[c - nzo] : T(0),
+                                  backward);
     }
     __syncthreads();
     il = il_n;
-    bcur = bnext;
     ocur = onext;
   }
 #undef HS_IL_AT
@@ -258,7 +319,7 @@ __device__ bool gs_batch(const GsArgs<T>& a, T* sm, double* sh, int nsw, bool ba
 }
 
 template <typename T, int OPK, int NDIM>
-__global__ void __launch_bounds__(128) k_gs(GsArgs<T> a) {
+__global__ void __launch_bounds__(gs_threads<NDIM>()) k_gs(GsArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double sh[32 * MAX_SCAL];
   T* sm = reinterpret_cast<T*>(smraw);
@@ -372,14 +433,11 @@ static Coef<T> gs_jacobi_coef(const hs_op* A, T* invd, double* d2) {
   return cf;
 }
 
-hs_status finish_solve_pub(const SolveArgs& sa, const Common& cm, const void* D, const void* ax, const void* ay,
-                           const void* az, void* rbuf, hs_result* res, double* hist, bool want_hist);
-
 template <typename T, int OPK, int NDIM>
 static hs_status gs_run_t(const SolveArgs& sa, hs_result* res, double* hist) {
   constexpr int TX = GsTile<NDIM>::TX, TY = GsTile<NDIM>::TY, TZ = GsTile<NDIM>::TZ;
   constexpr int THREADS = TY * TZ;
-  static_assert(THREADS == 128, "GS tiles use 128 lines");
+  static_assert(THREADS % 32 == 0 && THREADS <= 1024, "GS tiles use whole warps of lines");
   const hs_op* A = sa.A;
   Geom g = geom_of(A);
   Carve c{sa.ws, 0, sa.ws_bytes, true};

@@ -28,13 +28,16 @@ struct hs_op {
 
 namespace hs {
 
-enum { KIND_LAPLACIAN = 0, KIND_UPWIND = 1, KIND_DIFFUSION = 2 };
+// KIND_HPCG7 / KIND_HPCG27: the paper's benchmark system (section 4.1),
+// diagonal 27 and -1 for each face (7) or box (27) neighbour, unscaled.
+enum { KIND_LAPLACIAN = 0, KIND_UPWIND = 1, KIND_DIFFUSION = 2, KIND_HPCG7 = 3, KIND_HPCG27 = 4 };
 
 void set_error(const char* fmt, ...);
 hs_status cuda_fail(cudaError_t e, const char* what);
 
 inline int opkind_of(const hs_op* A) {
   if (A->kind == KIND_DIFFUSION) return OP_VARK;
+  if (A->kind == KIND_HPCG27) return OP_BOX27;
   if (A->kind == KIND_UPWIND) {
     for (int d = 0; d < A->ndim; d++)
       if (A->beta[d] != 0.0) return OP_NONSYM;
@@ -112,12 +115,19 @@ size_t ws_bytes_for(const hs_op* A, hs_solver s, hs_dtype dt, int maxit);
 hs_status run_jacobi(const SolveArgs& a, hs_result* res, double* hist);
 hs_status run_cg(const SolveArgs& a, hs_result* res, double* hist);
 hs_status run_bicgstab(const SolveArgs& a, hs_result* res, double* hist);
+hs_status run_cg_nb(const SolveArgs& a, hs_result* res, double* hist);
 hs_status run_gauss_seidel(const SolveArgs& a, hs_result* res, double* hist);
 hs_status run_spmv(const hs_op* A, hs_dtype dt, const void* x, void* y, cudaStream_t st);
 hs_status run_residual_plain(const hs_op* A, hs_dtype dt, const void* b, const void* x, void* r, cudaStream_t st);
 size_t vark_coef_bytes(const hs_op* A, hs_dtype dt);
 // Fills D (diagonal, or its inverse when invert_diag), ax, ay, az in dtype dt
 // from the operator's k.
+// Launch helpers shared by the solver translation units.
+hs_status launch_coop(const void* fn, int grid, int block, void** args, size_t smem, cudaStream_t st);
+hs_status init_ctrl(const Common& cm, const hs_opts& o, cudaStream_t st);
+hs_status finish_solve_pub(const SolveArgs& sa, const Common& cm, const void* D, const void* ax, const void* ay,
+                           const void* az, void* rbuf, hs_result* res, double* hist, bool want_hist);
+
 // Options with defaults filled in and validated (false: invalid, error set).
 bool merge_opts(const hs_opts* in, hs_opts* out);
 

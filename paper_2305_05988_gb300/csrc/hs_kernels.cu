@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(512) k_spmv(Geom g, Tiling tl, Coef<T> cf, T s
   T* sm = reinterpret_cast<T*>(smraw);
   LoadSrc<T, false> src{x};
   SpmvSink<T, OPK, NDIM> sink{cf, g, sigma, y};
-  for (int item = blockIdx.x; item < tl.items(); item += gridDim.x) zmarch_item<T, NDIM, CX_ST>(g, tl, item, sm, src, sink);
+  for (int item = blockIdx.x; item < tl.items(); item += gridDim.x) zmarch_item<T, NDIM, cx_st<OPK>()>(g, tl, item, sm, src, sink);
 }
 
 template <typename T, int OPK, int NDIM>
@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(512) k_residual(Geom g, Tiling tl, Coef<T> cf,
   T* sm = reinterpret_cast<T*>(smraw);
   LoadSrc<T, false> src{x};
   ResidualSink<T, OPK, NDIM> sink{cf, g, sigma, b, r, {0.0, 0.0}};
-  for (int item = blockIdx.x; item < tl.items(); item += gridDim.x) zmarch_item<T, NDIM, CX_ST>(g, tl, item, sm, src, sink);
+  for (int item = blockIdx.x; item < tl.items(); item += gridDim.x) zmarch_item<T, NDIM, cx_st<OPK>()>(g, tl, item, sm, src, sink);
   block_sum<2>(sink.acc, sh);
   if (partials && threadIdx.x == 0) {
     partials[2 * blockIdx.x] = sink.acc[0];
@@ -127,15 +127,17 @@ struct JacArgs {
   int fuse;        // 1: fuse the residual of each iterate into the next sweep
 };
 
-// x' = Jacobi update of x; optionally accumulates the residual of x,
-// r = a_ii (x' - x).
-template <typename T, int OPK, int NDIM>
+// x' = Jacobi update of x; with FUSE also accumulates the residual of x,
+// r = a_ii (x' - x).  FUSE is a template parameter: a run-time flag lets the
+// compiler predicate the residual arithmetic, which then still issues on the
+// FP64 pipe for every node.
+template <typename T, int OPK, int NDIM, bool FUSE>
 struct JacobiSink {
+  static constexpr bool kBox = OPK == OP_BOX27;
   Coef<T> cf;
   Geom g;
   const T* bsrc;   // b/a_ii (constant) or b (variable)
   T* xd;
-  int fuse;
   double acc[1];
   struct Raw {
     OpRaw<T, OPK> o;
@@ -147,7 +149,7 @@ struct JacobiSink {
   __device__ __forceinline__ void operator()(long long idx, const Nbr<T>& nb, const Raw& q, int, int, int) {
     T xn = jacobi_apply<T, OPK, NDIM>(cf, q.o, nb, q.b);
     xd[idx] = xn;
-    if (fuse) {
+    if constexpr (FUSE) {
       T d = xn - nb.c;
       if constexpr (OPK == OP_VARK) d = d / q.o.d;
       acc[0] += widen(d) * widen(d);
@@ -155,7 +157,7 @@ struct JacobiSink {
   }
 };
 
-template <typename T, int OPK, int NDIM>
+template <typename T, int OPK, int NDIM, bool FUSE>
 __global__ void __launch_bounds__(512) k_jacobi(JacArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double sh[32 * MAX_SCAL];
@@ -182,15 +184,15 @@ __global__ void __launch_bounds__(512) k_jacobi(JacArgs<T> a) {
   int iters = 0, status = DS_CONVERGED;
   double rel = -1.0;
   for (int k = 0;; k++) {
-    if (!a.fuse && k == a.maxit) {
+    if (!FUSE && k == a.maxit) {
       iters = k;
       break;
     }
     LoadSrc<T, true> src{xs};
-    JacobiSink<T, OPK, NDIM> sink{a.cf, a.g, bsrc, xd, a.fuse, {0.0}};
+    JacobiSink<T, OPK, NDIM, FUSE> sink{a.cf, a.g, bsrc, xd, {0.0}};
     for (int pos = blockIdx.x; pos < a.tl.items(); pos += gridDim.x)
       zmarch_item<T, NDIM, (cx_jac<T, OPK>())>(a.g, a.tl, pos, sm, src, sink);
-    if (a.fuse) {
+    if constexpr (FUSE) {
       block_sum<1>(sink.acc, sh);
       double rr[1];
       if (!grid_reduce<1>(a.cm.ctrl, a.cm.partials, sink.acc, rr, sh)) return;
@@ -220,16 +222,42 @@ __global__ void __launch_bounds__(512) k_jacobi(JacArgs<T> a) {
   finish(a.cm.ctrl, status, iters, rel);
 }
 
-template <typename T, int OPK, int NDIM>
-__global__ void __launch_bounds__(512) k_cg(CgArgs<T> a) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  __shared__ double sh[32 * MAX_SCAL];
-  const Team tm = grid_team(a.cm.ctrl, a.cm.partials);
-  team_finish(tm, cg_body<T, OPK, NDIM>(a, tm, reinterpret_cast<T*>(smraw), sh));
+// Register caps of the persistent solver kernels (0: compiler's choice) and
+// the CG x-deferral.  Defaults from A/B runs on GB300 at 256^3: FP64 CG on a
+// constant-coefficient operator 421 -> 410 us/iteration with the x update
+// deferred and 64 registers (either alone is slower: 441 / 433); FP64
+// BiCGStab 890 -> 859 us/iteration at 80 registers (3 blocks of 256 threads
+// per SM); the deferral slows FP64 variable-coefficient CG (1.43 -> 1.50 s),
+// which keeps the classical pass 2.  Override with -DHS_CG_MAXNREG=... etc.
+#ifndef HS_CG_MAXNREG
+#define HS_CG_MAXNREG 64
+#endif
+#ifndef HS_CG_XDEFER
+#define HS_CG_XDEFER 1
+#endif
+#ifndef HS_BI_MAXNREG
+#define HS_BI_MAXNREG 80
+#endif
+template <typename T, int OPK>
+constexpr int cg_maxnreg() {
+  return (HS_CG_MAXNREG > 0 && sizeof(T) == 8 && OPK != OP_VARK) ? HS_CG_MAXNREG : 255;
+}
+template <typename T, int OPK>
+constexpr int bi_maxnreg() {
+  return (HS_BI_MAXNREG > 0 && sizeof(T) == 8) ? HS_BI_MAXNREG : 255;
 }
 
 template <typename T, int OPK, int NDIM>
-__global__ void __launch_bounds__(512) k_bicgstab(BiArgs<T> a) {
+__global__ void __launch_bounds__(512) __maxnreg__((cg_maxnreg<T, OPK>())) k_cg(CgArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ double sh[32 * MAX_SCAL];
+  const Team tm = grid_team(a.cm.ctrl, a.cm.partials);
+  constexpr bool xdefer = HS_CG_XDEFER && sizeof(T) == 8 && OPK != OP_VARK;
+  team_finish(tm, cg_body<T, OPK, NDIM, cx_cg<T, OPK>(), xdefer>(a, tm, reinterpret_cast<T*>(smraw), sh));
+}
+
+template <typename T, int OPK, int NDIM>
+__global__ void __launch_bounds__(512) __maxnreg__((bi_maxnreg<T, OPK>())) k_bicgstab(BiArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double sh[32 * MAX_SCAL];
   const Team tm = grid_team(a.cm.ctrl, a.cm.partials);
@@ -307,6 +335,14 @@ Tiling choose_tiling(const Geom& g, int by, int grid, bool src_expensive, int pl
 
 ConstRow const_row(const hs_op* A) {
   ConstRow c = {0, 0, 0, 0, 0, 0, 0};
+  if (A->kind == KIND_HPCG7 || A->kind == KIND_HPCG27) {
+    // every coupling -1, diagonal 27 (the 27-point kernels read only d and
+    // the x coupling, see scaled_coef and jacobi_coef)
+    c.d = 27.0;
+    double* cs[6] = {&c.xl, &c.xu, &c.yl, &c.yu, &c.zl, &c.zu};
+    for (int q = 0; q < 2 * A->ndim; q++) *cs[q] = -1.0;
+    return c;
+  }
   double* lo[3] = {&c.xl, &c.yl, &c.zl};
   double* up[3] = {&c.xu, &c.yu, &c.zu};
   for (int d = 0; d < A->ndim; d++) {
@@ -393,6 +429,7 @@ static hs_status dispatch(hs_dtype dt, int opk, int ndim, F&& f) {
     HS_CASE(double, OP_NONSYM, 3)
     HS_CASE(double, OP_VARK, 2)
     HS_CASE(double, OP_VARK, 3)
+    HS_CASE(double, OP_BOX27, 3)
   } else {
     HS_CASE(float, OP_SYM, 2)
     HS_CASE(float, OP_SYM, 3)
@@ -400,6 +437,7 @@ static hs_status dispatch(hs_dtype dt, int opk, int ndim, F&& f) {
     HS_CASE(float, OP_NONSYM, 3)
     HS_CASE(float, OP_VARK, 2)
     HS_CASE(float, OP_VARK, 3)
+    HS_CASE(float, OP_BOX27, 3)
   }
 #undef HS_CASE
   set_error("unsupported operator / dtype combination");
@@ -484,8 +522,8 @@ hs_status run_spmv(const hs_op* A, hs_dtype dt, const void* x, void* y, cudaStre
     double sigma;
     Coef<T> cf = op_coef<T>(A, nullptr, nullptr, nullptr, nullptr, &sigma);
     int by = rows_per_tile(g);
-    Tiling tl = choose_tiling(g, by, 0, false, 0, CX_ST);
-    k_spmv<T, OPK, NDIM><<<tl.items(), 32 * by, slab_bytes<T>(by, CX_ST), st>>>(g, tl, cf, (T)sigma, (const T*)x, (T*)y);
+    Tiling tl = choose_tiling(g, by, 0, false, 0, cx_st<OPK>());
+    k_spmv<T, OPK, NDIM><<<tl.items(), 32 * by, slab_bytes<T>(by, cx_st<OPK>()), st>>>(g, tl, cf, (T)sigma, (const T*)x, (T*)y);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? HS_OK : cuda_fail(e, "spmv launch");
   });
@@ -513,8 +551,8 @@ hs_status run_residual_plain(const hs_op* A, hs_dtype dt, const void* b, const v
     double sigma;
     Coef<T> cf = op_coef<T>(A, nullptr, nullptr, nullptr, nullptr, &sigma);
     int by = rows_per_tile(g);
-    Tiling tl = choose_tiling(g, by, 0, false, 0, CX_ST);
-    k_residual<T, OPK, NDIM><<<tl.items(), 32 * by, slab_bytes<T>(by, CX_ST), st>>>(g, tl, cf, (T)sigma, (const T*)b,
+    Tiling tl = choose_tiling(g, by, 0, false, 0, cx_st<OPK>());
+    k_residual<T, OPK, NDIM><<<tl.items(), 32 * by, slab_bytes<T>(by, cx_st<OPK>()), st>>>(g, tl, cf, (T)sigma, (const T*)b,
                                                                                (const T*)x, (T*)r, nullptr);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? HS_OK : cuda_fail(e, "residual launch");
@@ -546,33 +584,13 @@ static hs_status residual_norms(const hs_op* A, hs_dtype dt, const void* D, cons
   });
 }
 
-// ---- persistent launch planning ------------------------------------------------
-template <typename K>
-static hs_status plan_persistent(K kernel, int block, size_t smem, const Geom& g, int by, bool src_expensive,
-                                 int* grid_out, Tiling* tl_out, const hs_opts& o, int cx) {
-  int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem);
-  if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
-  if (per_sm < 1) {
-    set_error("persistent kernel cannot be resident (block %d, smem %zu)", block, smem);
-    return HS_ERR_CUDA;
-  }
-  int grid = std::min(per_sm * sm_count(), MAX_BLOCKS);
-  if (o.max_blocks > 0) grid = std::min(grid, o.max_blocks);
-  Tiling tl = choose_tiling(g, by, grid, src_expensive, o.tile_planes, cx);
-  grid = std::max(1, std::min(grid, tl.items()));
-  *tl_out = choose_tiling(g, by, grid, src_expensive, o.tile_planes, cx);
-  *grid_out = grid;
-  return HS_OK;
-}
-
-static hs_status launch_coop(const void* fn, int grid, int block, void** args, size_t smem, cudaStream_t st) {
+hs_status launch_coop(const void* fn, int grid, int block, void** args, size_t smem, cudaStream_t st) {
   cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, smem, st);
   if (e != cudaSuccess) return cuda_fail(e, "cooperative launch");
   return HS_OK;
 }
 
-static hs_status init_ctrl(const Common& cm, const hs_opts& o, cudaStream_t st) {
+hs_status init_ctrl(const Common& cm, const hs_opts& o, cudaStream_t st) {
   double t = o.timeout_s > 0 ? o.timeout_s : 2.0;
   k_init_ctrl<<<1, 32, 0, st>>>(cm.ctrl, (unsigned long long)(t * 1e9));
   cudaError_t e = cudaGetLastError();
@@ -689,10 +707,12 @@ hs_status run_jacobi(const SolveArgs& sa, hs_result* res, double* hist) {
     constexpr int cx = cx_jac<T, OPK>();
     size_t smem = slab_bytes<T>(by, cx);
     int grid;
-    s = plan_persistent(k_jacobi<T, OPK, NDIM>, 32 * by, smem, g, by, false, &grid, &a.tl, sa.o, cx);
+    const void* kern = a.fuse ? (const void*)k_jacobi<T, OPK, NDIM, true> : (const void*)k_jacobi<T, OPK, NDIM, false>;
+    s = a.fuse ? plan_persistent(k_jacobi<T, OPK, NDIM, true>, 32 * by, smem, g, by, false, &grid, &a.tl, sa.o, cx)
+               : plan_persistent(k_jacobi<T, OPK, NDIM, false>, 32 * by, smem, g, by, false, &grid, &a.tl, sa.o, cx);
     if (s != HS_OK) return s;
     void* args[] = {&a};
-    s = launch_coop((const void*)k_jacobi<T, OPK, NDIM>, grid, 32 * by, args, smem, sa.stream);
+    s = launch_coop(kern, grid, 32 * by, args, smem, sa.stream);
     if (s != HS_OK) return s;
     if (OPK == OP_VARK && sa.o.true_residual) {
       s = setup_vark(A, sa.dtype, D, ax, ay, az, false, sa.stream);  // un-inverted diagonal
@@ -750,6 +770,7 @@ static hs_status bicgstab_core(const hs_op* A, const Coef<T>& cf, double sigma, 
   a.s = v[6];
   a.t = v[7];
   a.cm = cm;
+  a.paper_order = o.paper_order;
   a.maxit = maxit;
   a.tol = tol;
   a.reps = o.restart_eps;

@@ -14,7 +14,9 @@ namespace hs {
 // the FP64-pipe-bound solver passes nor helps the HBM-bound FP32 ones (whose
 // occupancy drops with the extra registers), so the solvers use one; the
 // single-pass SpMV / residual kernels use two.
-constexpr int CX_ST = 2;    // SpMV / residual
+constexpr int CX_ST = 2;    // SpMV / residual (7-point operators)
+template <int OPK>
+__host__ __device__ constexpr int cx_st() { return OPK == OP_BOX27 ? 1 : CX_ST; }
 constexpr int CX_BI = 1;    // BiCGStab
 template <typename T, int OPK>
 __host__ __device__ constexpr int cx_jac() { return 1; }
@@ -74,6 +76,7 @@ __device__ __forceinline__ void team_finish(const Team& tm, const BodyOut& o) {
 // y = A x (scaled operator times sigma).
 template <typename T, int OPK, int NDIM>
 struct SpmvSink {
+  static constexpr bool kBox = OPK == OP_BOX27;
   Coef<T> cf;
   Geom g;
   T sigma;
@@ -92,6 +95,7 @@ struct SpmvSink {
 // r = b - A x, accumulating ||r||^2 and ||b||^2.
 template <typename T, int OPK, int NDIM>
 struct ResidualSink {
+  static constexpr bool kBox = OPK == OP_BOX27;
   Coef<T> cf;
   Geom g;
   T sigma;
@@ -169,12 +173,19 @@ struct PUpdateSrc {
   }
 };
 
-// w = A p / sigma, accumulating p.w.
-template <typename T, int OPK, int NDIM>
+// w = A p / sigma, accumulating p.w.  With XUPD the node's x also takes the
+// previous iteration's step, x += alpha_prev p_prev: the x update rides on
+// this FP64-pipe-bound pass instead of lengthening the memory-bound
+// elementwise pass.
+template <typename T, int OPK, int NDIM, bool XUPD>
 struct ApDotSink {
+  static constexpr bool kBox = OPK == OP_BOX27;
   Coef<T> cf;
   Geom g;
   T* w;
+  T* x;
+  const T* pold;
+  T ax;
   double acc[1];
   using Raw = OpRaw<T, OPK>;
   __device__ __forceinline__ Raw fetch(long long idx, int i, int j, int k) const {
@@ -184,12 +195,19 @@ struct ApDotSink {
     T wv = op_apply<T, OPK, NDIM>(cf, o, nb);
     w[idx] = wv;
     acc[0] += widen(nb.c) * widen(wv);
+    // p_old was read two planes earlier by the source: an L2 hit; not
+    // prefetched, which would raise the register count of every pass
+    if constexpr (XUPD) x[idx] = fma(ax, __ldcg(pold + idx), __ldcg(x + idx));
   }
 };
 
 // The CG iteration run by one team of blocks (the whole grid for a standalone
 // solve, a subset of blocks in the batched solver).
-template <typename T, int OPK, int NDIM, int CX = cx_cg<T, OPK>()>
+// XDEFER: the x update of iteration k runs in pass 1 of iteration k+1
+// (ApDotSink<XUPD>), leaving pass 2 with r alone.  It pays where pass 1 is
+// FP64-pipe bound (standalone FP64); FP32 passes are memory bound and the
+// batched kernel is register bound, so they keep x in pass 2.
+template <typename T, int OPK, int NDIM, int CX = cx_cg<T, OPK>(), bool XDEFER = false>
 __device__ BodyOut cg_body(const CgArgs<T>& a, const Team& tm, T* sm, double* sh) {
   const long long N = a.g.N;
   const T sig = (T)a.sigma;
@@ -217,7 +235,7 @@ __device__ BodyOut cg_body(const CgArgs<T>& a, const Team& tm, T* sm, double* sh
     return BodyOut{rel <= a.tol ? DS_CONVERGED : DS_MAXIT, 0, rel, 0, true};
   }
 
-  double beta = 0.0;
+  double beta = 0.0, alpha_prev = 0.0;
   bool first = true;
   int it = 0, status = DS_MAXIT;
   const long long st = tm.stride();
@@ -225,54 +243,87 @@ __device__ BodyOut cg_body(const CgArgs<T>& a, const Team& tm, T* sm, double* sh
     it++;
     const T* pold = (it & 1) ? a.p0 : a.p1;
     T* pnew = (it & 1) ? a.p1 : a.p0;
-    // ---- pass 1: p = r + beta p_old ; w = A p / sigma ; p.w
+    // ---- pass 1: p = r + beta p_old ; w = A p / sigma ; p.w ; x += alpha_prev p_old
     PUpdateSrc<T> src{a.r, pold, pnew, (T)beta, first};
-    ApDotSink<T, OPK, NDIM> sink{a.cf, a.g, a.w, {0.0}};
-    for (int item = tm.rank; item < a.tl.items(); item += tm.size)
-      zmarch_item<T, NDIM, CX>(a.g, a.tl, item, sm, src, sink);
-    block_sum<1>(sink.acc, sh);
-    double pw[1];
-    if (!team_reduce<1>(tm, sink.acc, pw, sh)) return BodyOut{DS_TIMEOUT, it, rel, 0, false};
+    double pw[1], acc0[1];
+    {
+      // first iteration: no step pending; x += 0 * r (r is finite, p_old
+      // undefined) leaves x unchanged
+      ApDotSink<T, OPK, NDIM, XDEFER> sink{a.cf, a.g, a.w, a.x, first ? a.r : pold,
+                                           first ? T(0) : (T)(alpha_prev / a.sigma), {0.0}};
+      for (int item = tm.rank; item < a.tl.items(); item += tm.size)
+        zmarch_item<T, NDIM, CX>(a.g, a.tl, item, sm, src, sink);
+      acc0[0] = sink.acc[0];
+    }
+    block_sum<1>(acc0, sh);
+    if (!team_reduce<1>(tm, acc0, pw, sh)) return BodyOut{DS_TIMEOUT, it, rel, 0, false};
     if (!(pw[0] > 0.0) || !finite_d(pw[0])) {
       status = finite_d(pw[0]) ? DS_BREAKDOWN : DS_NONFINITE;
-      break;
+      return BodyOut{status, it, rel, 0, true};   // x holds x_{it-1} in both forms
     }
     const double ar = rr / pw[0];           // multiplies w = A p / sigma
-    const double axs = ar / a.sigma;        // multiplies p
-    const T tar = (T)ar, tax = (T)axs;
-    // ---- pass 2: x += alpha p ; r -= alpha A p ; r.r
+    const T tar = (T)ar;
     double acc1[1] = {0.0};
-    long long i = tm.tid();
-    for (; i + (ILP - 1) * st < N; i += ILP * st) {
-      T pv[ILP], wv[ILP], xv[ILP], rv[ILP];
+    if constexpr (XDEFER) {
+      // ---- pass 2: r -= alpha A p ; r.r   (x follows in the next pass 1)
+      long long i = tm.tid();
+      for (; i + (ILP - 1) * st < N; i += ILP * st) {
+        T wv[ILP], rv[ILP];
 #pragma unroll
-      for (int u = 0; u < ILP; u++) {
-        const long long q = i + u * st;
-        pv[u] = ldcg(pnew + q);
-        wv[u] = ldcg(a.w + q);
-        xv[u] = ldcg(a.x + q);
-        rv[u] = ldcg(a.r + q);
-      }
+        for (int u = 0; u < ILP; u++) {
+          const long long q = i + u * st;
+          wv[u] = ldcg(a.w + q);
+          rv[u] = ldcg(a.r + q);
+        }
 #pragma unroll
-      for (int u = 0; u < ILP; u++) {
-        const long long q = i + u * st;
-        xv[u] = fma(tax, pv[u], xv[u]);
-        rv[u] = fma(-tar, wv[u], rv[u]);
-        a.x[q] = xv[u];
-        a.r[q] = rv[u];
-        acc1[0] += widen(rv[u]) * widen(rv[u]);
+        for (int u = 0; u < ILP; u++) {
+          const long long q = i + u * st;
+          rv[u] = fma(-tar, wv[u], rv[u]);
+          a.r[q] = rv[u];
+          acc1[0] += widen(rv[u]) * widen(rv[u]);
+        }
       }
-    }
-    for (; i < N; i += st) {
-      T xv = fma(tax, ldcg(pnew + i), ldcg(a.x + i));
-      T rv = fma(-tar, ldcg(a.w + i), ldcg(a.r + i));
-      a.x[i] = xv;
-      a.r[i] = rv;
-      acc1[0] += widen(rv) * widen(rv);
+      for (; i < N; i += st) {
+        T rv = fma(-tar, ldcg(a.w + i), ldcg(a.r + i));
+        a.r[i] = rv;
+        acc1[0] += widen(rv) * widen(rv);
+      }
+    } else {
+      // ---- pass 2: x += alpha p ; r -= alpha A p ; r.r
+      const T tax = (T)(ar / a.sigma);      // multiplies p
+      long long i = tm.tid();
+      for (; i + (ILP - 1) * st < N; i += ILP * st) {
+        T pv[ILP], wv[ILP], xv[ILP], rv[ILP];
+#pragma unroll
+        for (int u = 0; u < ILP; u++) {
+          const long long q = i + u * st;
+          pv[u] = ldcg(pnew + q);
+          wv[u] = ldcg(a.w + q);
+          xv[u] = ldcg(a.x + q);
+          rv[u] = ldcg(a.r + q);
+        }
+#pragma unroll
+        for (int u = 0; u < ILP; u++) {
+          const long long q = i + u * st;
+          xv[u] = fma(tax, pv[u], xv[u]);
+          rv[u] = fma(-tar, wv[u], rv[u]);
+          a.x[q] = xv[u];
+          a.r[q] = rv[u];
+          acc1[0] += widen(rv[u]) * widen(rv[u]);
+        }
+      }
+      for (; i < N; i += st) {
+        T xv = fma(tax, ldcg(pnew + i), ldcg(a.x + i));
+        T rv = fma(-tar, ldcg(a.w + i), ldcg(a.r + i));
+        a.x[i] = xv;
+        a.r[i] = rv;
+        acc1[0] += widen(rv) * widen(rv);
+      }
     }
     block_sum<1>(acc1, sh);
     double rn[1];
     if (!team_reduce<1>(tm, acc1, rn, sh)) return BodyOut{DS_TIMEOUT, it, rel, 0, false};
+    alpha_prev = ar;
     rel = sqrt(rn[0] / bb);
     if (tm.lead() && a.cm.hist) a.cm.hist[it] = rel;
     if (!finite_d(rel)) {
@@ -286,6 +337,13 @@ __device__ BodyOut cg_body(const CgArgs<T>& a, const Team& tm, T* sm, double* sh
     beta = rn[0] / rr;
     rr = rn[0];
     first = false;
+  }
+  // the last step of x, x += alpha p (same element -> thread map as the
+  // callers' elementwise passes, so no barrier is needed before they read x)
+  if constexpr (XDEFER) {
+    const T* plast = (it & 1) ? a.p1 : a.p0;
+    const T tax = (T)(alpha_prev / a.sigma);
+    for (long long i = tm.tid(); i < N; i += st) a.x[i] = fma(tax, ldcg(plast + i), ldcg(a.x + i));
   }
   return BodyOut{status, it, rel, 0, true};
 }
@@ -322,24 +380,26 @@ struct BiArgs {
   int maxit;
   double tol;
   double reps;
+  int paper_order;   // Algorithm 2's statement order (BiCGStab-B1)
 };
 
-// p = r + beta (p_old - omega sigma v_old), or p = r on (re)start.
-template <typename T>
+// p = r + beta (p_old - omega sigma v_old), or p = r on (re)start.  The
+// restart case is a separate instantiation (RESTART): a run-time flag would
+// let the compiler predicate the other branch's FP64 work, which still issues.
+template <typename T, bool RESTART>
 struct BiPSrc {
   const T* r;
   const T* pold;
   const T* vold;
   T* pnew;
   T beta, ws;
-  bool restart;
   struct Raw {
     T r, p, v;
   };
   __device__ __forceinline__ Raw fetch(long long idx) const {
     Raw q;
     q.r = __ldcg(r + idx);
-    if (restart) {
+    if constexpr (RESTART) {
       q.p = T(0);
       q.v = T(0);
     } else {
@@ -349,35 +409,39 @@ struct BiPSrc {
     return q;
   }
   __device__ __forceinline__ T make(const Raw& q, long long idx, bool own) const {
-    T pv = restart ? q.r : fma(beta, fma(-ws, q.v, q.p), q.r);
+    T pv;
+    if constexpr (RESTART)
+      pv = q.r;
+    else
+      pv = fma(beta, fma(-ws, q.v, q.p), q.r);
     if (own) pnew[idx] = pv;
     return pv;
   }
 };
 
 // v = A p / sigma; r' = r/||r|| stored on (re)start; partial v.r'.
-template <typename T, int OPK, int NDIM>
+template <typename T, int OPK, int NDIM, bool RESTART>
 struct BiVSink {
+  static constexpr bool kBox = OPK == OP_BOX27;
   Coef<T> cf;
   Geom g;
   const T* r;
   T* rs;
   T* vnew;
   T inv_rn;
-  bool restart;
   double acc[1];
   struct Raw {
     OpRaw<T, OPK> o;
     T q;   // r (restart) or r'
   };
   __device__ __forceinline__ Raw fetch(long long idx, int i, int j, int k) const {
-    return Raw{op_fetch<T, OPK, NDIM>(cf, g, idx, i, j, k), restart ? __ldcg(r + idx) : __ldcg(rs + idx)};
+    return Raw{op_fetch<T, OPK, NDIM>(cf, g, idx, i, j, k), RESTART ? __ldcg(r + idx) : __ldcg(rs + idx)};
   }
   __device__ __forceinline__ void operator()(long long idx, const Nbr<T>& nb, const Raw& q, int, int, int) {
     T vv = op_apply<T, OPK, NDIM>(cf, q.o, nb);
     vnew[idx] = vv;
     T rsv = q.q;
-    if (restart) {
+    if constexpr (RESTART) {
       rsv = q.q * inv_rn;
       rs[idx] = rsv;
     }
@@ -406,6 +470,7 @@ struct BiSSrc {
 // t = A s / sigma; partials s.s, t.s, t.t.
 template <typename T, int OPK, int NDIM>
 struct BiTSink {
+  static constexpr bool kBox = OPK == OP_BOX27;
   Coef<T> cf;
   Geom g;
   T* t;
@@ -467,12 +532,22 @@ __device__ BodyOut bicgstab_body(const BiArgs<T>& a, const Team& tm, T* sm, doub
     // ---- pass 1
     double ad[1];
     {
-      BiPSrc<T> src{a.r, pold, vold, pnew, (T)beta, (T)(omega * a.sigma), restart};
-      BiVSink<T, OPK, NDIM> sink{a.cf, a.g, a.r, a.rs, vnew, (T)inv_rn, restart, {0.0}};
-      for (int item = tm.rank; item < a.tl.items(); item += tm.size)
-        zmarch_item<T, NDIM, CX>(a.g, a.tl, item, sm, src, sink);
-      block_sum<1>(sink.acc, sh);
-      if (!team_reduce<1>(tm, sink.acc, ad, sh)) return BodyOut{DS_TIMEOUT, it, rel, restarts, false};
+      double acc1[1];
+      if (restart) {
+        BiPSrc<T, true> src{a.r, pold, vold, pnew, (T)beta, (T)(omega * a.sigma)};
+        BiVSink<T, OPK, NDIM, true> sink{a.cf, a.g, a.r, a.rs, vnew, (T)inv_rn, {0.0}};
+        for (int item = tm.rank; item < a.tl.items(); item += tm.size)
+          zmarch_item<T, NDIM, CX>(a.g, a.tl, item, sm, src, sink);
+        acc1[0] = sink.acc[0];
+      } else {
+        BiPSrc<T, false> src{a.r, pold, vold, pnew, (T)beta, (T)(omega * a.sigma)};
+        BiVSink<T, OPK, NDIM, false> sink{a.cf, a.g, a.r, a.rs, vnew, (T)inv_rn, {0.0}};
+        for (int item = tm.rank; item < a.tl.items(); item += tm.size)
+          zmarch_item<T, NDIM, CX>(a.g, a.tl, item, sm, src, sink);
+        acc1[0] = sink.acc[0];
+      }
+      block_sum<1>(acc1, sh);
+      if (!team_reduce<1>(tm, acc1, ad, sh)) return BodyOut{DS_TIMEOUT, it, rel, restarts, false};
     }
     const double alpha_d = a.sigma * ad[0];
     if (alpha_d == 0.0 || !finite_d(alpha_d)) {
@@ -491,7 +566,7 @@ __device__ BodyOut bicgstab_body(const BiArgs<T>& a, const Team& tm, T* sm, doub
       if (!team_reduce<3>(tm, sink.acc, st3, sh)) return BodyOut{DS_TIMEOUT, it, rel, restarts, false};
     }
     const double srel = sqrt(st3[0] / bb);
-    if (srel <= a.tol) {
+    if (!a.paper_order && srel <= a.tol) {
       const T ta = (T)alpha;
       for (long long i = tm.tid(); i < N; i += st) a.x[i] = fma(ta, ldcg(pnew + i), ldcg(a.x + i));
       if (tm.lead() && a.cm.hist) a.cm.hist[it] = srel;
@@ -509,8 +584,17 @@ __device__ BodyOut bicgstab_body(const BiArgs<T>& a, const Team& tm, T* sm, doub
       status = DS_BREAKDOWN;
       break;
     }
-    // ---- pass 3
     const T ta = (T)alpha, tom = (T)omega, toms = (T)(omega * a.sigma);
+    if (a.paper_order && rel <= a.tol) {
+      // Algorithm 2's order: the test on the residual of x_j comes after
+      // omega_j, and the loop ends with x = x_j + alpha_j p_j + omega_j s_j
+      for (long long i = tm.tid(); i < N; i += st)
+        a.x[i] = fma(tom, ldcg(a.s + i), fma(ta, ldcg(pnew + i), ldcg(a.x + i)));
+      if (tm.lead() && a.cm.hist) a.cm.hist[it] = nan("");   // residual of the last step not formed
+      status = DS_CONVERGED;
+      break;
+    }
+    // ---- pass 3
     double acc4[2] = {0.0, 0.0};
     long long i = tm.tid();
     for (; i + (ILP - 1) * st < N; i += ILP * st) {
@@ -554,7 +638,7 @@ __device__ BodyOut bicgstab_body(const BiArgs<T>& a, const Team& tm, T* sm, doub
       status = DS_NONFINITE;
       break;
     }
-    if (rel <= a.tol) {
+    if (!a.paper_order && rel <= a.tol) {
       status = DS_CONVERGED;
       break;
     }
@@ -590,6 +674,8 @@ inline Coef<T> scaled_coef(const hs_op* A, double* sigma) {
   cf.yu = (T)(c.yu / s);
   cf.zl = (T)(c.zl / s);
   cf.zu = (T)(c.zu / s);
+  // 27-point: A x = 27 x - (box - x) = 28 x - box (s = 1)
+  if (A->kind == KIND_HPCG27) cf.d = (T)(c.d + 1.0);
   return cf;
 }
 
@@ -626,5 +712,26 @@ inline Coef<T> op_coef(const hs_op* A, const void* D, const void* ax, const void
   }
   return scaled_coef<T>(A, sigma);
 }
+
+// ---- persistent launch planning ------------------------------------------------
+template <typename K>
+inline hs_status plan_persistent(K kernel, int block, size_t smem, const Geom& g, int by, bool src_expensive,
+                                 int* grid_out, Tiling* tl_out, const hs_opts& o, int cx) {
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem);
+  if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+  if (per_sm < 1) {
+    set_error("persistent kernel cannot be resident (block %d, smem %zu)", block, smem);
+    return HS_ERR_CUDA;
+  }
+  int grid = std::min(per_sm * sm_count(), MAX_BLOCKS);
+  if (o.max_blocks > 0) grid = std::min(grid, o.max_blocks);
+  Tiling tl = choose_tiling(g, by, grid, src_expensive, o.tile_planes, cx);
+  grid = std::max(1, std::min(grid, tl.items()));
+  *tl_out = choose_tiling(g, by, grid, src_expensive, o.tile_planes, cx);
+  *grid_out = grid;
+  return HS_OK;
+}
+
 
 }  // namespace hs

@@ -15,6 +15,8 @@
 // columns), so FP64 work is never issued for a handful of lanes.
 // Nodes outside the grid read as zero (homogeneous Dirichlet ghosts).
 #pragma once
+#include <type_traits>
+
 #include "hs_common.cuh"
 
 namespace hs {
@@ -49,11 +51,20 @@ __device__ __forceinline__ T& slab(T* sm, int by, int buf, int row, int col) {
   return sm[(buf * (by + 2) + row) * (BX * CX + 2) + col];
 }
 
-// Neighbour values of the current node handed to the stencil functor.
+// Neighbour values of the current node handed to the stencil functor (box:
+// the sum over the node's 3x3x3 box, center included, for OP_BOX27 sinks).
 template <typename T>
 struct Nbr {
   T c, w, e, s, n, b, t;
+  T box;
 };
+
+// A sink that applies the 27-point operator declares kBox = true; the tile
+// engine then hands it box sums instead of the 7-point neighbourhood.
+template <class S, class = void>
+struct is_box_sink : std::false_type {};
+template <class S>
+struct is_box_sink<S, std::void_t<decltype(S::kBox)>> : std::integral_constant<bool, S::kBox> {};
 
 // Process one work item, software-pipelined along z.
 //
@@ -72,9 +83,18 @@ struct Nbr {
 // Halo nodes are produced by whole warps: warp 0 the row below the tile (CX
 // nodes per lane), warp 1 the row above, warp 2 the two side columns (lanes
 // 0..by-1 left, 16..16+by-1 right).  Requires 3 <= by <= 16 and tl.cx == CX.
+template <typename T, class Src, class Sink>
+__device__ __forceinline__ void zmarch_box(const Geom& g, const Tiling& tl, int item, T* sm, const Src& src,
+                                           Sink& sink);
+
 template <typename T, int NDIM, int CX, class Src, class Sink>
 __device__ __forceinline__ void zmarch_item(const Geom& g, const Tiling& tl, int item, T* sm, const Src& src,
                                             Sink& sink) {
+  if constexpr (is_box_sink<Sink>::value) {
+    static_assert(NDIM == 3 && CX == 1, "the 27-point engine is 3-D with one column per lane");
+    zmarch_box<T>(g, tl, item, sm, src, sink);
+    return;
+  }
   using SR = typename Src::Raw;
   using KR = typename Sink::Raw;
   constexpr int TW = BX * CX;
@@ -222,6 +242,124 @@ __device__ __forceinline__ void zmarch_item(const Geom& g, const Tiling& tl, int
   }
 }
 
+// The 27-point engine (OP_BOX27).  Same work items, source / sink functors
+// and prefetch scheme as zmarch_item, one column per lane; the sink receives
+// the node value c and its 3x3x3 box sum, formed separably so that a node
+// costs 6 additions instead of 26:
+//   Rx(i,j) = x(i-1,j) + x(i,j) + x(i+1,j)       rows j0-1 .. j0+by (shared)
+//   P(i,j)  = Rx(i,j-1) + Rx(i,j) + Rx(i,j+1)     per column and plane
+//   box_k   = P_k-1 + P_k + P_k+1                 per column, P kept in registers
+// Plane k+1 is staged (tile plus a one-node ring including the corners),
+// its row sums are formed, then its P, and the sink runs on plane k: two
+// barriers per plane.  Halo producers: warp 0 the row below the tile, warp 1
+// the row above, warp 2 the side columns, warp 3 lanes 0..3 the corners
+// (requires 4 <= by <= 16).  Shared memory: the plane, (by + 2) x 34 values,
+// then the row sums, (by + 2) x 32 values.
+template <typename T, class Src, class Sink>
+__device__ __forceinline__ void zmarch_box(const Geom& g, const Tiling& tl, int item, T* sm, const Src& src,
+                                           Sink& sink) {
+  using SR = typename Src::Raw;
+  using KR = typename Sink::Raw;
+  constexpr int SW = BX + 2;   // staged row width
+  int i0, j0, z0, z1;
+  decode_item(tl, g, item, i0, j0, z0, z1);
+  const int by = tl.by;
+  T* rx = sm + (by + 2) * SW;  // row sums, (by + 2) x BX
+  const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
+  const int i = i0 + lx, j = j0 + ly;
+  const bool inside = (i < g.nx) && (j < g.ny);
+  const long long P = g.plane;
+  const long long col = (long long)j * g.nx + i;
+  // the halo node of this thread (one at most)
+  int hrow = -1, hcp = 0, hi = 0, hj = 0;
+  if (ly == 0) {
+    hi = i0 + lx; hj = j0 - 1; hrow = 0; hcp = lx + 1;
+  } else if (ly == 1) {
+    hi = i0 + lx; hj = j0 + by; hrow = by + 1; hcp = lx + 1;
+  } else if (ly == 2) {
+    if (lx < by) {
+      hi = i0 - 1; hj = j0 + lx; hrow = lx + 1; hcp = 0;
+    } else if (lx >= 16 && lx < 16 + by) {
+      hi = i0 + BX; hj = j0 + lx - 16; hrow = lx - 15; hcp = BX + 1;
+    }
+  } else if (ly == 3 && lx < 4) {
+    hi = (lx & 1) ? i0 + BX : i0 - 1;
+    hj = (lx & 2) ? j0 + by : j0 - 1;
+    hrow = (lx & 2) ? by + 1 : 0;
+    hcp = (lx & 1) ? BX + 1 : 0;
+  }
+  const bool hin = hrow >= 0 && hi >= 0 && hi < g.nx && hj >= 0 && hj < g.ny;
+  const long long hcol = hin ? (long long)hj * g.nx + hi : 0;
+
+  // stage plane kk (values from raw loads issued earlier), form its row sums
+  // and return P of this thread's column; planes outside the grid give 0
+  auto plane_P = [&](int kk, const SR& rown, const SR& rhal, bool own, T& vown) -> T {
+    vown = T(0);
+    if (kk >= 0 && kk < g.nz) {
+      if (inside) vown = src.make(rown, col + (long long)kk * P, own);
+      sm[(ly + 1) * SW + lx + 1] = vown;
+      if (hrow >= 0) sm[hrow * SW + hcp] = hin ? src.make(rhal, hcol + (long long)kk * P, false) : T(0);
+    }
+    __syncthreads();
+    if (kk >= 0 && kk < g.nz) {
+      const T* r = sm + (ly + 1) * SW + lx;
+      rx[(ly + 1) * BX + lx] = (r[0] + r[1]) + r[2];
+      if (ly < 2) {
+        const int hr = ly == 0 ? 0 : by + 1;
+        const T* q = sm + hr * SW + lx;
+        rx[hr * BX + lx] = (q[0] + q[1]) + q[2];
+      }
+    }
+    __syncthreads();
+    if (kk < 0 || kk >= g.nz) return T(0);
+    return (rx[ly * BX + lx] + rx[(ly + 1) * BX + lx]) + rx[(ly + 2) * BX + lx];
+  };
+  auto fetch_plane = [&](int kk, SR& rown, SR& rhal) {
+    rown = SR{};
+    rhal = SR{};
+    if (kk >= 0 && kk < g.nz) {
+      if (inside) rown = src.fetch(col + (long long)kk * P);
+      if (hin) rhal = src.fetch(hcol + (long long)kk * P);
+    }
+  };
+
+  // prologue: P of planes z0 - 1 and z0, the center value at z0
+  SR ra, ha, rb, hb;
+  fetch_plane(z0 - 1, ra, ha);
+  fetch_plane(z0, rb, hb);
+  T vdummy, vc;
+  T Pm = plane_P(z0 - 1, ra, ha, false, vdummy);
+  SR rn, hn;
+  fetch_plane(z0 + 1, rn, hn);          // plane z0 + 1, staged in the first step
+  KR kown = KR{};
+  if (inside) kown = sink.fetch(col + (long long)z0 * P, i, j, z0);
+  T Pc = plane_P(z0, rb, hb, true, vc);
+
+  for (int k = z0; k < z1; k++) {
+    // loads of the next step: src plane k + 2, sink operands of plane k + 1
+    SR rn2, hn2;
+    fetch_plane(k + 2 < z1 + 1 ? k + 2 : g.nz, rn2, hn2);
+    KR kown2 = KR{};
+    if (inside && k + 1 < z1) kown2 = sink.fetch(col + (long long)(k + 1) * P, i, j, k + 1);
+    T vt;
+    const T Pn = plane_P(k + 1, rn, hn, k + 1 < z1, vt);
+    if (inside) {
+      Nbr<T> nb;
+      nb.c = vc;
+      nb.box = (Pm + Pc) + Pn;
+      nb.w = nb.e = nb.s = nb.n = nb.b = nb.t = T(0);
+      sink(col + (long long)k * P, nb, kown, i, j, k);
+    }
+    Pm = Pc;
+    Pc = Pn;
+    vc = vt;
+    rn = rn2;
+    hn = hn2;
+    kown = kown2;
+  }
+  __syncthreads();   // the next item restages the shared plane
+}
+
 // Plain load of one vector as the stencil input.  CG = true reads through
 // L2 only (data written earlier in the same persistent kernel).
 template <typename T, bool CG>
@@ -272,7 +410,10 @@ __device__ __forceinline__ OpRaw<T, OPK> op_fetch(const Coef<T>& cf, const Geom&
 // 3-D, 4 in 2-D).  Variable coefficients (sigma = 1): 7 instructions.
 template <typename T, int OPK, int NDIM>
 __device__ __forceinline__ T op_apply(const Coef<T>& cf, const OpRaw<T, OPK>& o, const Nbr<T>& nb) {
-  if constexpr (OPK == OP_SYM) {
+  if constexpr (OPK == OP_BOX27) {
+    // 27 c - (box - c), with cf.d = 28: 1 instruction after the box sums
+    return fma(cf.d, nb.c, -nb.box);
+  } else if constexpr (OPK == OP_SYM) {
     T y = fma(cf.d, nb.c, -(nb.w + nb.e));
     y = fma(cf.yl, nb.s + nb.n, y);
     if (NDIM == 3) y = fma(cf.zl, nb.b + nb.t, y);
@@ -307,7 +448,10 @@ __device__ __forceinline__ T op_apply(const Coef<T>& cf, const OpRaw<T, OPK>& o,
 // with o.d = 1/a_ii (7 instructions).
 template <typename T, int OPK, int NDIM>
 __device__ __forceinline__ T jacobi_apply(const Coef<T>& cf, const OpRaw<T, OPK>& o, const Nbr<T>& nb, T bv) {
-  if constexpr (OPK == OP_SYM) {
+  if constexpr (OPK == OP_BOX27) {
+    // b/a_ii + (box - c)/27: the 26 neighbours all couple with -1
+    return fma(cf.xl, nb.box - nb.c, bv);
+  } else if constexpr (OPK == OP_SYM) {
     T y = fma(cf.xl, nb.w + nb.e, bv);
     y = fma(cf.yl, nb.s + nb.n, y);
     if (NDIM == 3) y = fma(cf.zl, nb.b + nb.t, y);

@@ -42,9 +42,10 @@ class SolveInfo:
 
 
 class Operator:
-    """A matrix-free structured-grid operator (Laplacian, upwind convection-diffusion
-    or variable-coefficient diffusion) on n_x [* n_y [* n_z]] interior nodes with
-    homogeneous Dirichlet boundaries and spacing h_d = 1/(n_d + 1)."""
+    """A matrix-free structured-grid operator (Laplacian, upwind convection-diffusion,
+    variable-coefficient diffusion, or the HPCG 7/27-point benchmark matrix) on
+    n_x [* n_y [* n_z]] interior nodes with homogeneous Dirichlet boundaries and
+    spacing h_d = 1/(n_d + 1) (the HPCG matrices are unscaled)."""
 
     def __init__(self, shape: Sequence[int], kind: str = "laplacian", beta=None, k: Optional[torch.Tensor] = None):
         lib = _lib.load()
@@ -72,6 +73,8 @@ class Operator:
                 self._k = k.contiguous()
                 check(lib.hs_op_diffusion(self._grid, _DT[self._k.dtype], ctypes.c_void_p(self._k.data_ptr()),
                                           ctypes.byref(self._op)), "hs_op_diffusion")
+            elif kind in ("hpcg7", "hpcg27"):
+                check(lib.hs_op_hpcg(self._grid, 7 if kind == "hpcg7" else 27, ctypes.byref(self._op)), "hs_op_hpcg")
             else:
                 raise ValueError("unknown operator kind %r" % kind)
         finally:
@@ -91,6 +94,14 @@ class Operator:
     @classmethod
     def diffusion(cls, shape, k: torch.Tensor):
         return cls(shape, "diffusion", k=k)
+
+    @classmethod
+    def hpcg(cls, shape, points: int = 27):
+        """The paper's benchmark system (section 4.1): diagonal 27, -1 for each
+        of the 6 face (points=7) or 26 box (points=27) neighbours, unscaled."""
+        if points not in (7, 27):
+            raise ValueError("points must be 7 or 27")
+        return cls(shape, "hpcg%d" % points)
 
     def __del__(self):
         try:
@@ -167,7 +178,7 @@ def make_opts(**kw) -> _lib.hs_opts:
             v = _GS_MODES[v]
         if k == "inner_solver" and isinstance(v, str):
             v = {"cg": _lib.HS_SOLVER_CG, "bicgstab": _lib.HS_SOLVER_BICGSTAB}[v]
-        if k in ("true_residual", "use_graph"):
+        if k in ("true_residual", "use_graph", "paper_order"):
             v = int(bool(v))
         if not hasattr(o, k):
             raise TypeError("unknown solver option %r" % k)
@@ -180,6 +191,7 @@ _SOLVER_FN = {
     _lib.HS_SOLVER_GAUSS_SEIDEL: "hs_gauss_seidel",
     _lib.HS_SOLVER_CG: "hs_cg",
     _lib.HS_SOLVER_BICGSTAB: "hs_bicgstab",
+    _lib.HS_SOLVER_CG_NB: "hs_cg_nb",
 }
 
 
@@ -262,9 +274,17 @@ def cg(A: Operator, b, x0=None, tol: float = 1e-10, maxit: int = 10000, history:
     return _solve(_lib.HS_SOLVER_CG, A, b, x0, tol, maxit, history, **kw)
 
 
+def cg_nb(A: Operator, b, x0=None, tol: float = 1e-10, maxit: int = 10000, history: bool = True, **kw):
+    """CG-NB (the paper's Algorithm 1): SpMV on r, A p by recurrence, one fused
+    pass and one grid reduction per iteration.  paper_order=True applies the
+    printed final step x = x_l + alpha_l p_l."""
+    return _solve(_lib.HS_SOLVER_CG_NB, A, b, x0, tol, maxit, history, **kw)
+
+
 def bicgstab(A: Operator, b, x0=None, tol: float = 1e-10, maxit: int = 10000, history: bool = True,
              restart_eps: float = 1e-5, **kw):
-    """BiCGStab with Algorithm 2's normalised shadow residual and restart."""
+    """BiCGStab with Algorithm 2's normalised shadow residual and restart;
+    paper_order=True gives Algorithm 2's statement order (BiCGStab-B1)."""
     return _solve(_lib.HS_SOLVER_BICGSTAB, A, b, x0, tol, maxit, history, restart_eps=restart_eps, **kw)
 
 

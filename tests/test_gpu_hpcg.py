@@ -1,0 +1,120 @@
+"""The paper's benchmark system (section 4.1) on the GPU against the FP64 oracle:
+HPCG's 7- and 27-point matrices (diagonal 27, -1 per neighbour), b = A 1,
+x0 = 0, absolute criterion ||r|| < 1e-6.  The 27-point operator runs on the
+box-sum tile engine (separable 3x3x3 sums).
+
+Tolerances: SpMV 1e-13 relative; Jacobi iterates after k sweeps 1e-12;
+Krylov counts within +-2 of the oracle's and the solution within the
+conditioning bound of x = 1 (cond <= 54 for the 27-point system, <= 27/15 for
+the 7-point one)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2305_05988_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2305_05988_gb300 as hs  # noqa: E402
+from test_gpu_parity import dev, host, rel  # noqa: E402
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "hpcg_counts.json")
+SHAPES = [(37, 19, 11), (64, 33, 40), (5, 4, 3), (33, 8, 70), (1, 1, 1)]
+
+
+def ops(shape, points):
+    kind = oracle.HPCG7 if points == 7 else oracle.HPCG27
+    return oracle.Operator(shape, kind), hs.Operator.hpcg(shape, points)
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("points", [7, 27])
+def test_hpcg_spmv(shape, points):
+    A_o, A_g = ops(shape, points)
+    x = inputs.uniform_pm1(51, 1, A_o.N)
+    assert rel(host(A_g.spmv(dev(x))), A_o.spmv(x)) <= 1e-13
+    ones = np.ones(A_o.N)
+    assert np.array_equal(host(A_g.spmv(dev(ones))), A_o.spmv(ones))   # integer row sums: exact
+    xf = x.astype(np.float32).astype(np.float64)
+    assert rel(host(A_g.spmv(dev(xf, torch.float32))), A_o.spmv(xf)) <= 2e-6
+
+
+@pytest.mark.parametrize("shape", SHAPES[:4])
+@pytest.mark.parametrize("points", [7, 27])
+def test_hpcg_residual_and_jacobi(shape, points):
+    A_o, A_g = ops(shape, points)
+    b = inputs.uniform_pm1(52, 1, A_o.N)
+    x0 = inputs.uniform_pm1(53, 1, A_o.N)
+    assert rel(host(A_g.residual(dev(b), dev(x0))), b - A_o.spmv(x0)) <= 1e-13
+    for k in (1, 7, 30):
+        x_o, _, _, _ = oracle.jacobi(A_o, b, x0, maxit=k)
+        x_g, info = hs.jacobi(A_g, dev(b), dev(x0), maxit=k)
+        assert info.iters == k and rel(host(x_g), x_o) <= 1e-12
+
+
+def _paper_system(shape, points):
+    A_o, A_g = ops(shape, points)
+    b = A_o.spmv(np.ones(A_o.N))
+    return A_o, A_g, b, 1e-6 / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("points", [7, 27])
+def test_hpcg_krylov_paper_criterion(points):
+    shape = (64, 48, 72)
+    A_o, A_g, b, tol = _paper_system(shape, points)
+    bt = dev(b)
+    runs = (("cg", hs.cg, lambda: oracle.cg(A_o, b, tol=tol, maxit=5000)[1]),
+            ("cg_nb", hs.cg_nb, lambda: oracle.cg_nb(A_o, b, tol=tol, maxit=5000)[1]),
+            ("bicgstab", hs.bicgstab, lambda: oracle.bicgstab(A_o, b, tol=tol, maxit=5000)[1]),
+            ("jacobi", hs.jacobi, lambda: oracle.jacobi(A_o, b, tol=tol, maxit=5000)[1]))
+    for name, fn, ora in runs:
+        x, info = fn(A_g, bt, tol=tol, maxit=5000)
+        it_o = ora()
+        assert info.status == "OK", (name, info)
+        assert abs(info.iters - it_o) <= 2, (name, info.iters, it_o)
+        xh = host(x)
+        # absolute residual below the paper's 1e-6 (to the rounding of the check)
+        assert np.linalg.norm(b - A_o.spmv(xh)) <= 1e-6 * (1 + 1e-3), name
+        assert np.max(np.abs(xh - 1.0)) <= 54 * 1e-6, name
+
+
+def test_hpcg7_gauss_seidel_and_unsupported_paths():
+    A_o, A_g, b, tol = _paper_system((40, 30, 20), 7)
+    x_o, it_o, _, _ = oracle.gauss_seidel(A_o, b, tol=tol, maxit=500, mode=oracle.GS_SYMMETRIC)
+    x_g, info = hs.gauss_seidel(A_g, dev(b), tol=tol, maxit=500, mode="symmetric")
+    assert info.status == "OK" and abs(info.iters - it_o) <= 1
+    assert np.max(np.abs(host(x_g) - 1.0)) <= 1e-5
+    _, A27 = ops((20, 10, 10), 27)
+    with pytest.raises(hs.HsError):
+        hs.gauss_seidel(A27, dev(np.ones(2000)), maxit=2)
+    with pytest.raises(hs.HsError):
+        hs.Batch([A27], ["cg"])
+    with pytest.raises(hs.HsError):
+        hs.Operator.hpcg((20, 10), 27)
+
+
+@pytest.mark.parametrize("points", [7, 27])
+def test_hpcg_full_size_against_golden_counts(points):
+    # the paper's grid for one node: 48 ranks x 128^3 = 128 x 128 x 6144
+    if not os.path.exists(GOLDEN):
+        pytest.skip("golden counts not generated")
+    golden = json.load(open(GOLDEN)).get("hpcg%d" % points, {})
+    shape = (128, 128, 6144)
+    A_g = hs.Operator.hpcg(shape, points)
+    ones = torch.ones(A_g.N, dtype=torch.float64, device="cuda")
+    b = A_g.spmv(ones)
+    bn = torch.linalg.norm(b).item()
+    tol = 1e-6 / bn
+    for name, fn in (("cg", hs.cg), ("bicgstab", hs.bicgstab), ("jacobi", hs.jacobi)):
+        if name not in golden:
+            continue
+        g = golden[name]
+        assert abs(bn - g["norm_b"]) <= 1e-9 * bn
+        x, info = fn(A_g, b, tol=tol, maxit=5000)
+        assert info.status == "OK"
+        assert abs(info.iters - g["iters"]) <= 2, (name, info.iters, g)
+        assert torch.max(torch.abs(x - 1.0)).item() <= 54 * 1e-6

@@ -14,8 +14,8 @@ import pytest
 import scipy.linalg as sla
 
 import oracle
-from dense_ref import (grid_coords, laplacian_dense, tensor_vec, toeplitz_eig_1d,
-                       tridiag, upwind_dense)
+from dense_ref import (grid_coords, kron_sum, laplacian_dense, tensor_vec, toeplitz_eig_1d, tridiag,
+                       upwind_dense)
 from paper_2305_05988_gb300 import inputs
 
 TINY_SHAPES = [(1,), (7,), (1, 1), (2, 3), (5, 4), (3, 4, 5), (2, 1, 3)]
@@ -388,6 +388,67 @@ def test_bicgstab_restart_fires_and_both_converge():
     assert st0 == oracle.OK and st1 == oracle.OK
     for x in (x0, x1):
         assert np.linalg.norm(x - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+# --------------------------------------------------------------------------
+# HPCG 7- and 27-point systems (section 4.1)
+# --------------------------------------------------------------------------
+
+def hpcg27_dense(shape):
+    """28 I - T_z (x) T_y (x) T_x with T = tridiag(1, 1, 1): -1 on the 26
+    neighbours of the 3x3x3 box inside the grid, 27 on the diagonal."""
+    Ts = [tridiag(n, 1.0, 1.0, 1.0) for n in shape]
+    K = Ts[-1]
+    for T in reversed(Ts[:-1]):
+        K = np.kron(K, T)
+    return 28.0 * np.eye(K.shape[0]) - K
+
+
+def hpcg7_dense(shape):
+    """27 I - (B_x (+) B_y (+) B_z) with B = tridiag(1, 0, 1)."""
+    return 27.0 * np.eye(int(np.prod(shape))) - kron_sum([tridiag(n, 1.0, 0.0, 1.0) for n in shape])
+
+
+@pytest.mark.parametrize("shape", [(3, 4, 5), (2, 2, 2), (5, 1, 3), (4, 3)])
+def test_hpcg_dense_assembly(shape):
+    for kind, ref in ((oracle.HPCG27, hpcg27_dense), (oracle.HPCG7, hpcg7_dense)):
+        if kind == oracle.HPCG27 and len(shape) < 3:
+            continue
+        M = oracle.Operator(shape, kind).dense()
+        assert np.array_equal(M, ref(shape))
+        x = inputs.uniform_pm1(41, 1, M.shape[0])
+        assert np.allclose(oracle.Operator(shape, kind).spmv(x), M @ x, rtol=0, atol=1e-13)
+
+
+def test_hpcg27_closed_form_eigenpairs():
+    # T = tridiag(1,1,1) has eigenpairs 1 + 2 cos(m pi/(n+1)), sin(i m pi/(n+1))
+    shape = (9, 7, 6)
+    A = oracle.Operator(shape, oracle.HPCG27)
+    for ms in ((1, 1, 1), (2, 5, 3), (9, 7, 6)):
+        vs, prod = [], 1.0
+        for n, m in zip(shape, ms):
+            th = m * math.pi / (n + 1)
+            vs.append(np.sin(th * np.arange(1, n + 1)))
+            prod *= 1.0 + 2.0 * math.cos(th)
+        v = tensor_vec(vs)
+        lam = 28.0 - prod
+        assert np.linalg.norm(A.spmv(v) - lam * v) <= 1e-13 * np.linalg.norm(v) * 28
+
+
+def test_hpcg_exact_solution_ones():
+    # b = A 1 makes x = 1 the exact solution (section 4.1); every interior
+    # row of the 27-point system sums to 1, of the 7-point one to 21
+    shape = (12, 10, 9)
+    for kind, interior in ((oracle.HPCG27, 1.0), (oracle.HPCG7, 21.0)):
+        A = oracle.Operator(shape, kind)
+        b = A.spmv(np.ones(A.N))
+        assert b.reshape(9, 10, 12)[4, 5, 6] == interior
+        x, it, st, _ = oracle.cg(A, b, tol=1e-13, maxit=500)
+        assert st == oracle.OK and np.max(np.abs(x - 1.0)) <= 1e-12
+        xb, _, stb, _, _ = oracle.bicgstab(A, b, tol=1e-13, maxit=500)
+        assert stb == oracle.OK and np.max(np.abs(xb - 1.0)) <= 1e-12
+        xj, _, _, _ = oracle.jacobi(A, b, maxit=2000, tol=1e-14)
+        assert np.max(np.abs(xj - 1.0)) <= 1e-12
 
 
 # --------------------------------------------------------------------------
