@@ -60,6 +60,14 @@ BYTES = {
 #             s FMA, stencil 6 FMA, 3 dot FMA; x 2 FMA, r FMA,
 #             2 dot FMA                                             = 48
 FLOPS = {"spmv": 10.0, "jacobi": 9.0, "gauss_seidel": 9.0, "cg": 19.0, "bicgstab": 48.0}
+
+# DRAM bytes per unknown and iteration measured by ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum) on the 200^3 case of the same step (every vector is
+# 64 MB there, above the 129 MB L2 with the solver state), see
+# profiles/fp64_and_traffic_poisson3d_200.md.  Traffic grows with unknowns x
+# iterations (each pass streams every vector), so a launch at 256^3 moves
+# this figure x N x iterations.  Re-measure whenever the kernel changes.
+TRAFFIC_B_PER_UNIT = {"cg": 72.6, "bicgstab": 137.0, "jacobi": 24.5}
 # FP64 pipe: 2 FMA lanes per SM per clock (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on
 # peak_sustained = 2 per SM per cycle) x 2 flops x 152 SMs.
 FP64_FLOPS_PER_CLK = 2 * 2 * 152
@@ -218,6 +226,21 @@ def run_reference(args, rank, world):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def replica_throughput(local_bytes, local_ms, dist=None, device="cpu"):
+    """Whole-job throughput of independent replicas ("replicas only": no data
+    exchange between ranks): the bytes every rank processed over the slowest
+    rank's time.  Returns (GB/s, max ms, total bytes)."""
+    if dist is None:
+        return local_bytes / (local_ms * 1e-3) / 1e9, local_ms, local_bytes
+    import torch
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    nb = torch.tensor([float(local_bytes)], dtype=torch.float64, device=device)
+    dist.all_reduce(nb, op=dist.ReduceOp.SUM)
+    ms, total = float(t.item()), float(nb.item())
+    return total / (ms * 1e-3) / 1e9, ms, total
+
+
 def run_ours(args, rank, world, dist):
     import torch
 
@@ -242,30 +265,39 @@ def run_ours(args, rank, world, dist):
     # workspaces are allocated once, outside the timed region
     xs = {k: torch.zeros(N, dtype=torch.float64, device=dev) for k in ("y", "jacobi", "gs", "cg", "bicgstab")}
 
-    def step(bv, record=None):
+    def step(bv, record=None, on_done=None):
+        """One pass of the hot path; on_done(name) runs after each solver (the
+        end-to-end loop uses it to start that solution's copy to the host while
+        the next solver computes)."""
         info = {}
+        done = on_done or (lambda name: None)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)] if record is not None else None
         if ev:
             ev[0].record(stream)
         A.spmv(bv, out=xs["y"])
+        done("y")
         if ev:
             ev[1].record(stream)
         xs["jacobi"].zero_()
         _, info["jacobi"] = hs.jacobi(A, bv, xs["jacobi"], maxit=args.sweeps, inplace=True, timeout_s=tmo)
+        done("jacobi")
         if ev:
             ev[2].record(stream)
         xs["gs"].zero_()
         _, info["gauss_seidel"] = hs.gauss_seidel(A, bv, xs["gs"], maxit=args.sweeps, inplace=True,
                                                   timeout_s=tmo)
+        done("gs")
         if ev:
             ev[3].record(stream)
         xs["cg"].zero_()
         _, info["cg"] = hs.cg(A, bv, xs["cg"], tol=args.tol, maxit=maxk, inplace=True, timeout_s=tmo)
+        done("cg")
         if ev:
             ev[4].record(stream)
         xs["bicgstab"].zero_()
         _, info["bicgstab"] = hs.bicgstab(U, bv, xs["bicgstab"], tol=args.tol, maxit=maxk, inplace=True,
                                           timeout_s=tmo)
+        done("bicgstab")
         if ev:
             ev[5].record(stream)
             record.append(ev)
@@ -305,12 +337,7 @@ def run_ours(args, rank, world, dist):
     barrier()
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    total_bytes = sum(step_bytes(i) for i in infos) * world
-    value = total_bytes / (ms * 1e-3) / 1e9
+    value, ms, total_bytes = replica_throughput(sum(step_bytes(i) for i in infos), ms, dist, dev)
 
     # per-solver breakdown from the in-step events
     names = ["spmv", "jacobi", "gauss_seidel", "cg", "bicgstab"]
@@ -373,7 +400,9 @@ def run_ours(args, rank, world, dist):
                     "frac": round(tflops / fp64_peak, 4),
                     "peak_source": "FP64 pipe: 2 FMA lanes/SM/clock x 2 flops x 152 SMs x %.0f MHz (median SM "
                                    "clock sampled in the timed region)" % (clk / 1e6),
-                    "traffic": None, "flops_per_unknown_iter": FLOPS[dom], "iters": its, "launch_ms": round(dt, 3),
+                    "traffic": (round(TRAFFIC_B_PER_UNIT[dom] * N * its) if dom in TRAFFIC_B_PER_UNIT else None),
+                    "traffic_source": "ncu DRAM bytes per unknown-iteration at 200^3 x N x iterations",
+                    "flops_per_unknown_iter": FLOPS[dom], "iters": its, "launch_ms": round(dt, 3),
                     "hbm": {"achieved": round(hbm_gbs, 1), "peak": peak, "unit": "GB/s",
                             "frac": round(hbm_gbs / peak, 4), "peak_source": peak_kind,
                             "alg_bytes_per_unknown_iter": BYTES[dom]}}
@@ -388,21 +417,26 @@ def run_ours(args, rank, world, dist):
         torch.cuda.synchronize()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e_infos = []
+        copy_stream = torch.cuda.Stream(dev)
+
+        def start_copy(name):
+            # the solution is final: copy it out on the side stream while the
+            # next solver runs on the main one
+            copy_stream.wait_stream(stream)
+            with torch.cuda.stream(copy_stream):
+                outs[name].copy_(xs[name], non_blocking=True)
+
         f0.record(stream)
         for _ in range(args.steps):
+            stream.wait_stream(copy_stream)   # the previous step's copies read xs
             bd.copy_(bp, non_blocking=True)
-            e_infos.append(step(bd))
-            for k in xs:
-                outs[k].copy_(xs[k], non_blocking=True)
+            e_infos.append(step(bd, on_done=start_copy))
+        stream.wait_stream(copy_stream)
         f1.record(stream)
         torch.cuda.synchronize()
         ems = f0.elapsed_time(f1)
-        if dist is not None:
-            t = torch.tensor([ems], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
-        e_bytes = sum(step_bytes(i) for i in e_infos) * world
-        e2e = {"value": e_bytes / (ems * 1e-3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": 8 * N,
+        e_value, ems, _ = replica_throughput(sum(step_bytes(i) for i in e_infos), ems, dist, dev)
+        e2e = {"value": e_value, "unit": "GB/s", "h2d_bytes_per_step": 8 * N,
                "d2h_bytes_per_step": 8 * N * len(xs), "ms_per_step": ems / args.steps}
 
     # ---- CPU baseline (rank 0, N = 1 only) ----
@@ -423,6 +457,8 @@ def run_ours(args, rank, world, dist):
         extras["paper_variants"] = variant_comparison(n, dev, tmo)
     if rank == 0 and args.hpcg_nz > 0:
         extras["hpcg"] = hpcg_timing(args.hpcg_nz, dev, tmo)
+    if rank == 0 and not args.no_variants:
+        extras["temporal_blocking"] = blocking_timing(n, args.sweeps, dev, tmo)
 
     # kernels launched per step: spmv 1; jacobi, cg, bicgstab: control init +
     # persistent solver + residual + finalize = 4 each; gauss-seidel: solver +
@@ -442,6 +478,36 @@ def run_ours(args, rank, world, dist):
             "extras": extras,
         }
         print(json.dumps(line), flush=True)
+
+
+def blocking_timing(n, sweeps, dev, tmo):
+    """Temporal blocking of Jacobi on the step's Laplacian: 1..4 sweeps per pass
+    over the grid, FP64 and FP32, microseconds per sweep (the iterates are
+    bitwise those of one sweep per pass)."""
+    import torch
+
+    import paper_2305_05988_gb300 as hs
+    from paper_2305_05988_gb300 import inputs
+    shape = (n, n, n)
+    A = hs.Operator.laplacian(shape)
+    stream = torch.cuda.current_stream(dev)
+    out = {"workload": "%d^3 Laplacian, Jacobi x%d, sweeps per pass 1..4" % (n, sweeps)}
+    for dt, name in ((torch.float64, "f64"), (torch.float32, "f32")):
+        b = torch.from_numpy(inputs.rhs_uniform(shape, 0)).to(device=dev, dtype=dt)
+        rec = {}
+        for spp in (1, 2, 3, 4):
+            hs.jacobi(A, b, maxit=sweeps, sweeps_per_pass=spp, true_residual=False, timeout_s=max(tmo, 10.0))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            hs.jacobi(A, b, maxit=sweeps, sweeps_per_pass=spp, true_residual=False, timeout_s=max(tmo, 10.0))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            rec["spp%d" % spp] = round(1e3 * e0.elapsed_time(e1) / sweeps, 2)
+        out[name + "_us_per_sweep"] = rec
+        del b
+    torch.cuda.empty_cache()
+    return out
 
 
 def hpcg_timing(nz, dev, tmo):

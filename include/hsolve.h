@@ -109,6 +109,11 @@ typedef struct {
                                the iterate one step beyond the converged one);
                                0 (default): test right after each residual
                                update and return that iterate                   */
+    int sweeps_per_pass;    /* Jacobi: sweeps applied per pass over the grid
+                               (temporal blocking, 1..4; default 1).  Used for
+                               constant-coefficient 3-D 7-point operators with
+                               tol = 0; the iterates are bitwise those of single
+                               sweeps.  Other cases run one sweep per pass.     */
 } hs_opts;
 
 typedef struct {

@@ -44,7 +44,8 @@ class hs_opts(ctypes.Structure):
                 ("tile_rows", ctypes.c_int),
                 ("tile_planes", ctypes.c_int),
                 ("max_blocks", ctypes.c_int),
-                ("paper_order", ctypes.c_int)]
+                ("paper_order", ctypes.c_int),
+                ("sweeps_per_pass", ctypes.c_int)]
 
 
 class hs_result(ctypes.Structure):

@@ -75,6 +75,7 @@ static hs_opts default_opts() {
   o.inner_solver = HS_SOLVER_CG;
   o.inner_maxit = 10000;
   o.use_graph = 1;
+  o.sweeps_per_pass = 1;
   return o;
 }
 
@@ -110,6 +111,8 @@ bool merge_opts(const hs_opts* in, hs_opts* out) {
   if (out->tile_planes < 0) out->tile_planes = 0;
   if (out->max_blocks < 0) out->max_blocks = 0;
   out->paper_order = out->paper_order ? 1 : 0;
+  if (out->sweeps_per_pass < 1) out->sweeps_per_pass = 1;
+  if (out->sweeps_per_pass > 4) out->sweeps_per_pass = 4;
   return true;
 }
 

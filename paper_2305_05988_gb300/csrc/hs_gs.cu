@@ -33,11 +33,13 @@ namespace hs {
 
 template <int NDIM>
 struct GsTile;
-// Tile shapes (one thread per x-line: TY * TZ threads per block).  The 3-D
-// default 32 x 16 x 8 can be overridden at build time for measurements
-// (-DHS_GS_TY=.. -DHS_GS_TZ=..).
+// Tile shapes (one thread per x-line: TY * TZ threads per block).  3-D
+// default 32 x 8 x 8 (two warps; measured on GB300 at 256^3, 200 sweeps:
+// 418 us/sweep against 456 for 32 x 16 x 8, 522 for one-warp 32 x 4 x 8 and
+// 32 x 8 x 4, 458-460 for 32 x 4 x 16 and 32 x 16 x 4).  Override at build
+// time for measurements (-DHS_GS_TY=.. -DHS_GS_TZ=..).
 #ifndef HS_GS_TY
-#define HS_GS_TY 16
+#define HS_GS_TY 8
 #endif
 #ifndef HS_GS_TZ
 #define HS_GS_TZ 8
@@ -56,7 +58,6 @@ constexpr int gs_threads() { return GsTile<NDIM>::TY * GsTile<NDIM>::TZ; }
 template <typename T>
 struct GsArgs {
   Geom g;
-  Tiling tl;            // z-march tiling for the residual pass (by = lines / 32)
   Coef<T> cf;           // Jacobi-form couplings (g = -a/a_ii) or var-k arrays (D = 1/a_ii)
   T invd;
   double dscale2;
@@ -91,39 +92,38 @@ __device__ __forceinline__ void line_of_thread(int t, int TY, int TZ, int& jl, i
   }
 }
 
-// Residual of x via the Jacobi form r = a_ii (x' - x), accumulated per thread.
+// Relative residual of x through the Jacobi form r_i = a_ii (x'_i - x_i),
+// reduced over the grid.  Neighbours come straight from global memory (a
+// residual is formed once per check_every sweeps, so no tile staging; this
+// also frees the GS block from the tile engine's three-warp minimum).
 template <typename T, int OPK, int NDIM>
-struct GsResSink {
-  Coef<T> cf;
-  Geom g;
-  const T* bsrc;
-  double acc[1];
-  struct Raw {
-    OpRaw<T, OPK> o;
-    T b;
-  };
-  __device__ __forceinline__ Raw fetch(long long idx, int i, int j, int k) const {
-    return Raw{op_fetch<T, OPK, NDIM>(cf, g, idx, i, j, k), __ldcg(bsrc + idx)};
-  }
-  __device__ __forceinline__ void operator()(long long, const Nbr<T>& nb, const Raw& q, int, int, int) {
-    T d = jacobi_apply<T, OPK, NDIM>(cf, q.o, nb, q.b) - nb.c;
-    if constexpr (OPK == OP_VARK) d = d / q.o.d;
+__device__ bool gs_residual(const GsArgs<T>& a, T* /*sm*/, double* sh, double bb, double* rel) {
+  const Geom& g = a.g;
+  const T* bsrc = (OPK == OP_VARK) ? a.b : a.bD;
+  const T* x = a.x;
+  double acc[1] = {0.0};
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < g.N;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % g.nx);
+    const int j = (int)((idx / g.nx) % g.ny);
+    const int k = (int)(idx / g.plane);
+    Nbr<T> nb;
+    nb.c = __ldcg(x + idx);
+    nb.w = i > 0 ? __ldcg(x + idx - 1) : T(0);
+    nb.e = i + 1 < g.nx ? __ldcg(x + idx + 1) : T(0);
+    nb.s = j > 0 ? __ldcg(x + idx - g.nx) : T(0);
+    nb.n = j + 1 < g.ny ? __ldcg(x + idx + g.nx) : T(0);
+    nb.b = (NDIM == 3 && k > 0) ? __ldcg(x + idx - g.plane) : T(0);
+    nb.t = (NDIM == 3 && k + 1 < g.nz) ? __ldcg(x + idx + g.plane) : T(0);
+    const OpRaw<T, OPK> o = op_fetch<T, OPK, NDIM>(a.cf, g, idx, i, j, k);
+    T d = jacobi_apply<T, OPK, NDIM>(a.cf, o, nb, __ldcg(bsrc + idx)) - nb.c;
+    if constexpr (OPK == OP_VARK) d = d / o.d;
     acc[0] += widen(d) * widen(d);
   }
-};
-
-// Relative residual of x reduced over the grid.
-template <typename T, int OPK, int NDIM>
-__device__ bool gs_residual(const GsArgs<T>& a, T* sm, double* sh, double bb, double* rel) {
-  const T* bsrc = (OPK == OP_VARK) ? a.b : a.bD;
-  LoadSrc<T, true> src{a.x};
-  GsResSink<T, OPK, NDIM> sink{a.cf, a.g, bsrc, {0.0}};
-  for (int item = blockIdx.x; item < a.tl.items(); item += gridDim.x)
-    zmarch_item<T, NDIM, 1>(a.g, a.tl, item, sm, src, sink);
-  block_sum<1>(sink.acc, sh);
+  block_sum<1>(acc, sh);
   double rr[1];
-  if (!grid_reduce<1>(a.cm.ctrl, a.cm.partials, sink.acc, rr, sh)) return false;
-  double sc = (OPK == OP_VARK) ? 1.0 : a.dscale2;
+  if (!grid_reduce<1>(a.cm.ctrl, a.cm.partials, acc, rr, sh)) return false;
+  const double sc = (OPK == OP_VARK) ? 1.0 : a.dscale2;
   *rel = sqrt(rr[0] * sc / bb);
   return true;
 }
@@ -514,9 +514,7 @@ static hs_status gs_run_t(const SolveArgs& sa, hs_result* res, double* hist) {
   a.check_every = sa.o.check_every;
   a.tol = sa.tol;
   const int sx = TX + 2, sy = TY + 2, sz = (NDIM == 3) ? TZ + 2 : 1;
-  size_t smem = (size_t)sx * sy * sz * sizeof(T);
-  size_t slab = (size_t)2 * (THREADS / 32 + 2) * (BX + 2) * sizeof(T);
-  smem = std::max(smem, slab);
+  const size_t smem = (size_t)sx * sy * sz * sizeof(T);
   auto kern = k_gs<T, OPK, NDIM>;
   // static shared memory (reduction scratch) comes on top of the dynamic
   // tile, so always raise the dynamic limit to what the tile needs
@@ -530,7 +528,6 @@ static hs_status gs_run_t(const SolveArgs& sa, hs_result* res, double* hist) {
     return HS_ERR_CUDA;
   }
   int grid = std::min(per_sm * sm_count(), MAX_BLOCKS);
-  a.tl = choose_tiling(g, THREADS / 32, grid, false, 0, 1);
   void* args[] = {&a};
   e = cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(THREADS), args, smem, sa.stream);
   if (e != cudaSuccess) return cuda_fail(e, "cooperative launch");

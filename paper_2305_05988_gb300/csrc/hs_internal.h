@@ -116,6 +116,8 @@ hs_status run_jacobi(const SolveArgs& a, hs_result* res, double* hist);
 hs_status run_cg(const SolveArgs& a, hs_result* res, double* hist);
 hs_status run_bicgstab(const SolveArgs& a, hs_result* res, double* hist);
 hs_status run_cg_nb(const SolveArgs& a, hs_result* res, double* hist);
+bool jacobi_tb_applies(const SolveArgs& a);
+hs_status run_jacobi_tb(const SolveArgs& a, hs_result* res, double* hist);
 hs_status run_gauss_seidel(const SolveArgs& a, hs_result* res, double* hist);
 hs_status run_spmv(const hs_op* A, hs_dtype dt, const void* x, void* y, cudaStream_t st);
 hs_status run_residual_plain(const hs_op* A, hs_dtype dt, const void* b, const void* x, void* r, cudaStream_t st);

@@ -661,6 +661,7 @@ hs_status finish_solve_pub(const SolveArgs& sa, const Common& cm, const void* D,
 
 // ---- Jacobi -----------------------------------------------------------------
 hs_status run_jacobi(const SolveArgs& sa, hs_result* res, double* hist) {
+  if (jacobi_tb_applies(sa)) return run_jacobi_tb(sa, res, hist);
   return dispatch(sa.dtype, opkind_of(sa.A), sa.A->ndim, [&](auto tag) -> hs_status {
     using Tg = decltype(tag);
     using T = typename Tg::T;

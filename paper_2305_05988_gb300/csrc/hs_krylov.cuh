@@ -18,8 +18,13 @@ constexpr int CX_ST = 2;    // SpMV / residual (7-point operators)
 template <int OPK>
 __host__ __device__ constexpr int cx_st() { return OPK == OP_BOX27 ? 1 : CX_ST; }
 constexpr int CX_BI = 1;    // BiCGStab
+#ifndef HS_JAC_CX32
+#define HS_JAC_CX32 1
+#endif
 template <typename T, int OPK>
-__host__ __device__ constexpr int cx_jac() { return 1; }
+__host__ __device__ constexpr int cx_jac() {
+  return (sizeof(T) == 4 && OPK != OP_BOX27) ? HS_JAC_CX32 : 1;
+}
 template <typename T, int OPK>
 __host__ __device__ constexpr int cx_cg() { return 1; }
 

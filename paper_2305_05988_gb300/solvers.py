@@ -173,6 +173,7 @@ def make_opts(**kw) -> _lib.hs_opts:
     o.inner_solver = _lib.HS_SOLVER_CG
     o.inner_maxit = 10000
     o.use_graph = 1
+    o.sweeps_per_pass = 1
     for k, v in kw.items():
         if k == "gs_mode" and isinstance(v, str):
             v = _GS_MODES[v]
