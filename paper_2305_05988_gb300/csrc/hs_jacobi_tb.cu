@@ -39,100 +39,110 @@ struct JacTbArgs {
   int sweeps;      // total sweeps
 };
 
+// Block layout: one thread per column of the widest region, the tile widened
+// by S nodes on every side: (32 + 2S) x (by + 2S) threads (TB_BY = 8 rows).
+constexpr int TB_BY = 8;
 template <int S>
-__host__ __device__ constexpr int tb_w(int s) { return BX + 2 * (S - s); }
+__host__ __device__ constexpr int tb_w() { return BX + 2 * S; }
 template <int S>
-__host__ __device__ inline int tb_h(int by, int s) { return by + 2 * (S - s); }
-
-// Shared-memory values of the level rings (levels 0 .. S-1, 3 planes each).
+__host__ __device__ constexpr int tb_h() { return TB_BY + 2 * S; }
 template <int S>
-__host__ __device__ inline int tb_ring_values(int by) {
-  int v = 0;
-  for (int s = 0; s < S; s++) v += 3 * tb_w<S>(s) * tb_h<S>(by, s);
-  return v;
-}
-
-template <typename T, int S>
-__device__ __forceinline__ T* tb_ring(T* sm, int by, int s) {
-  int off = 0;
-  for (int q = 0; q < s; q++) off += 3 * tb_w<S>(q) * tb_h<S>(by, q);
-  return sm + off;
-}
+__host__ __device__ constexpr int tb_threads() { return ((tb_w<S>() * tb_h<S>() + 31) / 32) * 32; }
+// shared memory: levels 0 .. S-1, two plane buffers each
+template <int S>
+__host__ __device__ constexpr int tb_smem_values() { return S * 2 * tb_w<S>() * tb_h<S>(); }
 
 // One pass of L sweeps (1 <= L <= S) over one work item, src -> dst.
+//
+// Thread (tx, ty) owns column (i0 - S + tx, j0 - S + ty) and keeps, per level
+// s < S, the column's values at the last three planes in registers (the z
+// neighbours); the plane of each level also goes to shared memory, double
+// buffered, for the x / y neighbours.  Step t loads level 0 at plane t and
+// forms level s at plane t - s inside region s (the tile widened by S - s):
+// every shared read of step t is of a plane written in step t - 1, so one
+// barrier per step suffices.  The chunk starts S planes early (levels fill
+// up) and runs S planes past its end (level S needs level S - 1 one plane up).
 template <typename T, int S>
 __device__ void tb_item(const JacTbArgs<T>& a, int item, int L, const T* __restrict__ src, T* __restrict__ dst,
                         T* sm) {
+  constexpr int W = tb_w<S>(), H = tb_h<S>(), PL = W * H;
   const Geom& g = a.g;
   int i0, j0, z0, z1;
   decode_item(a.tl, g, item, i0, j0, z0, z1);
-  const int by = a.tl.by;
-  const int nt = blockDim.x;
+  const int tx = threadIdx.x % W, ty = threadIdx.x / W;
+  const bool live = threadIdx.x < PL;
+  const int gi = i0 - S + tx, gj = j0 - S + ty;
+  const bool col_in = live && gi >= 0 && gi < g.nx && gj >= 0 && gj < g.ny;
+  const long long col = (long long)gj * g.nx + gi;
   const long long P = g.plane;
-  for (int t = z0 - L; t <= z1 - 1 + L; t++) {
-    // ---- level 0: stage plane t of the input over the widest region
+  const int c = ty * W + tx;
+  T q[S][3];   // level s at planes t-s-2, t-s-1, t-s (slots rotate)
+#pragma unroll
+  for (int s = 0; s < S; s++) q[s][0] = q[s][1] = q[s][2] = T(0);
+  // loads run PD planes ahead of their use: the input at plane t + PD, and b/a_ii
+  // for planes t - S .. t + PD - 1 (level s at step t needs plane t - s)
+  constexpr int PD = 2;
+  auto ld_src = [&](int pl) -> T {
+    return (col_in && pl >= 0 && pl < g.nz) ? __ldcg(src + (long long)pl * P + col) : T(0);
+  };
+  auto ld_bd = [&](int pl) -> T {   // bD: written in this kernel, so through L2
+    return (col_in && pl >= 0 && pl < g.nz) ? __ldcg(a.bD + (long long)pl * P + col) : T(0);
+  };
+  const int t0 = z0 - S;
+  T srcq[PD], bdq[S + PD];
+#pragma unroll
+  for (int m = 0; m < PD; m++) srcq[m] = ld_src(t0 + m);
+#pragma unroll
+  for (int m = 0; m < S + PD; m++) bdq[m] = ld_bd(t0 - S + m);
+  for (int t = t0; t <= z1 - 1 + S; t++) {
+    // level 0, plane t
     {
-      const int W = tb_w<S>(0), H = tb_h<S>(by, 0);
-      T* r0 = tb_ring<T, S>(sm, by, 0) + ((t % 3 + 3) % 3) * W * H;
-      const int ib = i0 - S, jb = j0 - S;
-      const bool zin = t >= 0 && t < g.nz;
-      for (int e = threadIdx.x; e < W * H; e += nt) {
-        const int ii = e % W, jj = e / W;
-        const int gi = ib + ii, gj = jb + jj;
-        T v = T(0);
-        if (zin && gi >= 0 && gi < g.nx && gj >= 0 && gj < g.ny) v = __ldcg(src + (long long)t * P + (long long)gj * g.nx + gi);
-        r0[e] = v;
+      const T v = srcq[0];
+#pragma unroll
+      for (int m = 0; m + 1 < PD; m++) srcq[m] = srcq[m + 1];
+      srcq[PD - 1] = ld_src(t + PD);
+      q[0][0] = q[0][1];
+      q[0][1] = q[0][2];
+      q[0][2] = v;
+      if (live) sm[(t & 1) * PL + c] = v;
+    }
+    // levels 1 .. L on plane t - s, from level s - 1 at planes t - s - 1 .. t - s + 1
+#pragma unroll
+    for (int s = 1; s <= S; s++) {
+      if (s > L) break;
+      const int p = t - s;
+      const bool in_region = live && tx >= s && tx < W - s && ty >= s && ty < H - s;
+      T v = T(0);
+      if (in_region && col_in && p >= 0 && p < g.nz) {
+        const T* pl = sm + (s - 1) * 2 * PL + (p & 1) * PL;   // level s-1, plane p (written last step)
+        Nbr<T> nb;
+        nb.c = q[s - 1][1];
+        nb.w = pl[c - 1];
+        nb.e = pl[c + 1];
+        nb.s = pl[c - W];
+        nb.n = pl[c + W];
+        nb.b = q[s - 1][0];
+        nb.t = q[s - 1][2];
+        v = jacobi_apply<T, OP_SYM, 3>(a.cf, OpRaw<T, OP_SYM>{}, nb, bdq[S - s]);
+        if (s == L && p >= z0 && p < z1 && tx >= S && tx < W - S && ty >= S && ty < H - S)
+          dst[(long long)p * P + col] = v;
+      }
+      if (s < S) {
+        q[s][0] = q[s][1];
+        q[s][1] = q[s][2];
+        q[s][2] = v;
+        if (live) sm[s * 2 * PL + (p & 1) * PL + c] = v;
       }
     }
+#pragma unroll
+    for (int m = 0; m + 1 < S + PD; m++) bdq[m] = bdq[m + 1];
+    bdq[S + PD - 1] = ld_bd(t + 1 + PD - 1);
     __syncthreads();
-    // ---- levels 1 .. L: level s on plane q = t - s from level s-1 planes q-1, q, q+1
-    for (int s = 1; s <= L; s++) {
-      const int q = t - s;
-      const bool out = (s == L);
-      // planes of level s this chunk needs: [z0 - (L - s), z1 - 1 + (L - s)]
-      const bool need = q >= z0 - (L - s) && q <= z1 - 1 + (L - s);
-      if (need) {
-        const int lv = s - 1;   // ring of the input level (region widened by S - lv)
-        const int Wi = tb_w<S>(lv), Hi = tb_h<S>(by, lv);
-        const T* rin = tb_ring<T, S>(sm, by, lv);
-        const T* pm = rin + (((q - 1) % 3 + 3) % 3) * Wi * Hi;
-        const T* pc = rin + ((q % 3 + 3) % 3) * Wi * Hi;
-        const T* pp = rin + (((q + 1) % 3 + 3) % 3) * Wi * Hi;
-        // output region: the tile (last level) or the tile widened by S - s
-        const int wide = out ? 0 : S - s;
-        const int W = BX + 2 * wide, H = by + 2 * wide;
-        const int off = (S - lv) - wide;   // input-region coordinates of output (0, 0)
-        const bool zin = q >= 0 && q < g.nz;
-        T* rout = out ? nullptr : tb_ring<T, S>(sm, by, s) + ((q % 3 + 3) % 3) * W * H;
-        for (int e = threadIdx.x; e < W * H; e += nt) {
-          const int ii = e % W, jj = e / W;
-          const int gi = i0 - wide + ii, gj = j0 - wide + jj;
-          const bool in = zin && gi >= 0 && gi < g.nx && gj >= 0 && gj < g.ny;
-          T v = T(0);
-          if (in) {
-            const int c = (jj + off) * Wi + (ii + off);
-            Nbr<T> nb;
-            nb.c = pc[c];
-            nb.w = pc[c - 1];
-            nb.e = pc[c + 1];
-            nb.s = pc[c - Wi];
-            nb.n = pc[c + Wi];
-            nb.b = pm[c];
-            nb.t = pp[c];
-            const long long idx = (long long)q * P + (long long)gj * g.nx + gi;
-            v = jacobi_apply<T, OP_SYM, 3>(a.cf, OpRaw<T, OP_SYM>{}, nb, __ldcg(a.bD + idx));   // bD: written in this kernel
-            if (out && q >= z0 && q < z1) dst[idx] = v;
-          }
-          if (!out) rout[e] = v;
-        }
-      }
-      __syncthreads();
-    }
   }
 }
 
 template <typename T, int S>
-__global__ void __launch_bounds__(512) k_jacobi_tb(JacTbArgs<T> a) {
+__global__ void __launch_bounds__(tb_threads<S>()) k_jacobi_tb(JacTbArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double sh[32 * MAX_SCAL];
   T* sm = reinterpret_cast<T*>(smraw);
@@ -198,9 +208,9 @@ static hs_status jacobi_tb_t(const SolveArgs& sa, hs_result* res, double* hist) 
   a.x0 = (T*)sa.x;
   a.cm = cm;
   a.sweeps = sa.maxit;
-  const int by = 8;
-  const int block = 32 * by;
-  const size_t smem = (size_t)tb_ring_values<S>(by) * sizeof(T);
+  const int by = TB_BY;
+  const int block = tb_threads<S>();
+  const size_t smem = (size_t)tb_smem_values<S>() * sizeof(T);
   int per_sm = 0;
   cudaError_t e = cudaFuncSetAttribute(k_jacobi_tb<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_tb<T, S>, block, smem);

@@ -138,8 +138,8 @@ def test_adjoint_full_size():
     # cancellation: with A(theta) u = f, the perturbed solution is u + du where
     # A(theta+-) du = -(A(theta+-) - A(theta)) u (a right-hand side that lives
     # next to the perturbed cell), and L(u + du) - L(u) = du . (du + 2 (u - u_obs)).
-    cells = (inputs.uniform(0, inputs.STREAM_FD, 4) * N).astype(np.int64)
-    delta = 1e-4
+    cells = np.unique((inputs.uniform(0, inputs.STREAM_FD, 16) * N).astype(np.int64))
+    delta = 1e-5
     lk = torch.from_numpy(logk).cuda()
     Au = A_g.spmv(u)
     d_obs = 2 * (u - u_obs)
@@ -158,7 +158,11 @@ def test_adjoint_full_size():
         lm[c] -= delta
         fd.append((dloss(lp) - dloss(lm)) / (2 * delta))
     fd = np.array(fd)
+    # over the sampled cells and per cell (floor 1e-3 max |g_FD|): the central
+    # difference error is O(delta^2) relative, the solves' O(1e-12)
     assert np.linalg.norm(g[cells] - fd) <= 1e-6 * np.linalg.norm(fd), (g[cells], fd)
+    floor = 1e-3 * np.max(np.abs(fd))
+    assert np.all(np.abs(g[cells] - fd) <= 1e-5 * np.maximum(np.abs(fd), floor)), (g[cells], fd)
 
 
 def test_batched_512_sampled_against_oracle():

@@ -118,3 +118,13 @@ def test_hpcg_full_size_against_golden_counts(points):
         assert info.status == "OK"
         assert abs(info.iters - g["iters"]) <= 2, (name, info.iters, g)
         assert torch.max(torch.abs(x - 1.0)).item() <= 54 * 1e-6
+
+
+def test_hpcg27_mixed_precision_certified():
+    # FP64 refinement with FP32 inner CG on the 27-point box engine reaches
+    # an FP64 residual below what FP32 alone can represent
+    A_o, A_g, b, _ = _paper_system((48, 40, 36), 27)
+    x, info = hs.solve_mixed(A_g, dev(b), tol=1e-12, maxit=20, inner_tol=1e-4)
+    assert info.status == "OK" and info.outer >= 2
+    assert A_o.relres(b, host(x)) <= 1e-12 * (1 + 1e-3)
+    assert np.max(np.abs(host(x) - 1.0)) <= 54 * 1e-12 * 10
