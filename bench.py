@@ -459,6 +459,7 @@ def run_ours(args, rank, world, dist):
         extras["hpcg"] = hpcg_timing(args.hpcg_nz, dev, tmo)
     if rank == 0 and not args.no_variants:
         extras["temporal_blocking"] = blocking_timing(n, args.sweeps, dev, tmo)
+        extras["poisson2d"] = poisson2d_timing(dev, tmo)
 
     # kernels launched per step: spmv 1; jacobi, cg, bicgstab: control init +
     # persistent solver + residual + finalize = 4 each; gauss-seidel: solver +
@@ -478,6 +479,34 @@ def run_ours(args, rank, world, dist):
             "extras": extras,
         }
         print(json.dumps(line), flush=True)
+
+
+def poisson2d_timing(dev, tmo):
+    """The small configuration (2-D Poisson, 128^2 interior nodes, FP64, b ~ U(-1,1)):
+    Jacobi x500, lexicographic GS x500, CG and BiCGStab to 1e-10; the working set
+    is L2-resident, so iterations/s and time-to-tolerance are the figures."""
+    import torch
+
+    import paper_2305_05988_gb300 as hs
+    from paper_2305_05988_gb300 import inputs
+    shape = (128, 128)
+    A = hs.Operator.laplacian(shape)
+    b = torch.from_numpy(inputs.rhs_uniform(shape, 0)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    out = {"workload": "poisson2d 128^2 FP64: Jacobi x500, GS x500, CG and BiCGStab to 1e-10"}
+    runs = (("jacobi", hs.jacobi, {"maxit": 500}), ("gauss_seidel", hs.gauss_seidel, {"maxit": 500}),
+            ("cg", hs.cg, {"tol": 1e-10, "maxit": 20000}), ("bicgstab", hs.bicgstab, {"tol": 1e-10, "maxit": 20000}))
+    for name, fn, kw in runs:
+        fn(A, b, true_residual=False, timeout_s=max(tmo, 10.0), **kw)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        _, info = fn(A, b, true_residual=False, timeout_s=max(tmo, 10.0), **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[name] = {"ms": round(ms, 3), "iters": info.iters, "iters_per_s": round(info.iters / (ms * 1e-3), 1)}
+    return out
 
 
 def blocking_timing(n, sweeps, dev, tmo):
@@ -523,6 +552,10 @@ def hpcg_timing(nz, dev, tmo):
     shape = (128, 128, nz)
     stream = torch.cuda.current_stream(dev)
     paper = {"hpcg7": {"cg": 12, "bicgstab": 8, "jacobi": 18}, "hpcg27": {"cg": 72, "bicgstab": 45, "jacobi": 515}}
+    # the paper's wall times on one MareNostrum 4 node (2x Xeon Platinum 8160,
+    # 48 cores, MPI-only, same grid): context, not a target
+    paper_s = {"hpcg7": {"cg": 1.52, "bicgstab": 1.96, "jacobi": 1.40},
+               "hpcg27": {"cg": 19.35, "bicgstab": 23.76, "jacobi": 113.91}}
     out = {"workload": "HPCG %dx%dx%d, b = A 1, x0 = 0, ||r|| < 1e-6" % shape}
     for pts in (7, 27):
         A = hs.Operator.hpcg(shape, pts)
@@ -539,6 +572,7 @@ def hpcg_timing(nz, dev, tmo):
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1)
             rec[name] = {"ms": round(ms, 3), "iters": info.iters, "paper_iters": paper["hpcg%d" % pts].get(name),
+                         "paper_node_s": paper_s["hpcg%d" % pts].get(name),
                          "us_per_iter": round(1e3 * ms / max(info.iters, 1), 2), "status": info.status,
                          "max_err_vs_ones": torch.max(torch.abs(x - 1.0)).item()}
             del x

@@ -572,9 +572,10 @@ static hs_status residual_norms(const hs_op* A, hs_dtype dt, const void* D, cons
     double sigma;
     Coef<T> cf = op_coef<T>(A, D, ax, ay, az, &sigma);
     int by = rows_per_tile(g);
-    Tiling tl = choose_tiling(g, by, 0, false, 0, CX_ST);
+    constexpr int cx = cx_st<OPK>();   // must match the kernel's columns per lane
+    Tiling tl = choose_tiling(g, by, 0, false, 0, cx);
     int grid = std::min(tl.items(), MAX_BLOCKS * MAX_SCAL / 2);
-    k_residual<T, OPK, NDIM><<<grid, 32 * by, slab_bytes<T>(by, CX_ST), st>>>(g, tl, cf, (T)sigma, (const T*)b,
+    k_residual<T, OPK, NDIM><<<grid, 32 * by, slab_bytes<T>(by, cx), st>>>(g, tl, cf, (T)sigma, (const T*)b,
                                                                         (const T*)x, (T*)r, partials_dev);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "residual launch");
