@@ -137,3 +137,49 @@ def test_cg_rejects_nonsymmetric_operator(lib):
                    ctypes.c_void_p(0x100000), 1 << 30, None, ctypes.byref(res), None)
     assert st == _lib.HS_ERR_INVALID and b"symmetric" in lib.hs_last_error()
     lib.hs_op_destroy(op)
+
+
+def test_hpcg_operator_validation_and_workspace(lib):
+    g2, g3 = ctypes.c_void_p(), ctypes.c_void_p()
+    lib.hs_grid_create(2, (ctypes.c_int64 * 3)(8, 6, 1), ctypes.byref(g2))
+    lib.hs_grid_create(3, (ctypes.c_int64 * 3)(8, 6, 5), ctypes.byref(g3))
+    op = ctypes.c_void_p()
+    assert lib.hs_op_hpcg(g3, 5, ctypes.byref(op)) == _lib.HS_ERR_INVALID
+    assert lib.hs_op_hpcg(g2, 27, ctypes.byref(op)) == _lib.HS_ERR_INVALID
+    assert b"3-D" in lib.hs_last_error()
+    op7, op27 = ctypes.c_void_p(), ctypes.c_void_p()
+    assert lib.hs_op_hpcg(g2, 7, ctypes.byref(op7)) == _lib.HS_OK
+    assert lib.hs_op_hpcg(g3, 27, ctypes.byref(op27)) == _lib.HS_OK
+    assert lib.hs_op_size(op27) == 240
+    lib.hs_grid_destroy(g2)
+    lib.hs_grid_destroy(g3)
+    # CG-NB keeps r, w, q in two copies plus p: more than CG, less than BiCGStab
+    sz = {}
+    for s in (_lib.HS_SOLVER_CG, _lib.HS_SOLVER_CG_NB, _lib.HS_SOLVER_BICGSTAB):
+        b = ctypes.c_size_t()
+        assert lib.hs_workspace_size(op27, s, _lib.HS_F64, None, 50, ctypes.byref(b)) == _lib.HS_OK
+        sz[s] = b.value
+    assert sz[_lib.HS_SOLVER_CG] < sz[_lib.HS_SOLVER_CG_NB] < sz[_lib.HS_SOLVER_BICGSTAB]
+    lib.hs_op_destroy(op7)
+    lib.hs_op_destroy(op27)
+
+
+@no_gpu_only
+def test_cg_nb_and_batch_reject_bad_operators(lib):
+    g = ctypes.c_void_p()
+    lib.hs_grid_create(3, (ctypes.c_int64 * 3)(8, 8, 8), ctypes.byref(g))
+    up, box = ctypes.c_void_p(), ctypes.c_void_p()
+    lib.hs_op_convdiff_upwind(g, (ctypes.c_double * 3)(3.0, 1.0, 0.5), ctypes.byref(up))
+    lib.hs_op_hpcg(g, 27, ctypes.byref(box))
+    lib.hs_grid_destroy(g)
+    res = _lib.hs_result()
+    st = lib.hs_cg_nb(up, 0, ctypes.c_void_p(0x1000), ctypes.c_void_p(0x2000), 1e-8, 3, None,
+                      ctypes.c_void_p(0x100000), 1 << 30, None, ctypes.byref(res), None)
+    assert st == _lib.HS_ERR_INVALID and b"symmetric" in lib.hs_last_error()
+    batch = ctypes.c_void_p()
+    ops = (ctypes.c_void_p * 1)(box.value)
+    sol = (ctypes.c_int * 1)(_lib.HS_SOLVER_CG)
+    assert lib.hs_batch_create(1, ops, sol, ctypes.byref(batch)) == _lib.HS_ERR_INVALID
+    assert b"7-point" in lib.hs_last_error()
+    lib.hs_op_destroy(up)
+    lib.hs_op_destroy(box)

@@ -451,6 +451,23 @@ def test_hpcg_exact_solution_ones():
         assert np.max(np.abs(xj - 1.0)) <= 1e-12
 
 
+@pytest.mark.parametrize("shape", [(4, 3, 5), (3, 3, 3)])
+def test_hpcg27_gauss_seidel_dense_triangular(shape):
+    # forward: (D + L) x' = b - U x; backward: (D + U) x' = b - L x
+    M = hpcg27_dense(shape)
+    N = M.shape[0]
+    Lw, Up = np.tril(M), np.triu(M, 1)
+    b = inputs.uniform_pm1(44, 1, N)
+    x0 = inputs.uniform_pm1(45, 1, N)
+    A = oracle.Operator(shape, oracle.HPCG27)
+    x1 = oracle.gs_sweep(A, b, x0)
+    ref = sla.solve_triangular(Lw, b - Up @ x0, lower=True)
+    assert np.linalg.norm(x1 - ref) <= 1e-14 * np.linalg.norm(ref)
+    xb, _, _, _ = oracle.gauss_seidel(A, b, x0, maxit=1, mode=oracle.GS_BACKWARD)
+    refb = sla.solve_triangular(np.triu(M), b - np.tril(M, -1) @ x0, lower=False)
+    assert np.linalg.norm(xb - refb) <= 1e-14 * np.linalg.norm(refb)
+
+
 # --------------------------------------------------------------------------
 # CG-NB (Algorithm 1) and BiCGStab-B1 (Algorithm 2's statement order)
 # --------------------------------------------------------------------------
