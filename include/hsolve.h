@@ -143,8 +143,10 @@ hs_status hs_op_laplacian(const hs_grid *g, hs_op **out);
  * The paper solves it with b = A 1 (exact solution x = 1) from x0 = 0 to an
  * absolute residual of 1e-6.  The coefficients are the reading that fits the
  * paper's printed iteration counts.  The 27-point operator supports SpMV,
- * residual, Jacobi, CG, CG-NB, BiCGStab and mixed precision; lexicographic
- * Gauss-Seidel and the batched solver return HS_ERR_INVALID for it.
+ * residual, Jacobi, CG, CG-NB, BiCGStab, mixed precision and lexicographic
+ * Gauss-Seidel (one grid-wide step per point hyperplane i + 2j + 4k, so a
+ * sweep takes nx + 2 ny + 4 nz steps); the batched solver returns
+ * HS_ERR_INVALID for it.
  * HS_ERR_INVALID: points not 7 or 27, a 27-point operator on a 1-/2-D grid. */
 hs_status hs_op_hpcg(const hs_grid *g, int points, hs_op **out);
 

@@ -541,6 +541,7 @@ static hs_status gs_run_t(const SolveArgs& sa, hs_result* res, double* hist) {
 hs_status run_gauss_seidel(const SolveArgs& sa, hs_result* res, double* hist) {
   const int opk = opkind_of(sa.A);
   const bool d3 = sa.A->ndim >= 3;
+  if (opk == OP_BOX27) return run_gauss_seidel27(sa, res, hist);
 #define HS_GS(TT, OK)                                                        \
   if (opk == OK) return d3 ? gs_run_t<TT, OK, 3>(sa, res, hist) : gs_run_t<TT, OK, 2>(sa, res, hist);
   if (sa.dtype == HS_F64) {

@@ -1,9 +1,11 @@
 """The paper's benchmark system (section 4.1) on the GPU against the FP64 oracle:
 HPCG's 7- and 27-point matrices (diagonal 27, -1 per neighbour), b = A 1,
 x0 = 0, absolute criterion ||r|| < 1e-6.  The 27-point operator runs on the
-box-sum tile engine (separable 3x3x3 sums).
+box-sum tile engine (separable 3x3x3 sums); its lexicographic Gauss-Seidel on
+the point-hyperplane kernel (one grid step per i + 2j + 4k).
 
-Tolerances: SpMV 1e-13 relative; Jacobi iterates after k sweeps 1e-12;
+Tolerances: SpMV 1e-13 relative; Jacobi and GS iterates after k sweeps 1e-12
+(FP32 GS 2e-6);
 Krylov counts within +-2 of the oracle's and the solution within the
 conditioning bound of x = 1 (cond <= 54 for the 27-point system, <= 27/15 for
 the 7-point one)."""
@@ -91,13 +93,56 @@ def test_hpcg7_gauss_seidel_and_unsupported_paths():
     assert info.status == "OK" and abs(info.iters - it_o) <= 1
     assert np.max(np.abs(host(x_g) - 1.0)) <= 1e-5
     _, A27 = ops((20, 10, 10), 27)
-    # 27-point lexicographic GS is not built (its dependencies admit no tile order)
-    with pytest.raises(hs.HsError):
-        hs.gauss_seidel(A27, dev(np.ones(2000)), maxit=2)
     with pytest.raises(hs.HsError):
         hs.Batch([A27], ["cg"])
     with pytest.raises(hs.HsError):
         hs.Operator.hpcg((20, 10), 27)
+
+
+GS27_SHAPES = [(37, 19, 11), (5, 4, 3), (1, 9, 7), (8, 1, 5), (6, 5, 1), (1, 1, 1), (64, 33, 40)]
+
+
+@pytest.mark.parametrize("shape", GS27_SHAPES)
+@pytest.mark.parametrize("mode", ["forward", "backward", "symmetric"])
+def test_hpcg27_gauss_seidel_sweeps(shape, mode):
+    # the 27-point sweep runs one grid step per point hyperplane i + 2j + 4k;
+    # tol = 0 pipelines all sweeps of a direction 8 hyperplanes apart
+    A_o, A_g = ops(shape, 27)
+    b = inputs.uniform_pm1(54, 1, A_o.N)
+    x0 = inputs.uniform_pm1(55, 1, A_o.N)
+    om = {"forward": oracle.GS_FORWARD, "backward": oracle.GS_BACKWARD, "symmetric": oracle.GS_SYMMETRIC}[mode]
+    for k in (1, 3, 11):
+        x_o, _, _, _ = oracle.gauss_seidel(A_o, b, x0, maxit=k, mode=om)
+        x_g, info = hs.gauss_seidel(A_g, dev(b), dev(x0), maxit=k, mode=mode)
+        assert info.iters == k and rel(host(x_g), x_o) <= 1e-12, (k, rel(host(x_g), x_o))
+    xf0 = x0.astype(np.float32)
+    bf = b.astype(np.float32)
+    x_o, _, _, _ = oracle.gauss_seidel(A_o, bf.astype(np.float64), xf0.astype(np.float64), maxit=3, mode=om)
+    x_g, info = hs.gauss_seidel(A_g, dev(bf, torch.float32), dev(xf0, torch.float32), maxit=3, mode=mode)
+    assert rel(host(x_g), x_o) <= 2e-6
+
+
+@pytest.mark.parametrize("mode", ["forward", "symmetric"])
+@pytest.mark.parametrize("check_every", [1, 4])
+def test_hpcg27_gauss_seidel_paper_criterion(mode, check_every):
+    A_o, A_g, b, tol = _paper_system((24, 20, 18), 27)
+    om = oracle.GS_FORWARD if mode == "forward" else oracle.GS_SYMMETRIC
+    x_o, it_o, st_o, h_o = oracle.gauss_seidel(A_o, b, tol=tol, maxit=2000, mode=om, history=True)
+    assert st_o == 0
+    x_g, info = hs.gauss_seidel(A_g, dev(b), tol=tol, maxit=2000, mode=mode, check_every=check_every,
+                                history=True)
+    assert info.status == "OK"
+    if check_every == 1:
+        assert abs(info.iters - it_o) <= 1
+        assert rel(host(x_g), x_o) <= 1e-9
+        # the residual history follows the oracle's
+        n = min(info.iters, it_o)
+        h_g = np.asarray(info.history)[: n + 1]
+        assert np.allclose(h_g[1:], h_o[1: n + 1], rtol=1e-6, atol=0)
+    else:
+        # the first checked multiple of check_every at or after the oracle's count
+        assert info.iters % check_every == 0 and it_o - 1 <= info.iters <= it_o + check_every
+    assert np.linalg.norm(b - A_o.spmv(host(x_g))) <= 1e-6 * (1 + 1e-3)
 
 
 @pytest.mark.parametrize("points", [7, 27])
