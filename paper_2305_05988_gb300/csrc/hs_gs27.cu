@@ -9,16 +9,28 @@
 // sweep runs them in the reverse order.  Unlike the 7-point case there is no
 // tile order (a lower neighbour such as (i+1, j-1, k) can lie in the next
 // tile along x while that tile needs this one's values), so every hyperplane
-// is one grid-wide step and nodes are updated in place in global memory.
+// is one step and nodes are updated in place in global memory.
 //
 // Consecutive sweeps of one direction are pipelined: sweep t runs hyperplane
 // tau - 8t at step tau.  A node's neighbours lie within 7 hyperplanes, so the
 // upper neighbours sweep t+1 reads hold sweep t's values and no two active
 // hyperplanes of a step touch each other's nodes.
 //
+// The steps need no grid-wide barrier.  The z planes are dealt to the blocks
+// round robin (plane k to block k mod G), and a node of plane k reads planes
+// k-1, k and k+1 only, so a block waits before each step until its two ring
+// neighbours (the owners of planes k-1 and k+1) have completed the previous
+// step, and then publishes its own step count.  Waiting on both sides keeps
+// a block from overwriting values a neighbour still has to read (with
+// pipelined sweeps the lower plane's next sweep would otherwise catch up);
+// a block with no node on the step's hyperplanes publishes without waiting.
+// Batches and directions follow one another under the same rule, so a
+// backward sweep starts on a plane as soon as its neighbours have finished
+// the forward one.
+//
 // Hyperplane h holds, for each k with a non-empty range, the lines j with
-// 0 <= h - 4k - 2j < nx; threads take (k, slot) pairs with M = nx/2 + 1
-// slots per k (the longest j range).
+// 0 <= h - 4k - 2j < nx; a block's threads take (sweep, plane, slot) triples
+// with M = nx/2 + 1 slots per plane (the longest j range).
 #include <algorithm>
 #include <cmath>
 
@@ -36,6 +48,7 @@ struct Gs27Args {
   T* bD;            // b / 27
   T* x;
   Common cm;
+  unsigned long long* prog;    // per block: steps completed (only grows)
   int H;            // hyperplanes per sweep
   int M;            // slots per k
   int maxit;
@@ -45,6 +58,39 @@ struct Gs27Args {
 };
 
 constexpr int GS27_LAG = 8;
+constexpr int GS27_THREADS = 256;
+// progress words reserved in the workspace (the grid is at most one block per SM)
+constexpr int GS27_MAX_BLOCKS = 1024;
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Thread 0 of a block: wait until both ring neighbours have completed
+// `target` steps.  Bounded by the solve's timeout (status DS_TIMEOUT); ends
+// early when another block has flagged an error.
+__device__ __forceinline__ bool wait_neighbours(const unsigned long long* lo, const unsigned long long* hi,
+                                unsigned long long target, Ctrl* ctrl) {
+  unsigned spins = 0;
+  unsigned long long t0 = 0;
+  while (ld_acquire_u64(lo) < target || ld_acquire_u64(hi) < target) {
+    if ((++spins & 1023) == 0) {
+      if (t0 == 0) t0 = global_ns();
+      if (ld_acquire_int(&ctrl->status) < 0) return false;
+      if (global_ns() - t0 > ctrl->timeout_ns) {
+        atomicCAS(&ctrl->status, 0, (int)DS_TIMEOUT);
+        return false;
+      }
+    }
+  }
+  return true;
+}
 
 // k range of hyperplane h (empty when klo > khi).
 __device__ __forceinline__ void gs27_krange(const Geom& g, int h, int& klo, int& khi) {
@@ -53,59 +99,104 @@ __device__ __forceinline__ void gs27_krange(const Geom& g, int h, int& klo, int&
   klo = r <= 0 ? 0 : (r + 3) / 4;
 }
 
-// x_i <- (b_i + sum of the 26 neighbours) / 27, in place.
+// x_i <- (b_i + sum of the 26 neighbours) / 27, in place.  All 26 loads are
+// issued before the first addition (nodes outside the grid read as zero).
 template <typename T>
 __device__ __forceinline__ void gs27_node(const Gs27Args<T>& a, int i, int j, int k) {
   const Geom& g = a.g;
   const long long idx = (long long)k * g.plane + (long long)j * g.nx + i;
-  T box = T(0);
+  const bool okx[3] = {i > 0, true, i + 1 < g.nx};
+  const bool oky[3] = {j > 0, true, j + 1 < g.ny};
+  const bool okz[3] = {k > 0, true, k + 1 < g.nz};
+  T v[27];
 #pragma unroll
-  for (int dz = -1; dz <= 1; dz++)
+  for (int dz = 0; dz < 3; dz++)
 #pragma unroll
-    for (int dy = -1; dy <= 1; dy++)
+    for (int dy = 0; dy < 3; dy++)
 #pragma unroll
-      for (int dx = -1; dx <= 1; dx++) {
-        const int ii = i + dx, jj = j + dy, kk = k + dz;
-        if (ii >= 0 && ii < g.nx && jj >= 0 && jj < g.ny && kk >= 0 && kk < g.nz)
-          box += __ldcg(a.x + idx + (long long)dz * g.plane + (long long)dy * g.nx + dx);
+      for (int dx = 0; dx < 3; dx++) {
+        const long long off = (long long)(dz - 1) * g.plane + (long long)(dy - 1) * g.nx + (dx - 1);
+        const bool center = dz == 1 && dy == 1 && dx == 1;   // not needed
+        v[dz * 9 + dy * 3 + dx] = (!center && okz[dz] && oky[dy] && okx[dx]) ? __ldcg(a.x + idx + off) : T(0);
       }
-  const T c = __ldcg(a.x + idx);
-  a.x[idx] = fma(a.g27, box - c, __ldcg(a.bD + idx));
-}
-
-// Nodes of hyperplane h handed out over the whole grid.
-template <typename T>
-__device__ __forceinline__ void gs27_plane(const Gs27Args<T>& a, int h) {
-  const Geom& g = a.g;
-  int klo, khi;
-  gs27_krange(g, h, klo, khi);
-  if (klo > khi) return;
-  const long long slots = (long long)(khi - klo + 1) * a.M;
-  for (long long e = gtid(); e < slots; e += gstride()) {
-    const int k = klo + (int)(e / a.M);
-    const int q = (int)(e % a.M);
-    const int rem = h - 4 * k;                       // = i + 2j
-    const int jlo = rem - (g.nx - 1) <= 0 ? 0 : (rem - (g.nx - 1) + 1) / 2;
-    const int j = jlo + q;
-    if (j >= g.ny || 2 * j > rem) continue;
-    gs27_node(a, rem - 2 * j, j, k);
+  const T bD = __ldcg(a.bD + idx);
+  // ring of each plane (the 8 nodes around the column), then the columns
+  T ring[3];
+#pragma unroll
+  for (int dz = 0; dz < 3; dz++) {
+    const T* q = v + dz * 9;
+    ring[dz] = ((q[0] + q[1]) + (q[2] + q[3])) + ((q[5] + q[6]) + (q[7] + q[8]));
   }
+  const T nbr = ((ring[0] + ring[2]) + ring[1]) + (v[4] + v[22]);
+  a.x[idx] = fma(a.g27, nbr, bD);
 }
 
-// nsw pipelined sweeps of one direction.
+// First plane at or above klo owned by block b of G (plane k belongs to block
+// k mod G) and the number of owned planes in [klo, khi].
+__device__ __forceinline__ int gs27_owned(int klo, int khi, int b, int G, int& k0) {
+  k0 = klo + ((b - klo % G) % G + G) % G;
+  return k0 <= khi ? (khi - k0) / G + 1 : 0;
+}
+
+// nsw pipelined sweeps of one direction.  `base` counts the steps completed
+// before this batch (the same in every block) and advances by the batch's
+// step count.
 template <typename T>
-__device__ bool gs27_batch(const Gs27Args<T>& a, double* sh, int nsw, bool backward) {
-  const int H = a.H;
+__device__ __forceinline__ bool gs27_batch(const Gs27Args<T>& a, unsigned long long& base, int nsw, bool backward) {
+  __shared__ int s_ok;
+  const Geom& g = a.g;
+  const int H = a.H, M = a.M;
+  const int G = gridDim.x, b = blockIdx.x;
+  const unsigned long long* plo = a.prog + (b + G - 1) % G;
+  const unsigned long long* phi = a.prog + (b + 1) % G;
   const int nsteps = H + GS27_LAG * (nsw - 1);
   for (int tau = 0; tau < nsteps; tau++) {
     const int t_hi = min(nsw - 1, tau / GS27_LAG);
+    // owned work of this step: sweeps t_hi .. t_lo are active
+    int total = 0;
     for (int t = t_hi; t >= 0; t--) {
-      const int s = tau - GS27_LAG * t;
-      if (s >= H) break;   // older sweeps have finished
-      gs27_plane(a, backward ? H - 1 - s : s);
+      const int sidx = tau - GS27_LAG * t;
+      if (sidx >= H) break;
+      const int h = backward ? H - 1 - sidx : sidx;
+      int klo, khi, k0;
+      gs27_krange(g, h, klo, khi);
+      if (klo <= khi) total += gs27_owned(klo, khi, b, G, k0);
     }
-    if (!grid_sync(a.cm.ctrl, a.cm.partials, sh)) return false;
+    if (total > 0) {
+      if (threadIdx.x == 0) s_ok = wait_neighbours(plo, phi, base + tau, a.cm.ctrl);
+      __syncthreads();
+      if (!s_ok) return false;
+      int off = 0;   // first slot index of the current (sweep, plane) group
+      for (int t = t_hi; t >= 0; t--) {
+        const int sidx = tau - GS27_LAG * t;
+        if (sidx >= H) break;
+        const int h = backward ? H - 1 - sidx : sidx;
+        int klo, khi, k0;
+        gs27_krange(g, h, klo, khi);
+        if (klo > khi) continue;
+        const int cnt = gs27_owned(klo, khi, b, G, k0);
+        const int nslot = cnt * M;
+        // this thread's slots are those congruent to threadIdx.x mod blockDim.x
+        int e = off + ((int)threadIdx.x - off % (int)blockDim.x + (int)blockDim.x) % (int)blockDim.x;
+        for (; e < off + nslot; e += blockDim.x) {
+          const int loc = e - off;
+          const int k = k0 + (loc / M) * G;
+          const int rem = h - 4 * k;                       // = i + 2j
+          const int jlo = rem - (g.nx - 1) <= 0 ? 0 : (rem - (g.nx - 1) + 1) / 2;
+          const int j = jlo + loc % M;
+          if (j >= g.ny || 2 * j > rem) continue;
+          gs27_node(a, rem - 2 * j, j, k);
+        }
+        off += nslot;
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      __threadfence();
+      st_release_u64(a.prog + b, base + tau + 1);
+    }
   }
+  base += nsteps;
   return true;
 }
 
@@ -113,6 +204,8 @@ __device__ bool gs27_batch(const Gs27Args<T>& a, double* sh, int nsw, bool backw
 template <typename T>
 __device__ bool gs27_residual(const Gs27Args<T>& a, double* sh, double bb, double* rel) {
   const Geom& g = a.g;
+  // blocks finish a batch at different times: all sweeps must be complete
+  if (!grid_sync(a.cm.ctrl, a.cm.partials, sh)) return false;
   double acc[1] = {0.0};
   for (long long idx = gtid(); idx < g.N; idx += gstride()) {
     const int i = (int)(idx % g.nx);
@@ -138,9 +231,11 @@ __device__ bool gs27_residual(const Gs27Args<T>& a, double* sh, double bb, doubl
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_gs27(Gs27Args<T> a) {
+__global__ void __launch_bounds__(GS27_THREADS) k_gs27(Gs27Args<T> a) {
   __shared__ double sh[32 * MAX_SCAL];
   const long long N = a.g.N;
+  unsigned long long base = 0;
+  if (threadIdx.x == 0) a.prog[blockIdx.x] = 0;   // ordered by the reduction below
   double acc[1] = {0.0};
   for (long long i = gtid(); i < N; i += gstride()) {
     const T bv = a.b[i];
@@ -172,17 +267,17 @@ __global__ void __launch_bounds__(256) k_gs27(Gs27Args<T> a) {
       const int nb = (a.tol > 0.0) ? min(a.check_every, a.maxit - done) : a.maxit - done;
       if (a.mode == HS_GS_SYMMETRIC) {
         for (int q = 0; q < nb; q++) {
-          if (!gs27_batch(a, sh, 1, false)) return;
-          if (!gs27_batch(a, sh, 1, true)) return;
+          if (!gs27_batch(a, base, 1, false)) return;
+          if (!gs27_batch(a, base, 1, true)) return;
         }
       } else {
-        if (!gs27_batch(a, sh, nb, a.mode == HS_GS_BACKWARD)) return;
+        if (!gs27_batch(a, base, nb, a.mode == HS_GS_BACKWARD)) return;
       }
       done += nb;
       if (a.tol > 0.0) {
         if (!gs27_residual(a, sh, bb[0], &rel)) return;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
-          for (int q = done - nb + 1; q < done; q++) a.cm.hist[q] = nan("");   // not evaluated
+          for (int q = done - nb + 1; q < done; q++) a.cm.hist[q] = __longlong_as_double(0x7ff8000000000000LL);   // not evaluated (quiet NaN)
           a.cm.hist[done] = rel;
         }
         if (!isfinite(rel)) {
@@ -212,6 +307,7 @@ static hs_status gs27_t(const SolveArgs& sa, hs_result* res, double* hist) {
   Common cm = carve_common(c, sa.maxit);
   Gs27Args<T> a = {};
   a.bD = c.take<T>(g.N);
+  a.prog = c.take<unsigned long long>(GS27_MAX_BLOCKS);
   if (!c.ok) {
     set_error("workspace too small for Gauss-Seidel");
     return HS_ERR_WORKSPACE;
@@ -231,20 +327,24 @@ static hs_status gs27_t(const SolveArgs& sa, hs_result* res, double* hist) {
   a.mode = sa.o.gs_mode;
   a.check_every = sa.o.check_every;
   a.tol = sa.tol;
+  // one block per SM: a hyperplane holds a few thousand nodes (about 65 per
+  // plane), so more blocks would only idle
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gs27<T>, 256, 0);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gs27<T>, GS27_THREADS, 0);
   if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
   if (per_sm < 1) {
     set_error("Gauss-Seidel kernel cannot be resident");
     return HS_ERR_CUDA;
   }
-  int grid = std::min(per_sm * sm_count(), MAX_BLOCKS);
+  int grid = std::min(sm_count(), GS27_MAX_BLOCKS);
   if (sa.o.max_blocks > 0) grid = std::min(grid, sa.o.max_blocks);
   void* args[] = {&a};
-  s = launch_coop((const void*)k_gs27<T>, grid, 256, args, 0, sa.stream);
+  s = launch_coop((const void*)k_gs27<T>, grid, GS27_THREADS, args, 0, sa.stream);
   if (s != HS_OK) return s;
   return finish_solve_pub(sa, cm, nullptr, nullptr, nullptr, nullptr, a.bD, res, hist, sa.tol > 0.0);
 }
+
+size_t gs27_progress_bytes() { return (GS27_MAX_BLOCKS * sizeof(unsigned long long) + 255) & ~(size_t)255; }
 
 hs_status run_gauss_seidel27(const SolveArgs& sa, hs_result* res, double* hist) {
   return sa.dtype == HS_F64 ? gs27_t<double>(sa, res, hist) : gs27_t<float>(sa, res, hist);

@@ -122,6 +122,20 @@ def test_hpcg27_gauss_seidel_sweeps(shape, mode):
     assert rel(host(x_g), x_o) <= 2e-6
 
 
+@pytest.mark.parametrize("blocks", [1, 2, 3, 7])
+def test_hpcg27_gauss_seidel_few_blocks(blocks):
+    # planes are dealt to the blocks round robin; with few blocks each owns
+    # several planes of a hyperplane and the ring closes on itself
+    shape = (9, 6, 23)
+    A_o, A_g = ops(shape, 27)
+    b = inputs.uniform_pm1(56, 1, A_o.N)
+    x0 = inputs.uniform_pm1(57, 1, A_o.N)
+    for mode, om in (("forward", oracle.GS_FORWARD), ("symmetric", oracle.GS_SYMMETRIC)):
+        x_o, _, _, _ = oracle.gauss_seidel(A_o, b, x0, maxit=5, mode=om)
+        x_g, info = hs.gauss_seidel(A_g, dev(b), dev(x0), maxit=5, mode=mode, max_blocks=blocks)
+        assert info.iters == 5 and rel(host(x_g), x_o) <= 1e-12, (mode, rel(host(x_g), x_o))
+
+
 @pytest.mark.parametrize("mode", ["forward", "symmetric"])
 @pytest.mark.parametrize("check_every", [1, 4])
 def test_hpcg27_gauss_seidel_paper_criterion(mode, check_every):
