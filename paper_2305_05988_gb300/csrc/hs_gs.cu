@@ -8,12 +8,14 @@
 // hyperplane order at two levels, which reproduces the sequential sweep up
 // to the rounding order inside a single update (no recolouring):
 //
-//   * tiles of TX x TY x TZ nodes, tile hyperplane S = I + J + K: tiles on
-//     one tile plane are processed in parallel, one grid step per plane;
-//     sweep t runs tile plane S = tau - 2t at step tau, so consecutive
-//     sweeps of the same direction overlap (sweep t+1 trails sweep t by two
-//     tile planes, which leaves every tile's upper neighbours holding the
-//     previous sweep's values and its lower neighbours the current sweep's);
+//   * tiles of TX x TY x TZ nodes, tile hyperplane S = I + J + K: a tile
+//     needs the current sweep's values of its three lower face neighbours
+//     and the previous sweep's of its three upper ones.  The tiles are
+//     scheduled as a dataflow graph, not in grid-wide steps: blocks take
+//     (sweep, tile) items from a counter in the order of the step schedule
+//     (sweep t's tile plane S at step 2t + S, so consecutive sweeps of the
+//     same direction overlap) and wait on per-tile sweep counts of the
+//     face neighbours before sweeping a tile;
 //   * inside a tile (staged in shared memory with a one-node halo), one
 //     thread per x-line; the line (j, k) processes node i at local step
 //     i + j + k.  Lines are dealt to threads in order of j + k so that the
@@ -21,7 +23,8 @@
 //     scarce FP64 pipe is not spent on idle lanes.
 //
 // A backward sweep mirrors every direction.  The symmetric method (forward
-// then backward per iteration) runs one sweep per pipeline batch.
+// then backward per iteration) alternates directions inside one batch; a
+// sweep then starts only after the previous one has passed every tile plane.
 #include <math.h>
 
 #include <algorithm>
@@ -31,13 +34,19 @@
 
 namespace hs {
 
-template <int NDIM>
+template <int NDIM, int W>
 struct GsTile;
-// Tile shapes (one thread per x-line: TY * TZ threads per block).  3-D
-// default 32 x 8 x 8 (two warps; measured on GB300 at 256^3, 200 sweeps:
-// 418 us/sweep against 456 for 32 x 16 x 8, 522 for one-warp 32 x 4 x 8 and
-// 32 x 8 x 4, 458-460 for 32 x 4 x 16 and 32 x 16 x 4).  Override at build
-// time for measurements (-DHS_GS_TY=.. -DHS_GS_TZ=..).
+// Tile shapes (one thread per x-line: TY * TZ threads per block), 3-D:
+//   W = 0, 32 x 8 x 8 (two warps), for batches of four or more sweeps of one
+//     direction, which pipeline: many small tiles keep more blocks resident
+//     per SM (256^3, 200 sweeps: 325 us/sweep against 336 for 32 x 16 x 16,
+//     341 for 32 x 16 x 8 and 32 x 8 x 16, 356 for 32 x 4 x 16);
+//   W = 1, 32 x 16 x 16 (eight warps), for single sweeps and the symmetric
+//     method, whose time is the number of tile planes times the time of a
+//     tile (256^3 symmetric, residual every iteration: 3.48 ms/iteration
+//     against 4.68 for 32 x 8 x 8).
+// The W = 0 shape can be overridden at build time for measurements
+// (-DHS_GS_TY=.. -DHS_GS_TZ=..).  2-D grids use 32 x 128 lines for both.
 #ifndef HS_GS_TY
 #define HS_GS_TY 8
 #endif
@@ -45,15 +54,19 @@ struct GsTile;
 #define HS_GS_TZ 8
 #endif
 template <>
-struct GsTile<3> {
+struct GsTile<3, 0> {
   static constexpr int TX = 32, TY = HS_GS_TY, TZ = HS_GS_TZ;
 };
 template <>
-struct GsTile<2> {
+struct GsTile<3, 1> {
+  static constexpr int TX = 32, TY = 16, TZ = 16;
+};
+template <int W>
+struct GsTile<2, W> {
   static constexpr int TX = 32, TY = 128, TZ = 1;
 };
-template <int NDIM>
-constexpr int gs_threads() { return GsTile<NDIM>::TY * GsTile<NDIM>::TZ; }
+template <int NDIM, int W>
+constexpr int gs_threads() { return GsTile<NDIM, W>::TY * GsTile<NDIM, W>::TZ; }
 
 template <typename T>
 struct GsArgs {
@@ -67,6 +80,8 @@ struct GsArgs {
   Common cm;
   const int* plane_off;   // P + 1 offsets into plane_tiles
   const int* plane_tiles; // tile ids grouped by tile plane I + J + K
+  unsigned* tile_done;    // per tile: sweeps completed (only grows)
+  unsigned long long* claim;   // work counter of the dataflow schedule (only grows)
   int ntx, nty, ntz, P;
   int maxit;
   int mode;               // HS_GS_FORWARD / BACKWARD / SYMMETRIC
@@ -99,6 +114,8 @@ __device__ __forceinline__ void line_of_thread(int t, int TY, int TZ, int& jl, i
 template <typename T, int OPK, int NDIM>
 __device__ bool gs_residual(const GsArgs<T>& a, T* /*sm*/, double* sh, double bb, double* rel) {
   const Geom& g = a.g;
+  // blocks leave a batch at different times
+  if (!grid_sync(a.cm.ctrl, a.cm.partials, sh)) return false;
   const T* bsrc = (OPK == OP_VARK) ? a.b : a.bD;
   const T* x = a.x;
   double acc[1] = {0.0};
@@ -172,9 +189,9 @@ __device__ __forceinline__ T gs_new(const Coef<T>& cf, const OpRaw<T, OPK>& o, T
 }
 
 // One tile of one sweep: load tile + halo, wavefront in shared memory, store.
-template <typename T, int OPK, int NDIM>
+template <typename T, int OPK, int NDIM, int W>
 __device__ __forceinline__ void gs_tile(const GsArgs<T>& a, T* sm, int tile, bool backward) {
-  constexpr int TX = GsTile<NDIM>::TX, TY = GsTile<NDIM>::TY, TZ = GsTile<NDIM>::TZ;
+  constexpr int TX = GsTile<NDIM, W>::TX, TY = GsTile<NDIM, W>::TY, TZ = GsTile<NDIM, W>::TZ;
   constexpr int SX = TX + 2, SY = TY + 2, SZ = (NDIM == 3) ? TZ + 2 : 1;
   constexpr int ZOFF = (NDIM == 3) ? 1 : 0;
   const Geom& g = a.g;
@@ -245,14 +262,27 @@ __device__ __forceinline__ void gs_tile(const GsArgs<T>& a, T* sm, int tile, boo
     yold = gs_old<T, OPK, NDIM>(a.cf, ocur, bv, sm[c - nxo], sm[c - nyo], NDIM == 3 ? sm[c - nzo] : T(0), backward);
     wreg = sm[c + nxo];
   }
+  // right-hand sides of the line's next four nodes in flight (a substep is
+  // far shorter than a global load, so a one-substep prefetch would stall
+  // every substep on it)
+  T bq[4];
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    const int ilq = HS_IL_AT(q + 1);
+    bq[q] = ilq >= 0 ? __ldcg(bsrc + gbase + ilq) : T(0);
+  }
   for (int s = 0; s < nsteps; s++) {
     const int il_n = HS_IL_AT(s + 1);
-    T bnext = T(0);
-    OpRaw<T, OPK> onext{};
-    if (il_n >= 0) {
-      bnext = __ldcg(bsrc + gbase + il_n);
-      onext = op_fetch<T, OPK, NDIM>(a.cf, g, gbase + il_n, i0 + il_n, gj, gk);
+    const T bnext = bq[0];
+    {
+      const int il_f = HS_IL_AT(s + 5);
+      bq[0] = bq[1];
+      bq[1] = bq[2];
+      bq[2] = bq[3];
+      bq[3] = il_f >= 0 ? __ldcg(bsrc + gbase + il_f) : T(0);
     }
+    OpRaw<T, OPK> onext{};
+    if (il_n >= 0) onext = op_fetch<T, OPK, NDIM>(a.cf, g, gbase + il_n, i0 + il_n, gj, gk);
     if (il >= 0) {
       const int c = base + il;
       const T y = gs_new<T, OPK, NDIM>(a.cf, ocur, yold, wreg, sm[c + nyo], NDIM == 3 ? sm[c + nzo] : T(0), backward);
@@ -283,43 +313,140 @@ __device__ __forceinline__ void gs_tile(const GsArgs<T>& a, T* sm, int tile, boo
   __syncthreads();
 }
 
-// A batch of `nsw` sweeps of one direction, pipelined over tile planes.
-template <typename T, int OPK, int NDIM>
-__device__ bool gs_batch(const GsArgs<T>& a, T* sm, double* sh, int nsw, bool backward) {
+// Dataflow form of a batch: nsw sweeps (directions by `mode`; symmetric
+// alternates forward and backward) with no grid-wide step.  Work items are
+// (sweep, tile) pairs, taken from a counter in the order of the grid-step
+// schedule: sweep t's tile plane S sits at step off(t) + S, with off(t) =
+// 2t when all sweeps run one way (sweep t+1 trails sweep t by two tile
+// planes) and t P when they alternate.  Before a tile is swept, warp 0 waits
+// until its new-side face neighbours (lower ones for a forward sweep) have
+// completed this sweep, and the tile itself and its old-side neighbours the
+// previous one; after the tile is stored its sweep count is published.
+// Every wait is on an item that comes earlier in the order, so the earliest
+// unfinished item can always proceed.  `gsweep` (sweeps completed) and
+// `cbase` (claims made) are the same in every block; each block ends a batch
+// with exactly one claim past its end, so a batch takes nitems + G claims.
+// Batches must be separated by a grid barrier.
+template <typename T, int OPK, int NDIM, int W>
+__device__ bool gs_batch_df(const GsArgs<T>& a, T* sm, int nsw, int mode, unsigned& gsweep,
+                            unsigned long long& cbase) {
+  __shared__ long long s_item;
+  __shared__ int s_tile, s_bw, s_ok;
+  const int nt = a.ntx * a.nty * a.ntz;
   const int P = a.P;
-  const int nsteps = P + 2 * (nsw - 1);
-  for (int tau = 0; tau < nsteps; tau++) {
-    // active sweeps t with 0 <= tau - 2t < P
-    int t_lo = max(0, (tau - P + 2) / 2);
-    if (tau - 2 * t_lo >= P) t_lo++;
-    int t_hi = min(nsw - 1, tau / 2);
-    int total = 0;
-    for (int t = t_lo; t <= t_hi; t++) {
-      int S = tau - 2 * t;
-      int Se = backward ? P - 1 - S : S;
-      total += a.plane_off[Se + 1] - a.plane_off[Se];
-    }
-    for (int item = blockIdx.x; item < total; item += gridDim.x) {
-      int rem = item, tile = -1;
-      for (int t = t_lo; t <= t_hi; t++) {
-        int S = tau - 2 * t;
-        int Se = backward ? P - 1 - S : S;
-        int cnt = a.plane_off[Se + 1] - a.plane_off[Se];
-        if (rem < cnt) {
-          tile = a.plane_tiles[a.plane_off[Se] + rem];
-          break;
+  const int L = mode == HS_GS_SYMMETRIC ? P : 2;
+  const long long nitems = (long long)nsw * nt;
+  // lane 0 of warp 0: position of the schedule (its claims only grow)
+  int tau_c = 0;
+  long long cum_c = 0;   // items before step tau_c
+  while (true) {
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      long long u = 0;
+      int tile = 0, t = 0, bw = 0;
+      if (lane == 0) {
+        u = (long long)(atomicAdd(a.claim, 1ull) - cbase);
+        if (u < nitems) {
+          while (true) {
+            const int t_lo = tau_c < P ? 0 : (tau_c - P) / L + 1;
+            const int t_hi = min(nsw - 1, tau_c / L);
+            long long rem = u - cum_c;
+            int found = -1;
+            for (int tt = t_lo; tt <= t_hi; tt++) {
+              const int S = tau_c - L * tt;
+              const bool b2 = mode == HS_GS_BACKWARD || (mode == HS_GS_SYMMETRIC && (tt & 1));
+              const int Se = b2 ? P - 1 - S : S;
+              const int cnt = a.plane_off[Se + 1] - a.plane_off[Se];
+              if (rem < cnt) {
+                found = tt;
+                tile = a.plane_tiles[a.plane_off[Se] + (int)rem];
+                bw = b2;
+                break;
+              }
+              rem -= cnt;
+            }
+            if (found >= 0) {
+              t = found;
+              break;
+            }
+            cum_c = u - rem;   // all items of step tau_c lie before u
+            tau_c++;
+          }
         }
-        rem -= cnt;
       }
-      if (tile >= 0) gs_tile<T, OPK, NDIM>(a, sm, tile, backward);
+      u = __shfl_sync(0xffffffffu, u, 0);
+      tile = __shfl_sync(0xffffffffu, tile, 0);
+      t = __shfl_sync(0xffffffffu, t, 0);
+      bw = __shfl_sync(0xffffffffu, bw, 0);
+      int ok = 1;
+      if (u < nitems) {
+        const unsigned gs = gsweep + (unsigned)t;
+        const int I = tile % a.ntx, J = (tile / a.ntx) % a.nty, K = tile / (a.ntx * a.nty);
+        // lane 0: the tile itself; lanes 1..6: -x, +x, -y, +y, -z, +z
+        const unsigned* f = nullptr;
+        unsigned target = 0;
+        if (lane == 0) {
+          f = a.tile_done + tile;
+          target = gs;
+        } else if (lane <= 6) {
+          const int d = (lane - 1) >> 1, up = (lane - 1) & 1;
+          const int step = up ? 1 : -1;
+          const int c = d == 0 ? I + step : (d == 1 ? J + step : K + step);
+          const int lim = d == 0 ? a.ntx : (d == 1 ? a.nty : a.ntz);
+          if (c >= 0 && c < lim) {
+            f = a.tile_done + tile + step * (d == 0 ? 1 : (d == 1 ? a.ntx : a.ntx * a.nty));
+            const bool newside = bw ? up : !up;
+            target = newside ? gs + 1 : gs;
+          }
+        }
+        unsigned spins = 0;
+        unsigned long long t0 = 0;
+        while (true) {
+          const bool sat = f == nullptr || ld_acquire(f) >= target;
+          if (__all_sync(0xffffffffu, sat)) break;
+          int stop = 0;
+          if (lane == 0 && (++spins & 255) == 0) {
+            if (t0 == 0) t0 = global_ns();
+            if (ld_acquire_int(&a.cm.ctrl->status) < 0) {
+              stop = 1;
+            } else if (global_ns() - t0 > a.cm.ctrl->timeout_ns) {
+              atomicCAS(&a.cm.ctrl->status, 0, (int)DS_TIMEOUT);
+              stop = 1;
+            }
+          }
+          if (__shfl_sync(0xffffffffu, stop, 0)) {
+            ok = 0;
+            break;
+          }
+        }
+      }
+      if (lane == 0) {
+        s_item = u;
+        s_tile = tile;
+        s_bw = bw;
+        s_ok = ok;
+        if (u < nitems) s_item = (long long)t;   // the sweep, for the publish below
+        else s_item = -1;
+      }
     }
-    if (!grid_sync(a.cm.ctrl, a.cm.partials, sh)) return false;
+    __syncthreads();
+    const long long t = s_item;
+    if (!s_ok) return false;
+    if (t < 0) break;
+    const int tile = s_tile;
+    gs_tile<T, OPK, NDIM, W>(a, sm, tile, s_bw != 0);   // ends with a block barrier
+    if (threadIdx.x == 0) {
+      __threadfence();
+      st_release(a.tile_done + tile, gsweep + (unsigned)t + 1u);
+    }
   }
+  gsweep += (unsigned)nsw;
+  cbase += (unsigned long long)nitems + gridDim.x;
   return true;
 }
 
-template <typename T, int OPK, int NDIM>
-__global__ void __launch_bounds__(gs_threads<NDIM>()) k_gs(GsArgs<T> a) {
+template <typename T, int OPK, int NDIM, int W>
+__global__ void __launch_bounds__(gs_threads<NDIM, W>()) k_gs(GsArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double sh[32 * MAX_SCAL];
   T* sm = reinterpret_cast<T*>(smraw);
@@ -331,6 +458,12 @@ __global__ void __launch_bounds__(gs_threads<NDIM>()) k_gs(GsArgs<T> a) {
     if (OPK != OP_VARK) a.bD[i] = bv * a.invd;
     acc[0] += widen(bv) * widen(bv);
   }
+  // schedule state, ordered before its first use by the reduction below
+  const int ntiles = a.ntx * a.nty * a.ntz;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x) a.tile_done[t] = 0u;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *a.claim = 0ull;
+  unsigned gsweep = 0;
+  unsigned long long cbase = 0;
   block_sum<1>(acc, sh);
   double bb[1];
   if (!grid_reduce<1>(a.cm.ctrl, a.cm.partials, acc, bb, sh)) return;
@@ -356,14 +489,8 @@ __global__ void __launch_bounds__(gs_threads<NDIM>()) k_gs(GsArgs<T> a) {
   if (!(a.tol > 0.0) || status == DS_MAXIT) {
     while (done < a.maxit) {
       int nb = (a.tol > 0.0) ? min(a.check_every, a.maxit - done) : a.maxit - done;
-      if (a.mode == HS_GS_SYMMETRIC) {
-        for (int q = 0; q < nb; q++) {
-          if (!gs_batch<T, OPK, NDIM>(a, sm, sh, 1, false)) return;
-          if (!gs_batch<T, OPK, NDIM>(a, sm, sh, 1, true)) return;
-        }
-      } else {
-        if (!gs_batch<T, OPK, NDIM>(a, sm, sh, nb, a.mode == HS_GS_BACKWARD)) return;
-      }
+      if (!gs_batch_df<T, OPK, NDIM, W>(a, sm, a.mode == HS_GS_SYMMETRIC ? 2 * nb : nb, a.mode, gsweep, cbase))
+        return;
       done += nb;
       if (a.tol > 0.0) {
         if (!gs_residual<T, OPK, NDIM>(a, sm, sh, bb[0], &rel)) return;
@@ -394,17 +521,21 @@ __global__ void __launch_bounds__(gs_threads<NDIM>()) k_gs(GsArgs<T> a) {
 // Host side
 // ---------------------------------------------------------------------------
 
-template <int NDIM>
+template <int NDIM, int W>
 static void tile_counts(const hs_op* A, int* ntx, int* nty, int* ntz) {
-  *ntx = (int)((A->n[0] + GsTile<NDIM>::TX - 1) / GsTile<NDIM>::TX);
-  *nty = (int)((A->n[1] + GsTile<NDIM>::TY - 1) / GsTile<NDIM>::TY);
-  *ntz = (int)((A->n[2] + GsTile<NDIM>::TZ - 1) / GsTile<NDIM>::TZ);
+  *ntx = (int)((A->n[0] + GsTile<NDIM, W>::TX - 1) / GsTile<NDIM, W>::TX);
+  *nty = (int)((A->n[1] + GsTile<NDIM, W>::TY - 1) / GsTile<NDIM, W>::TY);
+  *ntz = (int)((A->n[2] + GsTile<NDIM, W>::TZ - 1) / GsTile<NDIM, W>::TZ);
 }
 
+// Tile count and tile planes of the larger table (the W = 0 shape has the
+// smaller tiles in every direction).
 static void gs_counts(const hs_op* A, int* ntiles, int* P) {
+  static_assert(GsTile<3, 0>::TY <= GsTile<3, 1>::TY && GsTile<3, 0>::TZ <= GsTile<3, 1>::TZ,
+                "workspace sizing assumes the W = 0 tiles are the smaller ones");
   int a, b, c;
-  if (A->ndim >= 3) tile_counts<3>(A, &a, &b, &c);
-  else tile_counts<2>(A, &a, &b, &c);
+  if (A->ndim >= 3) tile_counts<3, 0>(A, &a, &b, &c);
+  else tile_counts<2, 0>(A, &a, &b, &c);
   *ntiles = a * b * c;
   *P = a + b + c - 2;
 }
@@ -417,7 +548,9 @@ size_t gs_ws_vectors(const hs_op* A, hs_dtype dt) {
   int nt, P;
   gs_counts(A, &nt, &P);
   size_t ints = (size_t)nt + P + 1;
-  return ((N * es + 255) & ~(size_t)255) + ((ints * 4 + 255) & ~(size_t)255);
+  // b / a_ii, the tile-plane tables, per-tile sweep counts, the claim counter
+  return ((N * es + 255) & ~(size_t)255) + ((ints * 4 + 255) & ~(size_t)255) + (((size_t)nt * 4 + 255) & ~(size_t)255) +
+         256;
 }
 
 template <typename T>
@@ -435,9 +568,9 @@ static Coef<T> gs_jacobi_coef(const hs_op* A, T* invd, double* d2) {
   return cf;
 }
 
-template <typename T, int OPK, int NDIM>
+template <typename T, int OPK, int NDIM, int W>
 static hs_status gs_run_t(const SolveArgs& sa, hs_result* res, double* hist) {
-  constexpr int TX = GsTile<NDIM>::TX, TY = GsTile<NDIM>::TY, TZ = GsTile<NDIM>::TZ;
+  constexpr int TX = GsTile<NDIM, W>::TX, TY = GsTile<NDIM, W>::TY, TZ = GsTile<NDIM, W>::TZ;
   constexpr int THREADS = TY * TZ;
   static_assert(THREADS % 32 == 0 && THREADS <= 1024, "GS tiles use whole warps of lines");
   const hs_op* A = sa.A;
@@ -447,10 +580,12 @@ static hs_status gs_run_t(const SolveArgs& sa, hs_result* res, double* hist) {
   GsArgs<T> a = {};
   a.bD = c.take<T>(g.N);
   int ntx, nty, ntz;
-  tile_counts<NDIM>(A, &ntx, &nty, &ntz);
+  tile_counts<NDIM, W>(A, &ntx, &nty, &ntz);
   if (NDIM == 2) ntz = 1;
   const int ntiles = ntx * nty * ntz, P = ntx + nty + ntz - 2;
   int* tabs = c.take<int>((size_t)ntiles + P + 1);
+  a.tile_done = c.take<unsigned>((size_t)ntiles);
+  a.claim = c.take<unsigned long long>(1);
   T *D = nullptr, *ax = nullptr, *ay = nullptr, *az = nullptr;
   if (OPK == OP_VARK) {
     D = c.take<T>(g.N);
@@ -517,7 +652,7 @@ static hs_status gs_run_t(const SolveArgs& sa, hs_result* res, double* hist) {
   a.tol = sa.tol;
   const int sx = TX + 2, sy = TY + 2, sz = (NDIM == 3) ? TZ + 2 : 1;
   const size_t smem = (size_t)sx * sy * sz * sizeof(T);
-  auto kern = k_gs<T, OPK, NDIM>;
+  auto kern = k_gs<T, OPK, NDIM, W>;
   // static shared memory (reduction scratch) comes on top of the dynamic
   // tile, so always raise the dynamic limit to what the tile needs
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -544,8 +679,16 @@ hs_status run_gauss_seidel(const SolveArgs& sa, hs_result* res, double* hist) {
   const int opk = opkind_of(sa.A);
   const bool d3 = sa.A->ndim >= 3;
   if (opk == OP_BOX27) return run_gauss_seidel27(sa, res, hist);
-#define HS_GS(TT, OK)                                                        \
-  if (opk == OK) return d3 ? gs_run_t<TT, OK, 3>(sa, res, hist) : gs_run_t<TT, OK, 2>(sa, res, hist);
+  // batches of four or more sweeps of one direction pipeline (small tiles);
+  // single sweeps and symmetric batches are bound by the tile-plane chain
+  // (large tiles, fewer planes)
+  const int per_batch = sa.tol > 0.0 ? sa.o.check_every : sa.maxit;
+  const bool deep = sa.o.gs_mode == HS_GS_SYMMETRIC || per_batch < 4;
+#define HS_GS(TT, OK)                                                                         \
+  if (opk == OK) {                                                                            \
+    if (!d3) return gs_run_t<TT, OK, 2, 0>(sa, res, hist);                                    \
+    return deep ? gs_run_t<TT, OK, 3, 1>(sa, res, hist) : gs_run_t<TT, OK, 3, 0>(sa, res, hist); \
+  }
   if (sa.dtype == HS_F64) {
     HS_GS(double, OP_SYM)
     HS_GS(double, OP_NONSYM)
