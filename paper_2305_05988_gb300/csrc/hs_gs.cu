@@ -665,6 +665,7 @@ static hs_status gs_run_t(const SolveArgs& sa, hs_result* res, double* hist) {
     return HS_ERR_CUDA;
   }
   int grid = std::min(per_sm * sm_count(), MAX_BLOCKS);
+  if (sa.o.max_blocks > 0) grid = std::min(grid, sa.o.max_blocks);
   void* args[] = {&a};
   e = cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(THREADS), args, smem, sa.stream);
   if (e != cudaSuccess) return cuda_fail(e, "cooperative launch");

@@ -137,6 +137,24 @@ def test_gauss_seidel_sweeps(shape, kind, sweeps, mode):
     assert rel(host(x_g), x_o) <= 1e-12
 
 
+@pytest.mark.parametrize("blocks", [1, 2, 3, 13])
+@pytest.mark.parametrize("mode,sweeps,check_every", [("forward", 9, 1), ("forward", 9, 4), ("symmetric", 4, 1),
+                                                     ("backward", 7, 7)])
+def test_gauss_seidel_few_blocks(blocks, mode, sweeps, check_every):
+    # the tiles are a dataflow graph: with few blocks each one claims many
+    # (sweep, tile) items in turn, and with check_every > 1 sweeps overlap
+    shape = (70, 19, 21)
+    A_o, A_g, _k = make_ops(shape, "up")
+    b = inputs.uniform_pm1(11, 1, A_o.N)
+    x0 = inputs.uniform_pm1(12, 1, A_o.N)
+    m = {"forward": oracle.GS_FORWARD, "backward": oracle.GS_BACKWARD, "symmetric": oracle.GS_SYMMETRIC}[mode]
+    x_o, _, _, _ = oracle.gauss_seidel(A_o, b, x0, maxit=sweeps, mode=m)
+    x_g, info = hs.gauss_seidel(A_g, dev(b), dev(x0), maxit=sweeps, mode=mode, tol=1e-300,
+                                check_every=check_every, max_blocks=blocks)
+    assert info.iters == sweeps and info.status == "NOT_CONVERGED", info
+    assert rel(host(x_g), x_o) <= 1e-12
+
+
 def test_gauss_seidel_tolerance_history():
     shape = (45, 38)
     A_o, A_g, _k = make_ops(shape, "lap")
