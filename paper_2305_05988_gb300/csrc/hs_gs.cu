@@ -448,8 +448,14 @@ __device__ bool gs_batch_df(const GsArgs<T>& a, T* sm, int nsw, int mode, unsign
 template <typename T, int OPK, int NDIM, int W>
 __global__ void __launch_bounds__(gs_threads<NDIM, W>()) k_gs(GsArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  __shared__ double sh[32 * MAX_SCAL];
   T* sm = reinterpret_cast<T*>(smraw);
+  // the reductions run between batches, when no tile is staged: their
+  // scratch shares the tile buffer, which keeps a 32 x 8 x 8 FP64 block at
+  // 28.2 KB of shared memory (eight resident blocks per SM instead of seven)
+  static_assert((GsTile<NDIM, W>::TX + 2) * (GsTile<NDIM, W>::TY + 2) * (NDIM == 3 ? GsTile<NDIM, W>::TZ + 2 : 1) *
+                        sizeof(T) >= 32 * MAX_SCAL * sizeof(double),
+                "the tile buffer must hold the reduction scratch");
+  double* sh = reinterpret_cast<double*>(smraw);
   const long long N = a.g.N;
 
   double acc[1] = {0.0};
