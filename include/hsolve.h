@@ -144,7 +144,7 @@ hs_status hs_op_laplacian(const hs_grid *g, hs_op **out);
  * absolute residual of 1e-6.  The coefficients are the reading that fits the
  * paper's printed iteration counts.  The 27-point operator supports SpMV,
  * residual, Jacobi, CG, CG-NB, BiCGStab, mixed precision and lexicographic
- * Gauss-Seidel (one grid-wide step per point hyperplane i + 2j + 4k, so a
+ * Gauss-Seidel (one step per point hyperplane i + 2j + 4k, so a
  * sweep takes nx + 2 ny + 4 nz steps); the batched solver returns
  * HS_ERR_INVALID for it.
  * HS_ERR_INVALID: points not 7 or 27, a 27-point operator on a 1-/2-D grid. */

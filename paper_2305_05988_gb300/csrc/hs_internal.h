@@ -119,7 +119,7 @@ hs_status run_cg_nb(const SolveArgs& a, hs_result* res, double* hist);
 bool jacobi_tb_applies(const SolveArgs& a);
 hs_status run_jacobi_tb(const SolveArgs& a, hs_result* res, double* hist);
 hs_status run_gauss_seidel(const SolveArgs& a, hs_result* res, double* hist);
-// 27-point operator: one grid step per point hyperplane i + 2j + 4k (hs_gs27.cu).
+// 27-point operator: one step per point hyperplane i + 2j + 4k (hs_gs27.cu).
 hs_status run_gauss_seidel27(const SolveArgs& a, hs_result* res, double* hist);
 size_t gs27_progress_bytes();
 hs_status run_spmv(const hs_op* A, hs_dtype dt, const void* x, void* y, cudaStream_t st);

@@ -2,7 +2,7 @@
 HPCG's 7- and 27-point matrices (diagonal 27, -1 per neighbour), b = A 1,
 x0 = 0, absolute criterion ||r|| < 1e-6.  The 27-point operator runs on the
 box-sum tile engine (separable 3x3x3 sums); its lexicographic Gauss-Seidel on
-the point-hyperplane kernel (one grid step per i + 2j + 4k).
+the point-hyperplane kernel (one step per i + 2j + 4k).
 
 Tolerances: SpMV 1e-13 relative; Jacobi and GS iterates after k sweeps 1e-12
 (FP32 GS 2e-6);
@@ -105,7 +105,7 @@ GS27_SHAPES = [(37, 19, 11), (5, 4, 3), (1, 9, 7), (8, 1, 5), (6, 5, 1), (1, 1, 
 @pytest.mark.parametrize("shape", GS27_SHAPES)
 @pytest.mark.parametrize("mode", ["forward", "backward", "symmetric"])
 def test_hpcg27_gauss_seidel_sweeps(shape, mode):
-    # the 27-point sweep runs one grid step per point hyperplane i + 2j + 4k;
+    # the 27-point sweep runs one step per point hyperplane i + 2j + 4k;
     # tol = 0 pipelines all sweeps of a direction 8 hyperplanes apart
     A_o, A_g = ops(shape, 27)
     b = inputs.uniform_pm1(54, 1, A_o.N)
