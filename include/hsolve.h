@@ -337,6 +337,22 @@ int hs_batch_graph_used(const hs_batch *batch);
 int hs_batch_grid(const hs_batch *batch);
 hs_status hs_batch_team_sizes(const hs_batch *batch, int *teams);
 
+/* Diagnostics: runs one of the library's bounded device-side waits against a
+ * condition that never comes true, to show that the wait gives up, reports
+ * it and leaves the context usable.  kind:
+ *   0  the grid reduce-barrier of the persistent solvers (a team of two
+ *      blocks of which only one is launched),
+ *   1  the Gauss-Seidel tile-dependency wait (a sweep count that nothing
+ *      publishes),
+ *   2  the 27-point Gauss-Seidel ring-neighbour wait (progress words that
+ *      nothing publishes).
+ * timeout_s: the wait's limit, 0 < timeout_s <= 10 seconds.  Allocates 4 KB of
+ * device memory for the call and synchronises `stream`.
+ * Returns HS_ERR_TIMEOUT when the wait gave up as designed, HS_OK if it ended
+ * otherwise (a defect), HS_ERR_INVALID for a bad kind or limit, HS_ERR_CUDA
+ * on a CUDA error. */
+hs_status hs_diag_wait_timeout(int kind, double timeout_s, void *stream);
+
 /* Thread-local message describing the last non-OK status (never NULL). */
 const char *hs_last_error(void);
 

@@ -99,6 +99,7 @@ SIGNATURES = {
     "hs_batch_graph_used": (_i, [_vp]),
     "hs_batch_grid": (_i, [_vp]),
     "hs_batch_team_sizes": (_i, [_vp, ctypes.POINTER(_i)]),
+    "hs_diag_wait_timeout": (_i, [_i, ctypes.c_double, _vp]),
     "hs_last_error": (ctypes.c_char_p, []),
     "hs_version": (ctypes.c_char_p, []),
 }

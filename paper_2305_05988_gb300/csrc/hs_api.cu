@@ -190,6 +190,48 @@ extern "C" {
 const char* hs_last_error(void) { return g_err; }
 const char* hs_version(void) { return "hsolve 0.1 (sm_103a)"; }
 
+hs_status hs_diag_wait_timeout(int kind, double timeout_s, void* stream) {
+  if (kind < 0 || kind > 2) {
+    set_error("kind must be 0 (grid barrier), 1 (Gauss-Seidel tile wait) or 2 (27-point ring wait)");
+    return HS_ERR_INVALID;
+  }
+  if (!(timeout_s > 0.0) || timeout_s > 10.0) {
+    set_error("timeout_s must lie in (0, 10]");
+    return HS_ERR_INVALID;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  char* buf = nullptr;
+  cudaError_t e = cudaMalloc(&buf, 4096);
+  if (e != cudaSuccess) return cuda_fail(e, "diagnostic buffer");
+  // control block, then zeroed words: barrier partials / flags / progress
+  Common cm{reinterpret_cast<Ctrl*>(buf), reinterpret_cast<double*>(buf + 512), nullptr};
+  hs_opts o = default_opts();
+  o.timeout_s = timeout_s;
+  hs_status s = HS_OK;
+  e = cudaMemsetAsync(buf, 0, 4096, st);
+  if (e != cudaSuccess) s = cuda_fail(e, "diagnostic buffer");
+  if (s == HS_OK) s = init_ctrl(cm, o, st);
+  if (s == HS_OK) {
+    if (kind == 0) s = diag_team_wait(cm.ctrl, cm.partials, st);
+    else if (kind == 1) s = diag_gs_wait(cm.ctrl, reinterpret_cast<const unsigned*>(buf + 1024), st);
+    else s = diag_gs27_wait(cm.ctrl, reinterpret_cast<const unsigned long long*>(buf + 1024), st);
+  }
+  int status = 0;
+  if (s == HS_OK) {
+    e = cudaMemcpyAsync(&status, &cm.ctrl->status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) s = cuda_fail(e, "diagnostic wait");
+  }
+  cudaError_t ef = cudaFree(buf);
+  if (s != HS_OK) return s;
+  if (ef != cudaSuccess) return cuda_fail(ef, "diagnostic buffer");
+  if (status == DS_TIMEOUT) {
+    set_error("the wait gave up after %g s, as designed", timeout_s);
+    return HS_ERR_TIMEOUT;
+  }
+  return HS_OK;
+}
+
 hs_status hs_grid_create(int ndim, const int64_t n[3], hs_grid** out) {
   if (!out) { set_error("out is NULL"); return HS_ERR_INVALID; }
   *out = nullptr;

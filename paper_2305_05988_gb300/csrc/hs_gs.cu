@@ -313,6 +313,30 @@ __device__ __forceinline__ void gs_tile(const GsArgs<T>& a, T* sm, int tile, boo
   __syncthreads();
 }
 
+// Warp 0 waits until every participating lane's sweep count *f has reached
+// `target`, bounded by the solve's timeout (status DS_TIMEOUT); it ends early
+// when another block has flagged an error.  All 32 lanes call it.
+__device__ __forceinline__ bool gs_poll(bool mine, const unsigned* f, unsigned target, Ctrl* ctrl) {
+  const int lane = threadIdx.x & 31;
+  unsigned spins = 0;
+  unsigned long long t0 = 0;
+  while (true) {
+    const bool sat = !mine || ld_acquire(f) >= target;
+    if (__all_sync(0xffffffffu, sat)) return true;
+    int stop = 0;
+    if (lane == 0 && (++spins & 255) == 0) {
+      if (t0 == 0) t0 = global_ns();
+      if (ld_acquire_int(&ctrl->status) < 0) {
+        stop = 1;
+      } else if (global_ns() - t0 > ctrl->timeout_ns) {
+        atomicCAS(&ctrl->status, 0, (int)DS_TIMEOUT);
+        stop = 1;
+      }
+    }
+    if (__shfl_sync(0xffffffffu, stop, 0)) return false;
+  }
+}
+
 // Dataflow form of a batch: nsw sweeps (directions by `mode`; symmetric
 // alternates forward and backward) with no grid-wide step.  Work items are
 // (sweep, tile) pairs, taken from a counter in the order of the grid-step
@@ -399,26 +423,7 @@ __device__ bool gs_batch_df(const GsArgs<T>& a, T* sm, int nsw, int mode, unsign
             target = newside ? gs + 1 : gs;
           }
         }
-        unsigned spins = 0;
-        unsigned long long t0 = 0;
-        while (true) {
-          const bool sat = f == nullptr || ld_acquire(f) >= target;
-          if (__all_sync(0xffffffffu, sat)) break;
-          int stop = 0;
-          if (lane == 0 && (++spins & 255) == 0) {
-            if (t0 == 0) t0 = global_ns();
-            if (ld_acquire_int(&a.cm.ctrl->status) < 0) {
-              stop = 1;
-            } else if (global_ns() - t0 > a.cm.ctrl->timeout_ns) {
-              atomicCAS(&a.cm.ctrl->status, 0, (int)DS_TIMEOUT);
-              stop = 1;
-            }
-          }
-          if (__shfl_sync(0xffffffffu, stop, 0)) {
-            ok = 0;
-            break;
-          }
-        }
+        ok = gs_poll(f != nullptr, f, target, a.cm.ctrl);
       }
       if (lane == 0) {
         s_item = u;
@@ -680,6 +685,17 @@ static hs_status gs_run_t(const SolveArgs& sa, hs_result* res, double* hist) {
     if (s != HS_OK) return s;
   }
   return finish_solve_pub(sa, cm, D, ax, ay, az, a.bD, res, hist, sa.tol > 0.0);
+}
+
+// Warp 0 waits for a sweep count that nothing publishes (diagnostic).
+__global__ void k_diag_gs(Ctrl* ctrl, const unsigned* flag) {
+  if (threadIdx.x < 32) gs_poll(threadIdx.x == 0, flag, 1u, ctrl);
+}
+
+hs_status diag_gs_wait(Ctrl* ctrl, const unsigned* flag, cudaStream_t st) {
+  k_diag_gs<<<1, 32, 0, st>>>(ctrl, flag);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? HS_OK : cuda_fail(e, "diagnostic launch");
 }
 
 hs_status run_gauss_seidel(const SolveArgs& sa, hs_result* res, double* hist) {

@@ -344,6 +344,17 @@ static hs_status gs27_t(const SolveArgs& sa, hs_result* res, double* hist) {
   return finish_solve_pub(sa, cm, nullptr, nullptr, nullptr, nullptr, a.bD, res, hist, sa.tol > 0.0);
 }
 
+// Thread 0 waits for ring neighbours that never publish (diagnostic).
+__global__ void k_diag_gs27(Ctrl* ctrl, const unsigned long long* words) {
+  if (threadIdx.x == 0) wait_neighbours(words, words + 1, 1ull, ctrl);
+}
+
+hs_status diag_gs27_wait(Ctrl* ctrl, const unsigned long long* words, cudaStream_t st) {
+  k_diag_gs27<<<1, 32, 0, st>>>(ctrl, words);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? HS_OK : cuda_fail(e, "diagnostic launch");
+}
+
 size_t gs27_progress_bytes() { return (GS27_MAX_BLOCKS * sizeof(unsigned long long) + 255) & ~(size_t)255; }
 
 hs_status run_gauss_seidel27(const SolveArgs& sa, hs_result* res, double* hist) {

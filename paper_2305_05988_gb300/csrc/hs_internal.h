@@ -133,6 +133,12 @@ hs_status init_ctrl(const Common& cm, const hs_opts& o, cudaStream_t st);
 hs_status finish_solve_pub(const SolveArgs& sa, const Common& cm, const void* D, const void* ax, const void* ay,
                            const void* az, void* rbuf, hs_result* res, double* hist, bool want_hist);
 
+// Diagnostic kernels: one bounded wait each, on a condition that never comes
+// true (hs_diag_wait_timeout).  `ctrl` is initialised, `words` zeroed.
+hs_status diag_team_wait(Ctrl* ctrl, double* partials, cudaStream_t st);       // hs_kernels.cu
+hs_status diag_gs_wait(Ctrl* ctrl, const unsigned* flag, cudaStream_t st);     // hs_gs.cu
+hs_status diag_gs27_wait(Ctrl* ctrl, const unsigned long long* words, cudaStream_t st);   // hs_gs27.cu
+
 // Options with defaults filled in and validated (false: invalid, error set).
 bool merge_opts(const hs_opts* in, hs_opts* out);
 

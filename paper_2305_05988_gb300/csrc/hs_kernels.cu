@@ -591,6 +591,25 @@ hs_status launch_coop(const void* fn, int grid, int block, void** args, size_t s
   return HS_OK;
 }
 
+// One block of a team of two: the reduce-barrier waits for a block that is
+// never launched and must give up with DS_TIMEOUT.
+__global__ void k_diag_team(Ctrl* ctrl, double* partials) {
+  __shared__ double sh[32 * MAX_SCAL];
+  Team tm;
+  tm.rank = 0;
+  tm.size = 2;
+  tm.ctrl = ctrl;
+  tm.partials = partials;
+  double z[1] = {0.0}, o[1];
+  team_reduce<1>(tm, z, o, sh);
+}
+
+hs_status diag_team_wait(Ctrl* ctrl, double* partials, cudaStream_t st) {
+  k_diag_team<<<1, 128, 0, st>>>(ctrl, partials);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? HS_OK : cuda_fail(e, "diagnostic launch");
+}
+
 hs_status init_ctrl(const Common& cm, const hs_opts& o, cudaStream_t st) {
   double t = o.timeout_s > 0 ? o.timeout_s : 2.0;
   k_init_ctrl<<<1, 32, 0, st>>>(cm.ctrl, (unsigned long long)(t * 1e9));

@@ -289,6 +289,21 @@ def bicgstab(A: Operator, b, x0=None, tol: float = 1e-10, maxit: int = 10000, hi
     return _solve(_lib.HS_SOLVER_BICGSTAB, A, b, x0, tol, maxit, history, restart_eps=restart_eps, **kw)
 
 
+DIAG_WAITS = {"grid_barrier": 0, "gs_tile": 1, "gs27_ring": 2}
+
+
+def diag_wait_timeout(kind: str, timeout_s: float = 0.05) -> str:
+    """Run one of the library's bounded device-side waits against a condition
+    that never comes true; returns the status name ("ERR_TIMEOUT" when the
+    wait gave up as designed).  The CUDA context stays usable."""
+    lib = _lib.load()
+    stream = torch.cuda.current_stream().cuda_stream
+    st = lib.hs_diag_wait_timeout(DIAG_WAITS[kind], float(timeout_s), ctypes.c_void_p(stream))
+    if st not in (_lib.HS_OK, _lib.HS_ERR_TIMEOUT):
+        _lib.check(st, "hs_diag_wait_timeout")
+    return _lib.STATUS_NAMES.get(st, str(st))
+
+
 def grad_logk(A: Operator, u: torch.Tensor, lam: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
     """dL/dlog k per cell from the forward solution u and the adjoint lam (float64)."""
     if A.kind != "diffusion":
