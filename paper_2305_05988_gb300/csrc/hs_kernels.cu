@@ -238,9 +238,17 @@ __global__ void __launch_bounds__(512) k_jacobi(JacArgs<T> a) {
 #ifndef HS_BI_MAXNREG
 #define HS_BI_MAXNREG 80
 #endif
+// FP32 CG on the variable-coefficient operator (the inner solve of mixed
+// refinement): 64 registers, four blocks per SM instead of three (512^3:
+// 1.74 -> 1.63 ms/iteration; 48 or 40 spill and run at 2.1-2.2 ms; the
+// FP32 Laplacian is slower under the cap, 1.29 -> 1.59, and keeps none).
+#ifndef HS_CG32_MAXNREG
+#define HS_CG32_MAXNREG 64
+#endif
 template <typename T, int OPK>
 constexpr int cg_maxnreg() {
-  return (HS_CG_MAXNREG > 0 && sizeof(T) == 8 && OPK != OP_VARK) ? HS_CG_MAXNREG : 255;
+  if (sizeof(T) == 4) return (HS_CG32_MAXNREG > 0 && OPK == OP_VARK) ? HS_CG32_MAXNREG : 255;
+  return (HS_CG_MAXNREG > 0 && OPK != OP_VARK) ? HS_CG_MAXNREG : 255;
 }
 template <typename T, int OPK>
 constexpr int bi_maxnreg() {
