@@ -245,14 +245,26 @@ __global__ void __launch_bounds__(512) k_jacobi(JacArgs<T> a) {
 #ifndef HS_CG32_MAXNREG
 #define HS_CG32_MAXNREG 64
 #endif
+// FP64 CG on the variable-coefficient operator: 80 registers (512^3: 3.73 ->
+// 3.49 ms/iteration; 64 spills, 4.37).  FP32 BiCGStab: 64 registers, four
+// blocks per SM instead of two (512^3 upwind 3.63 -> 2.44, diffusion 4.24 ->
+// 3.23 ms/iteration; 80: 2.64 / 3.39).
+#ifndef HS_CGV64_MAXNREG
+#define HS_CGV64_MAXNREG 80
+#endif
+#ifndef HS_BI32_MAXNREG
+#define HS_BI32_MAXNREG 64
+#endif
 template <typename T, int OPK>
 constexpr int cg_maxnreg() {
   if (sizeof(T) == 4) return (HS_CG32_MAXNREG > 0 && OPK == OP_VARK) ? HS_CG32_MAXNREG : 255;
-  return (HS_CG_MAXNREG > 0 && OPK != OP_VARK) ? HS_CG_MAXNREG : 255;
+  if (OPK == OP_VARK) return HS_CGV64_MAXNREG > 0 ? HS_CGV64_MAXNREG : 255;
+  return HS_CG_MAXNREG > 0 ? HS_CG_MAXNREG : 255;
 }
 template <typename T, int OPK>
 constexpr int bi_maxnreg() {
-  return (HS_BI_MAXNREG > 0 && sizeof(T) == 8) ? HS_BI_MAXNREG : 255;
+  if (sizeof(T) == 4) return HS_BI32_MAXNREG > 0 ? HS_BI32_MAXNREG : 255;
+  return HS_BI_MAXNREG > 0 ? HS_BI_MAXNREG : 255;
 }
 
 template <typename T, int OPK, int NDIM>
