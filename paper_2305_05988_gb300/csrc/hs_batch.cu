@@ -114,7 +114,7 @@ __device__ __forceinline__ void batch_job(const BatchSys* __restrict__ sys, int 
 // system each), then takes single-block systems from a queue ordered
 // largest first until the queue is empty.  Queue jobs never wait on another
 // block, so no block can wait on a block that is busy elsewhere.
-__global__ void __launch_bounds__(BATCH_THREADS) k_batch(const BatchSys* __restrict__ sys,
+__global__ void __launch_bounds__(BATCH_THREADS, HS_BATCH_MINBLOCKS) k_batch(const BatchSys* __restrict__ sys,
                                                          const int* __restrict__ job_off,
                                                          const BatchJob* __restrict__ jobs,
                                                          const int* __restrict__ queue, int nqueue,

@@ -170,7 +170,7 @@ __device__ __forceinline__ void mx_job(const MxSys* __restrict__ sys, int s, int
 
 // Team jobs first, then single-block systems from the largest-first queue
 // (the scheme of the FP64 batch kernel).
-__global__ void __launch_bounds__(BATCH_THREADS) k_batch_mx(const MxSys* __restrict__ sys,
+__global__ void __launch_bounds__(BATCH_THREADS, HS_BATCHMX_MINBLOCKS) k_batch_mx(const MxSys* __restrict__ sys,
                                                             const int* __restrict__ job_off,
                                                             const BatchJob* __restrict__ jobs,
                                                             const int* __restrict__ queue, int nqueue,
