@@ -134,6 +134,10 @@ def test_hpcg27_gauss_seidel_few_blocks(blocks):
         x_o, _, _, _ = oracle.gauss_seidel(A_o, b, x0, maxit=5, mode=om)
         x_g, info = hs.gauss_seidel(A_g, dev(b), dev(x0), maxit=5, mode=mode, max_blocks=blocks)
         assert info.iters == 5 and rel(host(x_g), x_o) <= 1e-12, (mode, rel(host(x_g), x_o))
+        # residual checks every 2 iterations: batches of 2, 2 and 1
+        x_g, info = hs.gauss_seidel(A_g, dev(b), dev(x0), maxit=5, mode=mode, max_blocks=blocks, tol=1e-300,
+                                    check_every=2)
+        assert info.iters == 5 and rel(host(x_g), x_o) <= 1e-12, (mode, rel(host(x_g), x_o))
 
 
 @pytest.mark.parametrize("mode", ["forward", "symmetric"])

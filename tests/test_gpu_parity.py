@@ -139,7 +139,7 @@ def test_gauss_seidel_sweeps(shape, kind, sweeps, mode):
 
 @pytest.mark.parametrize("blocks", [1, 2, 3, 13])
 @pytest.mark.parametrize("mode,sweeps,check_every", [("forward", 9, 1), ("forward", 9, 4), ("symmetric", 4, 1),
-                                                     ("backward", 7, 7)])
+                                                     ("symmetric", 5, 2), ("backward", 7, 7)])
 def test_gauss_seidel_few_blocks(blocks, mode, sweeps, check_every):
     # the tiles are a dataflow graph: with few blocks each one claims many
     # (sweep, tile) items in turn, and with check_every > 1 sweeps overlap
