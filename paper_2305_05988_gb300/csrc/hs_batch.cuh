@@ -12,15 +12,15 @@ struct BatchJob {
 
 constexpr int BATCH_THREADS = 256;   // 8 rows per tile
 // Minimum resident blocks per SM asked of the compiler for the batched
-// kernels: three (80 registers) against its own choice of 128 (512-system
-// batch, fresh tile tuning each run: FP64 16.8 -> 9.7 s, FP32-inner
-// refinement 32.1 -> 9.7 s; two blocks: 10.8 / 13.0 s).  More resident
-// blocks give the large systems larger teams.
+// kernels: four (64 registers) against its own choice of 128 (512-system
+// batch, fresh tile tuning each run: FP64 16.8 -> 9.56 s, FP32-inner
+// refinement 32.1 -> 9.38 s; three blocks: 9.70 / 9.68 s, two: 10.8 /
+// 13.0 s).  More resident blocks give the large systems larger teams.
 #ifndef HS_BATCH_MINBLOCKS
-#define HS_BATCH_MINBLOCKS 3
+#define HS_BATCH_MINBLOCKS 4
 #endif
 #ifndef HS_BATCHMX_MINBLOCKS
-#define HS_BATCHMX_MINBLOCKS 3
+#define HS_BATCHMX_MINBLOCKS 4
 #endif
 constexpr int BATCH_BY = BATCH_THREADS / 32;
 // The batch kernels hold every iteration body at once, so they run them
