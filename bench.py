@@ -63,8 +63,8 @@ FLOPS = {"spmv": 10.0, "jacobi": 9.0, "gauss_seidel": 9.0, "cg": 19.0, "bicgstab
 
 # DRAM bytes per unknown and iteration measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum) on the 200^3 case of the same step (every vector is
-# 64 MB there, above the 129 MB L2 with the solver state), see
-# profiles/fp64_and_traffic_poisson3d_200.md.  Traffic grows with unknowns x
+# 64 MB there, above the 129 MB L2 with the solver state; CG 825 iterations,
+# BiCGStab 452, Jacobi 20 sweeps in one launch each).  Traffic grows with unknowns x
 # iterations (each pass streams every vector), so a launch at 256^3 moves
 # this figure x N x iterations.  Re-measure whenever the kernel changes.
 TRAFFIC_B_PER_UNIT = {"cg": 72.6, "bicgstab": 137.0, "jacobi": 24.5}

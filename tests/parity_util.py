@@ -29,8 +29,9 @@ def oracle_window(A_o, b, solver, it_o, tol, reps=4, **kw):
     if hi - lo <= 1 and not restarted:
         return it_o - 2, it_o + 2, counts
     # BiCGStab restarts on an absolute threshold of |r . r'|; when they fire,
-    # where they fire depends on the rounding of every inner product (the
-    # oracle alone moves by ~10 % under 1-ulp perturbations)
+    # where they fire depends on the rounding of every inner product (on the
+    # 128^2 Laplacian the oracle alone ranges 680-756 iterations under 1-ulp
+    # perturbations of b, about 10 %)
     frac = 0.10 if restarted else 0.01
     slack = 2 + int(math.ceil(frac * it_o))
     return lo - slack, hi + slack, counts
