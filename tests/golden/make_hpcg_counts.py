@@ -61,6 +61,6 @@ def run(name):
 
 if __name__ == "__main__":
     names = sys.argv[1:] or ["hpcg7.cg", "hpcg7.bicgstab", "hpcg7.jacobi", "hpcg7.gauss_seidel_symmetric",
-                             "hpcg27.cg", "hpcg27.bicgstab"]
+                             "hpcg27.cg", "hpcg27.bicgstab", "hpcg27.jacobi"]
     for n in names:
         run(n)
