@@ -262,7 +262,7 @@ static hs_status cg_nb_t(const SolveArgs& sa, hs_result* res, double* hist) {
   a.paper_order = sa.o.paper_order;
   const int by = rows_for(g, sa.o);
   const size_t smem = slab_bytes<T>(by, 1);
-  int grid;
+  int grid = 0;
   s = plan_persistent(k_cg_nb<T, OPK, NDIM>, 32 * by, smem, g, by, true, &grid, &a.tl, sa.o, 1);
   if (s != HS_OK) return s;
   void* args[] = {&a};

@@ -747,7 +747,7 @@ hs_status run_jacobi(const SolveArgs& sa, hs_result* res, double* hist) {
     int by = rows_for(g, sa.o);
     constexpr int cx = cx_jac<T, OPK>();
     size_t smem = slab_bytes<T>(by, cx);
-    int grid;
+    int grid = 0;
     const void* kern = a.fuse ? (const void*)k_jacobi<T, OPK, NDIM, true> : (const void*)k_jacobi<T, OPK, NDIM, false>;
     s = a.fuse ? plan_persistent(k_jacobi<T, OPK, NDIM, true>, 32 * by, smem, g, by, false, &grid, &a.tl, sa.o, cx)
                : plan_persistent(k_jacobi<T, OPK, NDIM, false>, 32 * by, smem, g, by, false, &grid, &a.tl, sa.o, cx);
@@ -786,7 +786,7 @@ static hs_status cg_core(const hs_op* A, const Coef<T>& cf, double sigma, const 
   int by = rows_for(a.g, o);
   constexpr int cx = cx_cg<T, OPK>();
   size_t smem = slab_bytes<T>(by, cx);
-  int grid;
+  int grid = 0;
   s = plan_persistent(k_cg<T, OPK, NDIM>, 32 * by, smem, a.g, by, true, &grid, &a.tl, o, cx);
   if (s != HS_OK) return s;
   void* args[] = {&a};
@@ -819,7 +819,7 @@ static hs_status bicgstab_core(const hs_op* A, const Coef<T>& cf, double sigma, 
   if (s != HS_OK) return s;
   int by = rows_for(a.g, o);
   size_t smem = slab_bytes<T>(by, CX_BI);
-  int grid;
+  int grid = 0;
   s = plan_persistent(k_bicgstab<T, OPK, NDIM>, 32 * by, smem, a.g, by, true, &grid, &a.tl, o, CX_BI);
   if (s != HS_OK) return s;
   void* args[] = {&a};
