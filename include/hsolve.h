@@ -198,7 +198,14 @@ hs_status hs_jacobi(const hs_op *A, hs_dtype dtype, const void *b, void *x, doub
 /* Gauss-Seidel (section 3.1), exactly lexicographic: every update uses the
  * entries already updated in the same sweep (forward: idx ascending,
  * backward: descending; symmetric = forward then backward).  No recolouring:
- * the result equals the sequential sweep up to rounding. */
+ * the result equals the sequential sweep up to rounding.  x is updated in
+ * place.  Performance: sweeps of one direction between residual checks
+ * (opts->check_every with tol > 0, all maxit sweeps with tol == 0) overlap
+ * when there are four or more of them; single sweeps and the symmetric method
+ * run one after another.  The 27-point HPCG operator takes one step per point
+ * hyperplane (nx + 2 ny + 4 nz per sweep).  opts->max_blocks caps the grid.
+ * The workspace holds b / a_ii and the schedule's tables
+ * (hs_workspace_size). */
 hs_status hs_gauss_seidel(const hs_op *A, hs_dtype dtype, const void *b, void *x, double tol,
                           int maxit, const hs_opts *opts, void *ws, size_t ws_bytes, void *stream,
                           hs_result *res, double *hist);
