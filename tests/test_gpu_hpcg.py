@@ -200,3 +200,20 @@ def test_hpcg27_mixed_precision_certified():
     assert A_o.relres(b, host(x)) <= 1e-12 * (1 + 1e-3)
     assert np.max(np.abs(host(x) - 1.0)) <= 54 * 1e-12 * 10
 
+
+
+def test_hpcg27_gauss_seidel_edge_cases():
+    A_o, A_g = ops((9, 7, 5), 27)
+    # zero right-hand side: x = 0 after 0 iterations
+    z = torch.zeros(A_o.N, dtype=torch.float64, device="cuda")
+    x, info = hs.gauss_seidel(A_g, z, torch.ones_like(z), tol=1e-8, maxit=10, mode="symmetric")
+    assert info.status == "OK" and info.iters == 0 and torch.count_nonzero(x).item() == 0
+    # maxit = 0 leaves x as given
+    b = inputs.uniform_pm1(58, 1, A_o.N)
+    x0 = inputs.uniform_pm1(59, 1, A_o.N)
+    x, info = hs.gauss_seidel(A_g, dev(b), dev(x0), maxit=0)
+    assert info.iters == 0 and np.array_equal(host(x), x0)
+    # a non-finite right-hand side is reported, not iterated on
+    b[11] = np.inf
+    x, info = hs.gauss_seidel(A_g, dev(b), tol=1e-8, maxit=10)
+    assert info.status == "ERR_NONFINITE"
