@@ -192,3 +192,32 @@ def test_diag_wait_validation(lib):
     assert lib.hs_diag_wait_timeout(0, 0.0, None) == _lib.HS_ERR_INVALID
     assert lib.hs_diag_wait_timeout(1, 10.5, None) == _lib.HS_ERR_INVALID
     assert lib.hs_diag_wait_timeout(2, float("nan"), None) == _lib.HS_ERR_INVALID
+
+
+def test_gauss_seidel_workspace_sizes(lib):
+    # GS keeps b / a_ii (one vector) plus its schedule: tile-plane tables,
+    # per-tile sweep counts and a claim counter (7-point), or per-block
+    # progress words (27-point); never less than the vector, never a
+    # Krylov solver's several vectors
+    g = ctypes.c_void_p()
+    lib.hs_grid_create(3, (ctypes.c_int64 * 3)(64, 48, 40), ctypes.byref(g))
+    lap, box = ctypes.c_void_p(), ctypes.c_void_p()
+    assert lib.hs_op_laplacian(g, ctypes.byref(lap)) == _lib.HS_OK
+    assert lib.hs_op_hpcg(g, 27, ctypes.byref(box)) == _lib.HS_OK
+    lib.hs_grid_destroy(g)
+    N = 64 * 48 * 40
+    for op in (lap, box):
+        gs, cg = ctypes.c_size_t(), ctypes.c_size_t()
+        assert lib.hs_workspace_size(op, _lib.HS_SOLVER_GAUSS_SEIDEL, _lib.HS_F64, None, 10,
+                                     ctypes.byref(gs)) == _lib.HS_OK
+        assert lib.hs_workspace_size(op, _lib.HS_SOLVER_CG, _lib.HS_F64, None, 10, ctypes.byref(cg)) == _lib.HS_OK
+        assert 8 * N < gs.value < cg.value
+        gs32 = ctypes.c_size_t()
+        lib.hs_workspace_size(op, _lib.HS_SOLVER_GAUSS_SEIDEL, _lib.HS_F32, None, 10, ctypes.byref(gs32))
+        assert 4 * N < gs32.value < gs.value
+        # the residual history grows with maxit
+        big = ctypes.c_size_t()
+        lib.hs_workspace_size(op, _lib.HS_SOLVER_GAUSS_SEIDEL, _lib.HS_F64, None, 100000, ctypes.byref(big))
+        assert big.value > gs.value
+    lib.hs_op_destroy(lap)
+    lib.hs_op_destroy(box)
