@@ -451,6 +451,26 @@ def test_hpcg_exact_solution_ones():
         assert np.max(np.abs(xj - 1.0)) <= 1e-12
 
 
+@pytest.mark.parametrize("ms,sweeps", [((1, 1, 1), 60), ((3, 2, 4), 25)])
+def test_hpcg27_jacobi_closed_form(ms, sweeps):
+    # D = 27 I: for b = lambda v (v an eigenvector of A) and x0 = 0 the Jacobi
+    # error contracts by mu = 1 - lambda/27 per sweep, x_k = (1 - mu^k) v
+    shape = (9, 7, 6)
+    A = oracle.Operator(shape, oracle.HPCG27)
+    vs, prod = [], 1.0
+    for n, m in zip(shape, ms):
+        th = m * math.pi / (n + 1)
+        vs.append(np.sin(th * np.arange(1, n + 1)))
+        prod *= 1.0 + 2.0 * math.cos(th)
+    v = tensor_vec(vs)
+    lam = 28.0 - prod
+    mu = 1.0 - lam / 27.0
+    x, it, _, _ = oracle.jacobi(A, lam * v, maxit=sweeps)
+    assert it == sweeps
+    ref = (1.0 - mu ** sweeps) * v
+    assert np.linalg.norm(x - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
 @pytest.mark.parametrize("shape", [(4, 3, 5), (3, 3, 3)])
 def test_hpcg27_gauss_seidel_dense_triangular(shape):
     # forward: (D + L) x' = b - U x; backward: (D + U) x' = b - L x
