@@ -471,6 +471,25 @@ def test_hpcg27_jacobi_closed_form(ms, sweeps):
     assert np.linalg.norm(x - ref) <= 1e-12 * np.linalg.norm(ref)
 
 
+def test_hpcg27_krylov_one_step_on_an_eigenvector():
+    # b = v with A v = lambda v: the first Krylov space holds x* = v / lambda
+    shape = (9, 7, 6)
+    A = oracle.Operator(shape, oracle.HPCG27)
+    vs, prod = [], 1.0
+    for n, m in zip(shape, (2, 3, 1)):
+        th = m * math.pi / (n + 1)
+        vs.append(np.sin(th * np.arange(1, n + 1)))
+        prod *= 1.0 + 2.0 * math.cos(th)
+    v = tensor_vec(vs)
+    lam = 28.0 - prod
+    x, it, st, _ = oracle.cg(A, v, tol=1e-12, maxit=10)
+    assert st == oracle.OK and it == 1
+    assert np.linalg.norm(x - v / lam) <= 1e-13 * np.linalg.norm(v / lam)
+    xb, itb, stb, _, _ = oracle.bicgstab(A, v, tol=1e-12, maxit=10)
+    assert stb == oracle.OK and itb == 1
+    assert np.linalg.norm(xb - v / lam) <= 1e-13 * np.linalg.norm(v / lam)
+
+
 @pytest.mark.parametrize("shape", [(4, 3, 5), (3, 3, 3)])
 def test_hpcg27_gauss_seidel_dense_triangular(shape):
     # forward: (D + L) x' = b - U x; backward: (D + U) x' = b - L x
