@@ -538,6 +538,16 @@ def test_cg_nb_equals_classical_cg_iterates():
         assert np.linalg.norm(xn - xc) <= 1e-10 * np.linalg.norm(xc), k
 
 
+def test_cg_nb_equals_classical_cg_on_the_27_point_system():
+    shape = (9, 8, 7)
+    A = oracle.Operator(shape, oracle.HPCG27)
+    b = A.spmv(np.ones(A.N))
+    for k in (1, 3, 10, 25):
+        xc, _, _, _ = oracle.cg(A, b, maxit=k, tol=0.0)
+        xn, _, _, _ = oracle.cg_nb(A, b, maxit=k, tol=0.0)
+        assert np.linalg.norm(xn - xc) <= 1e-10 * np.linalg.norm(xc), k
+
+
 def test_cg_nb_count_and_finite_termination():
     shape = (20, 17)
     A = oracle.Operator(shape)
