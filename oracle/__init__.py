@@ -19,6 +19,7 @@ is stated beside it in ``oracle.c``:
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -29,28 +30,43 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_OMP_PATH = os.path.join(_BUILD, "liboracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
+_use_omp = False
 
 LAPLACIAN, UPWIND, DIFFUSION, HPCG7, HPCG27 = 0, 1, 2, 3, 4
 GS_FORWARD, GS_BACKWARD, GS_SYMMETRIC = 0, 1, 2
 OK, NOT_CONVERGED, BREAKDOWN = 0, 1, -3
 
 
-def build(force: bool = False) -> str:
-    """Compile oracle.c into _build/liboracle.so (gcc, plain C11)."""
+def _compile(out: str, extra, force: bool) -> str:
     src = os.path.join(_HERE, "oracle.c")
     hdr = os.path.join(_HERE, "oracle.h")
-    if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(src), os.path.getmtime(hdr))):
-        return _LIB_PATH
+    if (not force and os.path.exists(out)
+            and os.path.getmtime(out) >= max(os.path.getmtime(src), os.path.getmtime(hdr))):
+        return out
     os.makedirs(_BUILD, exist_ok=True)
-    tmp = _LIB_PATH + ".%d.tmp" % os.getpid()
-    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           "-o", tmp, src, "-lm"]
+    tmp = out + ".%d.tmp" % os.getpid()
+    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"] + list(extra) + \
+        ["-o", tmp, src, "-lm"]
     subprocess.run(cmd, check=True, cwd=_HERE)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    os.replace(tmp, out)
+    return out
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into _build/liboracle.so (gcc, plain C11, sequential:
+    the parity checker) and, where gcc has OpenMP, _build/liboracle_omp.so
+    (the same source with its element-wise loops on all host cores; bitwise
+    the same results, used only to time the oracle and to run long
+    reference solves)."""
+    path = _compile(_LIB_PATH, [], force)
+    try:
+        _compile(_OMP_PATH, ["-fopenmp"], force)
+    except (subprocess.CalledProcessError, OSError):
+        pass
+    return path
 
 
 class _Op(ctypes.Structure):
@@ -59,11 +75,9 @@ class _Op(ctypes.Structure):
                 ("beta", ctypes.c_double * 3), ("k", ctypes.c_void_p)]
 
 
-def _load():
-    global _lib
-    with _lock:
-        if _lib is None:
-            lib = ctypes.CDLL(build())
+def _declare(lib):
+    if True:
+        if True:
             P = ctypes.POINTER
             dp = ctypes.c_void_p
             op = P(_Op)
@@ -81,7 +95,7 @@ def _load():
             lib.ora_cg.argtypes = [op, dp, dp, ctypes.c_int, ctypes.c_double, dp, P(ctypes.c_int)]
             lib.ora_cg.restype = ctypes.c_int
             lib.ora_bicgstab.argtypes = [op, dp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
-                                         dp, P(ctypes.c_int), P(ctypes.c_int)]
+                                         dp, P(ctypes.c_int), P(ctypes.c_int), dp, dp]
             lib.ora_bicgstab.restype = ctypes.c_int
             lib.ora_cg_nb.argtypes = [op, dp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_int, dp,
                                       P(ctypes.c_int)]
@@ -90,8 +104,49 @@ def _load():
                                             dp, P(ctypes.c_int), P(ctypes.c_int)]
             lib.ora_bicgstab_b1.restype = ctypes.c_int
             lib.ora_grad_logk.argtypes = [op, dp, dp, dp]; lib.ora_grad_logk.restype = ctypes.c_int
-            _lib = lib
-    return _lib
+            lib.ora_set_threads.argtypes = [ctypes.c_int]; lib.ora_set_threads.restype = None
+            lib.ora_threads.argtypes = []; lib.ora_threads.restype = ctypes.c_int
+    return lib
+
+
+def _load():
+    """The sequential build, or the OpenMP build inside ``all_cores()``."""
+    key = "omp" if _use_omp else "seq"
+    with _lock:
+        lib = _libs.get(key)
+        if lib is None:
+            path = build()
+            if key == "omp":
+                if not os.path.exists(_OMP_PATH):
+                    raise RuntimeError("the OpenMP build of the oracle is not available (gcc without -fopenmp)")
+                path = _OMP_PATH
+            lib = _libs[key] = _declare(ctypes.CDLL(path))
+    return lib
+
+
+def have_all_cores() -> bool:
+    """True when the OpenMP build of the oracle exists."""
+    build()
+    return os.path.exists(_OMP_PATH)
+
+
+@contextlib.contextmanager
+def all_cores(threads: int = 0):
+    """Run the oracle calls inside the block on the OpenMP build: element-wise
+    loops (SpMV, residuals, vector updates, Jacobi sweeps, the gradient) on
+    ``threads`` host threads (0 = all cores this process may use), inner
+    products and Gauss-Seidel sweeps sequential.  Results are bitwise those of
+    the sequential build.  Yields the thread count in use."""
+    global _use_omp
+    prev = _use_omp
+    _use_omp = True
+    try:
+        lib = _load()
+        n = threads if threads > 0 else len(os.sched_getaffinity(0))
+        lib.ora_set_threads(int(n))
+        yield lib.ora_threads()
+    finally:
+        _use_omp = prev
 
 
 def _f64(a):
@@ -225,8 +280,25 @@ def bicgstab(A: Operator, b, x0=None, maxit=1000, tol=1e-10, restart_eps=1e-5):
     it = ctypes.c_int(0)
     nr = ctypes.c_int(0)
     st = _load().ora_bicgstab(A._ref(), _ptr(b), _ptr(x), int(maxit), float(tol), float(restart_eps),
-                              _ptr(h), ctypes.byref(it), ctypes.byref(nr))
+                              _ptr(h), ctypes.byref(it), ctypes.byref(nr), None, None)
     return x, it.value, st, h[: it.value + 1], nr.value
+
+
+def bicgstab_trace(A: Operator, b, x0=None, maxit=1000, tol=1e-10, restart_eps=1e-5):
+    """BiCGStab as ``bicgstab`` that also returns what decides its restarts:
+    (x, iters, status, hist, alpha, restart_at) with alpha[k] = r_k . r' after
+    iteration k (the value the restart test compares, alpha[0] = r_0 . r') and
+    restart_at the iterations after which a restart was taken."""
+    b = _f64(b).reshape(-1)
+    x = np.zeros(A.N) if x0 is None else _f64(x0).reshape(-1).copy()
+    h = _hist(maxit, True)
+    tr = np.full(maxit + 1, np.nan)
+    at = np.zeros(max(maxit, 1), dtype=np.int32)
+    it = ctypes.c_int(0)
+    nr = ctypes.c_int(0)
+    st = _load().ora_bicgstab(A._ref(), _ptr(b), _ptr(x), int(maxit), float(tol), float(restart_eps),
+                              _ptr(h), ctypes.byref(it), ctypes.byref(nr), _ptr(tr), _ptr(at))
+    return x, it.value, st, h[: it.value + 1], tr[: it.value + 1], [int(v) for v in at[: nr.value]]
 
 
 def cg_nb(A: Operator, b, x0=None, maxit=1000, tol=1e-10, paper_order=False):

@@ -46,6 +46,38 @@
 
 #include "oracle.h"
 
+/*
+ * Element-wise loops (every iteration writes its own entries and reads only
+ * data no iteration writes) may run on several threads when this file is
+ * compiled with OpenMP: the result is bitwise that of the sequential loop.
+ * Inner products, the Gauss-Seidel sweeps and everything else stay
+ * sequential.  The parity checker is built without OpenMP.
+ */
+#ifdef _OPENMP
+#include <omp.h>
+#define ORA_PARALLEL_FOR _Pragma("omp parallel for schedule(static)")
+#else
+#define ORA_PARALLEL_FOR
+#endif
+
+void ora_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int ora_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
 /* ------------------------------------------------------------------------ */
 /* Operator rows                                                            */
 /* ------------------------------------------------------------------------ */
@@ -150,6 +182,7 @@ int ora_row(const ora_op *A, int64_t idx, double *diag, int64_t nb[ORA_MAXNB], d
 void ora_spmv(const ora_op *A, const double *x, double *y)
 {
     int64_t N = ora_size(A);
+    ORA_PARALLEL_FOR
     for (int64_t i = 0; i < N; i++) {
         double dg, c[ORA_MAXNB];
         int64_t nb[ORA_MAXNB];
@@ -206,6 +239,7 @@ void ora_residual(const ora_op *A, const double *b, const double *x, double *r)
 {
     int64_t N = ora_size(A);
     ora_spmv(A, x, r);
+    ORA_PARALLEL_FOR
     for (int64_t i = 0; i < N; i++) r[i] = b[i] - r[i];
 }
 
@@ -252,6 +286,7 @@ int ora_jacobi(const ora_op *A, const double *b, double *x, int maxit, double to
             if (rr <= tol) { status = ORA_OK; break; }
         }
         if (k == maxit) break;
+        ORA_PARALLEL_FOR
         for (int64_t i = 0; i < N; i++) {
             double dg, c[ORA_MAXNB];
             int64_t nb[ORA_MAXNB];
@@ -339,6 +374,7 @@ int ora_cg(const ora_op *A, const double *b, double *x, int maxit, double tol,
     int it = 0;
     double bn = sqrt(ora_dot(N, b, b));
     if (bn == 0.0) {
+        ORA_PARALLEL_FOR
         for (int64_t i = 0; i < N; i++) x[i] = 0.0;
         if (hist) hist[0] = 0.0;
         *iters = 0;
@@ -346,6 +382,7 @@ int ora_cg(const ora_op *A, const double *b, double *x, int maxit, double tol,
         return ORA_OK;
     }
     ora_residual(A, b, x, r);
+    ORA_PARALLEL_FOR
     for (int64_t i = 0; i < N; i++) p[i] = r[i];
     double rr = ora_dot(N, r, r);
     if (hist) hist[0] = sqrt(rr) / bn;
@@ -355,13 +392,16 @@ int ora_cg(const ora_op *A, const double *b, double *x, int maxit, double tol,
         double pw = ora_dot(N, p, w);
         if (!(pw > 0.0)) { status = ORA_BREAKDOWN; break; }
         double alpha = rr / pw;
+        ORA_PARALLEL_FOR
         for (int64_t i = 0; i < N; i++) x[i] += alpha * p[i];
+        ORA_PARALLEL_FOR
         for (int64_t i = 0; i < N; i++) r[i] -= alpha * w[i];
         double rr_new = ora_dot(N, r, r);
         it++;
         if (hist) hist[it] = sqrt(rr_new) / bn;
         if (sqrt(rr_new) / bn <= tol) { status = ORA_OK; break; }
         double beta = rr_new / rr;
+        ORA_PARALLEL_FOR
         for (int64_t i = 0; i < N; i++) p[i] = r[i] + beta * p[i];
         rr = rr_new;
     }
@@ -378,7 +418,8 @@ int ora_cg(const ora_op *A, const double *b, double *x, int maxit, double tol,
 /* ------------------------------------------------------------------------ */
 
 int ora_bicgstab(const ora_op *A, const double *b, double *x, int maxit, double tol,
-                 double restart_eps, double *hist, int *iters, int *restarts)
+                 double restart_eps, double *hist, int *iters, int *restarts,
+                 double *trace, int *restart_at)
 {
     int64_t N = ora_size(A);
     double *r = (double *)malloc((size_t)N * sizeof(double));
@@ -392,6 +433,7 @@ int ora_bicgstab(const ora_op *A, const double *b, double *x, int maxit, double 
     if (!r || !rs || !p || !v || !s || !t) { status = -1; goto done; }
     double bn = sqrt(ora_dot(N, b, b));
     if (bn == 0.0) {
+        ORA_PARALLEL_FOR
         for (int64_t i = 0; i < N; i++) x[i] = 0.0;
         if (hist) hist[0] = 0.0;
         status = ORA_OK;
@@ -402,18 +444,23 @@ int ora_bicgstab(const ora_op *A, const double *b, double *x, int maxit, double 
     if (hist) hist[0] = sqrt(beta_r) / bn;
     if (sqrt(beta_r) / bn <= tol) { status = ORA_OK; goto done; }
     double rn = sqrt(beta_r);
+    ORA_PARALLEL_FOR
     for (int64_t i = 0; i < N; i++) rs[i] = r[i] / rn;
     double alpha_n = ora_dot(N, r, rs);
+    if (trace) trace[0] = alpha_n;
+    ORA_PARALLEL_FOR
     for (int64_t i = 0; i < N; i++) p[i] = r[i];
     while (it < maxit) {
         ora_spmv(A, p, v);
         double alpha_d = ora_dot(N, v, rs);
         if (alpha_d == 0.0 || !isfinite(alpha_d)) { status = ORA_BREAKDOWN; break; }
         double alpha = alpha_n / alpha_d;
+        ORA_PARALLEL_FOR
         for (int64_t i = 0; i < N; i++) s[i] = r[i] - alpha * v[i];
         double ss = ora_dot(N, s, s);
         it++;
         if (sqrt(ss) / bn <= tol) {
+            ORA_PARALLEL_FOR
             for (int64_t i = 0; i < N; i++) x[i] += alpha * p[i];
             if (hist) hist[it] = sqrt(ss) / bn;
             status = ORA_OK;
@@ -425,21 +472,28 @@ int ora_bicgstab(const ora_op *A, const double *b, double *x, int maxit, double 
         if (tt == 0.0 || !isfinite(tt)) { status = ORA_BREAKDOWN; break; }
         double omega = ts / tt;
         if (omega == 0.0) { status = ORA_BREAKDOWN; break; }
+        ORA_PARALLEL_FOR
         for (int64_t i = 0; i < N; i++) x[i] += alpha * p[i] + omega * s[i];
+        ORA_PARALLEL_FOR
         for (int64_t i = 0; i < N; i++) r[i] = s[i] - omega * t[i];
         double alpha_n_new = ora_dot(N, r, rs);
         beta_r = ora_dot(N, r, r);
         if (hist) hist[it] = sqrt(beta_r) / bn;
+        if (trace) trace[it] = alpha_n_new;      /* the value the restart test reads */
         if (sqrt(beta_r) / bn <= tol) { status = ORA_OK; break; }
         if (restart_eps > 0.0 && sqrt(fabs(alpha_n_new)) < restart_eps) {
             /* restart: new search direction and new shadow residual */
             double rnorm = sqrt(beta_r);
+            ORA_PARALLEL_FOR
             for (int64_t i = 0; i < N; i++) p[i] = r[i];
+            ORA_PARALLEL_FOR
             for (int64_t i = 0; i < N; i++) rs[i] = r[i] / rnorm;
             alpha_n = ora_dot(N, r, rs);
+            if (restart_at) restart_at[nrestart] = it;
             nrestart++;
         } else {
             double beta = alpha_n_new / (alpha_d * omega);
+            ORA_PARALLEL_FOR
             for (int64_t i = 0; i < N; i++) p[i] = r[i] + beta * (p[i] - omega * v[i]);
             alpha_n = alpha_n_new;
         }
@@ -478,6 +532,7 @@ int ora_cg_nb(const ora_op *A, const double *b, double *x, int maxit, double tol
     if (!r || !p || !Ap || !Ar) { status = -1; goto done; }
     double bn = sqrt(ora_dot(N, b, b));
     if (bn == 0.0) {
+        ORA_PARALLEL_FOR
         for (int64_t i = 0; i < N; i++) x[i] = 0.0;
         if (hist) hist[0] = 0.0;
         status = ORA_OK;
@@ -485,6 +540,7 @@ int ora_cg_nb(const ora_op *A, const double *b, double *x, int maxit, double tol
     }
     /* r0 = b - A x0, p0 = r0, alpha_0 = (r0.r0) / ((A p0).p0) */
     ora_residual(A, b, x, r);
+    ORA_PARALLEL_FOR
     for (int64_t i = 0; i < N; i++) p[i] = r[i];
     ora_spmv(A, p, Ap);
     double an = ora_dot(N, r, r);
@@ -495,14 +551,18 @@ int ora_cg_nb(const ora_op *A, const double *b, double *x, int maxit, double tol
     double alpha = an / ad;
     for (it = 1; it <= maxit; it++) {
         if (paper_order && sqrt(an) / bn <= tol && it > 1) { it--; status = ORA_OK; break; }
+        ORA_PARALLEL_FOR
         for (int64_t i = 0; i < N; i++) r[i] -= alpha * Ap[i];
         double an_new = ora_dot(N, r, r);
         double beta = an_new / an;
         ora_spmv(A, r, Ar);
+        ORA_PARALLEL_FOR
         for (int64_t i = 0; i < N; i++) Ap[i] = Ar[i] + beta * Ap[i];
+        ORA_PARALLEL_FOR
         for (int64_t i = 0; i < N; i++) p[i] = r[i] + beta * p[i];
         double ad_new = ora_dot(N, Ap, p);
         double c = an * an / (ad * an_new);
+        ORA_PARALLEL_FOR
         for (int64_t i = 0; i < N; i++) x[i] += c * (p[i] - r[i]);
         if (hist) hist[it] = sqrt(an_new) / bn;
         an = an_new;
@@ -514,6 +574,7 @@ int ora_cg_nb(const ora_op *A, const double *b, double *x, int maxit, double tol
     if (it > maxit) it = maxit;
     if (paper_order && status != ORA_BREAKDOWN) {
         /* the printed final step x = x_l + alpha_l p_l */
+        ORA_PARALLEL_FOR
         for (int64_t i = 0; i < N; i++) x[i] += alpha * p[i];
         if (status != ORA_OK && sqrt(an) / bn <= tol) status = ORA_OK;
     }
@@ -546,6 +607,7 @@ int ora_bicgstab_b1(const ora_op *A, const double *b, double *x, int maxit, doub
     if (!r || !rs || !p || !Ap || !s || !As) { status = -1; goto done; }
     double bn = sqrt(ora_dot(N, b, b));
     if (bn == 0.0) {
+        ORA_PARALLEL_FOR
         for (int64_t i = 0; i < N; i++) x[i] = 0.0;
         if (hist) hist[0] = 0.0;
         status = ORA_OK;
@@ -555,39 +617,50 @@ int ora_bicgstab_b1(const ora_op *A, const double *b, double *x, int maxit, doub
     double beta_j = ora_dot(N, r, r);
     if (hist) hist[0] = sqrt(beta_j) / bn;
     if (sqrt(beta_j) / bn <= tol) { status = ORA_OK; goto done; }
+    ORA_PARALLEL_FOR
     for (int64_t i = 0; i < N; i++) rs[i] = r[i] / sqrt(beta_j);
     double an = ora_dot(N, r, rs);
+    ORA_PARALLEL_FOR
     for (int64_t i = 0; i < N; i++) p[i] = r[i];
     while (it < maxit) {
         ora_spmv(A, p, Ap);
         double ad = ora_dot(N, Ap, rs);
         if (ad == 0.0 || !isfinite(ad)) { status = ORA_BREAKDOWN; break; }
         double alpha = an / ad;
+        ORA_PARALLEL_FOR
         for (int64_t i = 0; i < N; i++) s[i] = r[i] - alpha * Ap[i];
         ora_spmv(A, s, As);
         double num = ora_dot(N, As, s), den = ora_dot(N, As, As);
         if (den == 0.0 || !isfinite(den)) { status = ORA_BREAKDOWN; break; }
         double omega = num / den;
+        ORA_PARALLEL_FOR
         for (int64_t i = 0; i < N; i++) x[i] += alpha * p[i];            /* x_j+1/2 */
         it++;
         if (sqrt(beta_j) / bn <= tol) {                                  /* late test */
+            ORA_PARALLEL_FOR
             for (int64_t i = 0; i < N; i++) x[i] += omega * s[i];        /* final step */
             status = ORA_OK;
             break;
         }
+        ORA_PARALLEL_FOR
         for (int64_t i = 0; i < N; i++) x[i] += omega * s[i];
+        ORA_PARALLEL_FOR
         for (int64_t i = 0; i < N; i++) r[i] = s[i] - omega * As[i];
         double an_new = ora_dot(N, r, rs);
         beta_j = ora_dot(N, r, r);
         if (hist) hist[it] = sqrt(beta_j) / bn;
+        ORA_PARALLEL_FOR
         for (int64_t i = 0; i < N; i++) Ap[i] = p[i] - omega * Ap[i];   /* p_j+1/2, stored in Ap */
         if (restart_eps > 0.0 && sqrt(fabs(an_new)) < restart_eps) {
+            ORA_PARALLEL_FOR
             for (int64_t i = 0; i < N; i++) p[i] = r[i];
+            ORA_PARALLEL_FOR
             for (int64_t i = 0; i < N; i++) rs[i] = r[i] / sqrt(beta_j);
             an = ora_dot(N, r, rs);
             nrestart++;
         } else {
             double c = an_new / (ad * omega);
+            ORA_PARALLEL_FOR
             for (int64_t i = 0; i < N; i++) p[i] = r[i] + c * Ap[i];
             an = an_new;
         }
@@ -613,6 +686,7 @@ int ora_grad_logk(const ora_op *A, const double *u, const double *lam, double *g
 {
     if (A->kind != ORA_DIFFUSION) return -1;
     int64_t N = ora_size(A);
+    ORA_PARALLEL_FOR
     for (int64_t i = 0; i < N; i++) {
         int64_t x[3] = {0, 0, 0};
         coords(A, i, x);

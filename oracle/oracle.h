@@ -35,12 +35,19 @@ int ora_gauss_seidel(const ora_op *A, const double *b, double *x, int maxit, dou
                      int mode, double *hist, int *iters);
 int ora_cg(const ora_op *A, const double *b, double *x, int maxit, double tol,
            double *hist, int *iters);
+/* trace (may be NULL, maxit + 1 entries): trace[k] = r_k . r', the value the
+ * restart test reads after iteration k (trace[0] = r_0 . r').  restart_at (may
+ * be NULL, maxit entries): the iterations after which a restart was taken. */
 int ora_bicgstab(const ora_op *A, const double *b, double *x, int maxit, double tol,
-                 double restart_eps, double *hist, int *iters, int *restarts);
+                 double restart_eps, double *hist, int *iters, int *restarts,
+                 double *trace, int *restart_at);
 int ora_cg_nb(const ora_op *A, const double *b, double *x, int maxit, double tol,
               int paper_order, double *hist, int *iters);
 int ora_bicgstab_b1(const ora_op *A, const double *b, double *x, int maxit, double tol,
                     double restart_eps, double *hist, int *iters, int *restarts);
 int ora_grad_logk(const ora_op *A, const double *u, const double *lam, double *g);
+/* Threads of the element-wise loops (OpenMP build only; 1 otherwise). */
+void ora_set_threads(int n);
+int ora_threads(void);
 
 #endif

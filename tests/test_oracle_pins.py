@@ -390,6 +390,73 @@ def test_bicgstab_restart_fires_and_both_converge():
         assert np.linalg.norm(x - ref) <= 1e-9 * np.linalg.norm(ref)
 
 
+def test_bicgstab_trace_is_the_shadow_residual_product():
+    # trace[k] = r_k . r' with r' = r_0 / ||r_0|| before any restart; computed
+    # here from the iterates with a dense matrix and numpy, not the oracle's
+    # recursion.  With restarts on every iteration (eps' = 1e3) the shadow
+    # residual of iteration k + 1 is r_k / ||r_k||.
+    shape = (9, 7, 5)
+    beta = inputs.upwind_beta(shape, 0.5)
+    A = oracle.Operator(shape, oracle.UPWIND, beta)
+    M = upwind_dense(shape, beta)
+    b = inputs.rhs_uniform(shape, 8)
+    r0 = b.copy()
+    rs = r0 / np.linalg.norm(r0)
+    _, it, _, _, tr, at = oracle.bicgstab_trace(A, b, tol=1e-12, maxit=400, restart_eps=0.0)
+    assert at == [] and np.isclose(tr[0], np.linalg.norm(r0), rtol=1e-14)
+    for k in (1, 2, 3, 5):
+        xk = oracle.bicgstab(A, b, tol=0.0, maxit=k, restart_eps=0.0)[0]
+        assert np.isclose(tr[k], (b - M @ xk) @ rs, rtol=1e-9, atol=1e-12 * np.linalg.norm(r0))
+    _, it, _, _, tr, at = oracle.bicgstab_trace(A, b, tol=1e-12, maxit=400, restart_eps=1e3)
+    assert at == list(range(1, it))
+    for k in (1, 2, 4):
+        xk = oracle.bicgstab(A, b, tol=0.0, maxit=k, restart_eps=1e3)[0]
+        xk1 = oracle.bicgstab(A, b, tol=0.0, maxit=k + 1, restart_eps=1e3)[0]
+        rk = b - M @ xk
+        assert np.isclose(tr[k + 1], (b - M @ xk1) @ (rk / np.linalg.norm(rk)), rtol=1e-7,
+                          atol=1e-11 * np.linalg.norm(r0))
+
+
+def test_bicgstab_restart_iterations_follow_the_threshold():
+    shape = (70, 45)
+    A = oracle.Operator(shape, oracle.UPWIND, inputs.upwind_beta(shape, 0.5))
+    b = inputs.uniform_pm1(12, 1, A.N)
+    _, it, st, _, tr, at = oracle.bicgstab_trace(A, b, tol=1e-10, maxit=5000, restart_eps=1e-5)
+    _, it2, _, _, nr = oracle.bicgstab(A, b, tol=1e-10, maxit=5000, restart_eps=1e-5)
+    assert st == oracle.OK and it == it2 and len(at) == nr > 0
+    below = [k for k in range(1, it) if math.sqrt(abs(tr[k])) < 1e-5]
+    assert below == at
+
+
+def test_all_cores_build_is_bitwise_the_sequential_one():
+    if not oracle.have_all_cores():
+        pytest.skip("gcc without OpenMP")
+    shape = (33, 21, 17)
+    N = int(np.prod(shape))
+    k = np.exp(inputs.normal(3, inputs.STREAM_K, N, 1.0))
+    ops = [oracle.Operator(shape), oracle.Operator(shape, oracle.UPWIND, inputs.upwind_beta(shape, 0.5)),
+           oracle.Operator(shape, oracle.DIFFUSION, k=k)]
+    b = inputs.uniform_pm1(4, 1, N)
+
+    def run():
+        out = []
+        for A in ops:
+            out.append(A.spmv(b))
+            out.append(oracle.jacobi(A, b, maxit=7)[0])
+            out.append(oracle.bicgstab(A, b, tol=1e-10, maxit=500)[0])
+            out.append(oracle.cg_nb(ops[0], b, tol=1e-10, maxit=500)[0])
+        out.append(oracle.cg(ops[2], b, tol=1e-10, maxit=2000)[0])
+        out.append(oracle.grad_logk(ops[2], out[0], out[1]))
+        return out
+
+    seq = run()
+    with oracle.all_cores(4) as n:
+        assert n == 4
+        par = run()
+    for a, c in zip(seq, par):
+        assert np.array_equal(a, c)
+
+
 # --------------------------------------------------------------------------
 # HPCG 7- and 27-point systems (section 4.1)
 # --------------------------------------------------------------------------
