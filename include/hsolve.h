@@ -114,6 +114,16 @@ typedef struct {
                                constant-coefficient 3-D 7-point operators with
                                tol = 0; the iterates are bitwise those of single
                                sweeps.  Other cases run one sweep per pass.     */
+    double *alpha_trace;    /* BiCGStab diagnostics (hs_bicgstab only): host
+                               array of maxit + 1 doubles, may be NULL.  Entry
+                               k receives r_k . r' after iteration k, the value
+                               whose square root Algorithm 2's restart test
+                               compares with restart_eps (entry 0: r_0 . r').
+                               Entries beyond res.iters are left untouched.   */
+    int *restart_iters;     /* BiCGStab diagnostics: host array of maxit ints,
+                               may be NULL; receives the iterations after which
+                               a restart was taken, in order (res.restarts of
+                               them).                                          */
 } hs_opts;
 
 typedef struct {
@@ -220,8 +230,9 @@ hs_status hs_cg(const hs_op *A, hs_dtype dtype, const void *b, void *x, double t
 /* CG-NB, the paper's nonblocking CG (section 3.2, Algorithm 1): the SpMV is
  * applied to r_j and A p_j = A r_j + beta_j A p_j-1 follows by recurrence.
  * One fused pass and ONE reduce-barrier per iteration: the denominator
- * (A p_j).p_j is expanded as r_j.A r_j - beta_j (r_j.r_j) / alpha_j-1 (equal in
- * exact arithmetic for symmetric A), so r.r and r.A r are reduced together.
+ * (A p_j).p_j is expanded as r_j.A r_j + 2 beta_j r_j.A p_j-1
+ * + beta_j^2 (A p_j-1).p_j-1 (exact for symmetric A), so r.r, r.A r and
+ * r.A p_j-1 are reduced together before beta_j is known.
  * A must be symmetric positive definite.  x is updated as x_j-1 + alpha_j-1
  * p_j-1 (Algorithm 1's x_j-1 + c (p_j - r_j) with c (p_j - r_j) = alpha_j-1
  * p_j-1).  Workspace: hs_workspace_size(A, HS_SOLVER_CG_NB, ...). */
@@ -284,7 +295,10 @@ hs_status hs_diffusion_grad_logk(const hs_op *A, const double *u, const double *
  *     constant-coefficient operator that is about 500 k unknowns.
  *   - The first call on a device, with that device current, looks up the
  *     array's device address (cudaGetSymbolAddress) and keeps it: make that
- *     first call before any stream capture on that device.
+ *     first call before any stream capture on that device.  Resetting the
+ *     device (cudaDeviceReset) while the library is loaded is not supported.
+ *   - `stream` must belong to the current device (HS_ERR_INVALID otherwise):
+ *     the kept address is that device's.
  *   - All calls on a device share the one array and it keeps the previous
  *     call's contents; the solver initialises what it reads first.  Calls that
  *     may overlap on the GPU (other streams, other host threads) race on the

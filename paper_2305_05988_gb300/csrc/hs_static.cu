@@ -19,6 +19,10 @@ static __device__ __align__(256) unsigned char g_static_scratch[HS_STATIC_SCRATC
 namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
+// Device address of the scratch array per device, looked up once per process
+// on the first call with that device current.  A device reset
+// (cudaDeviceReset) while the library is loaded is not supported: the kept
+// address would then belong to the destroyed context.
 void* g_scratch_dev[kMaxDevices] = {nullptr};
 }  // namespace
 
@@ -49,6 +53,17 @@ extern "C" hs_status hs_cg_static(const hs_op* A, hs_dtype dtype, const void* b,
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return hs::cuda_fail(e, "hs_cg_static: cudaGetDevice");
+  if (stream) {
+    // The scratch address belongs to the current device: a stream of another
+    // device would make the solve read memory of the wrong GPU.
+    int sdev = -1;
+    e = cudaStreamGetDevice((cudaStream_t)stream, &sdev);
+    if (e != cudaSuccess) return hs::cuda_fail(e, "hs_cg_static: cudaStreamGetDevice");
+    if (sdev != dev) {
+      hs::set_error("hs_cg_static: the stream belongs to device %d but device %d is current", sdev, dev);
+      return HS_ERR_INVALID;
+    }
+  }
   if (dev < 0 || dev >= kMaxDevices) {
     hs::set_error("hs_cg_static: device index %d not supported", dev);
     return HS_ERR_INVALID;

@@ -5,8 +5,10 @@ plug-in whose host application owns all GPU memory through its own pool).  The
 test calls it through the C ABI twice in a row -- the second call inherits the
 first call's leftovers in the shared static scratch -- and checks both results
 against hs_cg with a caller-allocated workspace, within the CG parity
-tolerance (1e-8 relative), plus the rejection of a problem too large for the
-scratch.  This file is collected last so that a failure here cannot hide any
+tolerance (1e-8 relative), and against the FP64 oracle's CG at the same
+iteration count (1e-8 relative), plus the rejection of a problem too large for
+the scratch and of a stream that belongs to another device than the current
+one (checked only where a second GPU exists).  This file is collected last so that a failure here cannot hide any
 other test's result.
 """
 import ctypes
@@ -14,6 +16,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 from paper_2305_05988_gb300 import _lib, inputs
 
 torch = pytest.importorskip("torch")
@@ -40,6 +43,8 @@ def test_cg_static_matches_cg_on_two_calls_in_a_row(shape):
     b = torch.from_numpy(inputs.uniform_pm1(21, 1, N)).cuda()
     x_ref, info = hs.cg(A, b, tol=1e-10, maxit=5000)
     assert info.status == "OK"
+    x_o, it_o, st_o, _ = oracle.cg(oracle.Operator(shape), b.cpu().numpy(), tol=0.0, maxit=info.iters)
+    assert it_o == info.iters
     for call in range(2):
         x = torch.zeros(N, dtype=torch.float64, device="cuda")
         status, res, hist = _solve_static(A, b, x, 1e-10, 5000)
@@ -48,6 +53,8 @@ def test_cg_static_matches_cg_on_two_calls_in_a_row(shape):
         err = (torch.linalg.norm(x - x_ref) / torch.linalg.norm(x_ref)).item()
         assert err <= 1e-8, (call, err)
         assert np.allclose(hist, info.history, rtol=1e-8, atol=0)
+        xh = x.cpu().numpy()
+        assert np.linalg.norm(xh - x_o) <= 1e-8 * np.linalg.norm(x_o), call
 
 
 def test_cg_static_rejects_problems_beyond_its_scratch():
@@ -60,3 +67,18 @@ def test_cg_static_rejects_problems_beyond_its_scratch():
     msg = _lib.load().hs_last_error().decode()
     assert "static scratch" in msg and str(_lib.HS_STATIC_SCRATCH_BYTES) in msg
     assert torch.count_nonzero(x).item() == 0
+
+
+def test_cg_static_rejects_a_stream_of_another_device():
+    if torch.cuda.device_count() < 2:
+        pytest.skip("needs a second GPU")
+    A = hs.Operator.laplacian((40, 30))
+    b = torch.ones(A.N, dtype=torch.float64, device="cuda:0")
+    x = torch.zeros_like(b)
+    with torch.cuda.device(1):
+        other = torch.cuda.Stream()
+    lib = _lib.load()
+    res = _lib.hs_result()
+    status = lib.hs_cg_static(A._op, _lib.HS_F64, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                              1e-8, 100, None, ctypes.c_void_p(other.cuda_stream), ctypes.byref(res), None)
+    assert status == _lib.HS_ERR_INVALID
