@@ -45,7 +45,9 @@ class hs_opts(ctypes.Structure):
                 ("tile_planes", ctypes.c_int),
                 ("max_blocks", ctypes.c_int),
                 ("paper_order", ctypes.c_int),
-                ("sweeps_per_pass", ctypes.c_int)]
+                ("sweeps_per_pass", ctypes.c_int),
+                ("alpha_trace", ctypes.POINTER(ctypes.c_double)),
+                ("restart_iters", ctypes.POINTER(ctypes.c_int))]
 
 
 class hs_result(ctypes.Structure):

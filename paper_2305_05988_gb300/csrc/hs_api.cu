@@ -59,7 +59,9 @@ size_t ws_bytes_for(const hs_op* A, hs_solver s, hs_dtype dt, int maxit) {
     case HS_SOLVER_MIXED: return 0;  // sized by mixed_ws_bytes with the options
     case HS_SOLVER_CG_NB: nvec = 7; break;  // r, w, q ping-pong pairs and p
   }
-  return common_bytes(maxit) + nvec * vec + vark_coef_bytes(A, dt);
+  size_t extra = 0;
+  if (s == HS_SOLVER_BICGSTAB) extra = (bicgstab_trace_len(maxit) * sizeof(double) + 255) & ~(size_t)255;
+  return common_bytes(maxit) + nvec * vec + vark_coef_bytes(A, dt) + extra;
 }
 
 static hs_opts default_opts() {

@@ -4,19 +4,24 @@
 // Algorithm 1 applies the SpMV to r_j instead of p_j and obtains A p_j by the
 // recurrence q_j = A p_j = w_j + beta_j q_j-1 with w_j = A r_j, so that the
 // reduction of alpha_n,j = r_j.r_j can overlap the SpMV.  On the GPU the
-// iteration's second reduction, alpha_d,j = q_j.p_j, is merged into the first:
-// for symmetric A,
+// iteration's second reduction, alpha_d,j = q_j.p_j, is merged into the first
+// by expanding it over the vectors one pass sees before beta_j is known:
 //   q_j.p_j = (w_j + beta_j q_j-1).(r_j + beta_j p_j-1)
-//           = r_j.w_j - beta_j alpha_n,j / alpha_j-1
-// in exact arithmetic (r_j is orthogonal to r_j-1 and to p_j-1, and
-// r_j.q_j-1 = -alpha_n,j / alpha_j-1), so one pass computes everything an
-// iteration needs and one barrier ends it:
+//           = r_j.w_j + 2 beta_j r_j.q_j-1 + beta_j^2 q_j-1.p_j-1
+// (w_j.p_j-1 = r_j.A p_j-1 = r_j.q_j-1 for symmetric A; q_j-1.p_j-1 is the
+// previous alpha_d).  The three terms come from the vectors themselves, with
+// no appeal to the orthogonality of r_j to p_j-1 that holds only in exact
+// arithmetic (the shorter form r_j.w_j - beta_j alpha_n,j / alpha_j-1 relies
+// on it and converged measurably later than Algorithm 1 on coefficient-
+// contrast problems), so one pass computes everything an iteration needs and
+// one barrier ends it:
 //
 //   source, every node the stencil reads (halo included):
 //     q_k = w_k + beta_k q_k-1,  r_k+1 = r_k - alpha_k q_k   (stored if owned)
 //   sink, owned nodes:
 //     w_k+1 = A r_k+1,  p_k = r_k + beta_k p_k-1,  x_k+1 = x_k + alpha_k p_k,
-//     partial sums r_k+1.r_k+1 and r_k+1.w_k+1
+//     partial sums r_k+1.r_k+1, r_k+1.w_k+1 and r_k+1.q_k (q_k formed again
+//     from w_k and q_k-1, bitwise as the source formed it)
 //
 // r, w and q are ping-ponged (a tile reads its neighbours' old values while
 // they write new ones); p and x are updated in place (owned nodes only).
@@ -73,7 +78,8 @@ struct CgnbSrc {
   }
 };
 
-// w_k+1 = S r_k+1 ; p_k = r_k + beta p_k-1 ; x += (alpha / sigma) p_k ; r.r, r.w.
+// w_k+1 = S r_k+1 ; p_k = r_k + beta p_k-1 ; x += (alpha / sigma) p_k ;
+// r.r, r.w, r.q_k.
 template <typename T, int OPK, int NDIM>
 struct CgnbSink {
   static constexpr bool kBox = OPK == OP_BOX27;
@@ -81,16 +87,19 @@ struct CgnbSink {
   Geom g;
   T* wnew;
   const T* rold;
+  const T* wk;      // w_k and q_k-1: q_k = w_k + beta q_k-1
+  const T* qkm1;
   T* p;
   T* x;
   T beta, ax;
-  double acc[2];
+  double acc[3];
   struct Raw {
     OpRaw<T, OPK> o;
-    T r, p, x;
+    T r, p, x, w, q;
   };
   __device__ __forceinline__ Raw fetch(long long idx, int i, int j, int k) const {
-    return Raw{op_fetch<T, OPK, NDIM>(cf, g, idx, i, j, k), __ldcg(rold + idx), __ldcg(p + idx), __ldcg(x + idx)};
+    return Raw{op_fetch<T, OPK, NDIM>(cf, g, idx, i, j, k), __ldcg(rold + idx), __ldcg(p + idx), __ldcg(x + idx),
+               __ldcg(wk + idx), __ldcg(qkm1 + idx)};
   }
   __device__ __forceinline__ void operator()(long long idx, const Nbr<T>& nb, const Raw& q, int, int, int) {
     const T wv = op_apply<T, OPK, NDIM>(cf, q.o, nb);
@@ -98,8 +107,11 @@ struct CgnbSink {
     const T pv = fma(beta, q.p, q.r);
     p[idx] = pv;
     x[idx] = fma(ax, pv, q.x);
-    acc[0] += widen(nb.c) * widen(nb.c);
-    acc[1] += widen(nb.c) * widen(wv);
+    const T qk = fma(beta, q.q, q.w);
+    const double rc = widen(nb.c);
+    acc[0] += rc * rc;
+    acc[1] += rc * widen(wv);
+    acc[2] += rc * widen(qk);
   }
 };
 
@@ -174,18 +186,18 @@ __global__ void __launch_bounds__(512) k_cg_nb(CgnbArgs<T> a) {
     team_finish(tm, isfinite(d0[0]) ? DS_BREAKDOWN : DS_NONFINITE, 0, rel);
     return;
   }
-  double alpha = an / d0[0], beta = 0.0;
+  double alpha = an / d0[0], beta = 0.0, ad_prev = d0[0];
   int it = 0, status = DS_MAXIT, cur = 0;
   while (it < a.maxit) {
     // ---- the iteration's single pass (buffers: cur = k, 1 - cur = k + 1 / k - 1)
     CgnbSrc<T> src{a.w[cur], a.q[1 - cur], a.r[cur], a.q[cur], a.r[1 - cur], (T)alpha, (T)beta};
-    CgnbSink<T, OPK, NDIM> sink{a.cf, a.g, a.w[1 - cur], a.r[cur], a.p, a.x, (T)beta, (T)(alpha / a.sigma),
-                                {0.0, 0.0}};
+    CgnbSink<T, OPK, NDIM> sink{a.cf,    a.g,        a.w[1 - cur], a.r[cur], a.w[cur], a.q[1 - cur],
+                                a.p,     a.x,        (T)beta,      (T)(alpha / a.sigma), {0.0, 0.0, 0.0}};
     for (int item = tm.rank; item < a.tl.items(); item += tm.size)
       zmarch_item<T, NDIM, 1>(a.g, a.tl, item, sm, src, sink);
-    block_sum<2>(sink.acc, sh);
-    double rw[2];
-    if (!team_reduce<2>(tm, sink.acc, rw, sh)) return;
+    block_sum<3>(sink.acc, sh);
+    double rw[3];
+    if (!team_reduce<3>(tm, sink.acc, rw, sh)) return;
     it++;
     cur = 1 - cur;
     const double an_new = rw[0];
@@ -196,7 +208,7 @@ __global__ void __launch_bounds__(512) k_cg_nb(CgnbArgs<T> a) {
       break;
     }
     const double beta_new = an_new / an;
-    const double ad = rw[1] - beta_new * an_new / alpha;   // q.p expanded
+    const double ad = rw[1] + beta_new * (2.0 * rw[2] + beta_new * ad_prev);   // q.p expanded
     if (rel <= a.tol) {
       status = DS_CONVERGED;
       if (a.paper_order) {
@@ -218,6 +230,7 @@ __global__ void __launch_bounds__(512) k_cg_nb(CgnbArgs<T> a) {
     beta = beta_new;
     alpha = an_new / ad;
     an = an_new;
+    ad_prev = ad;
   }
   team_finish(tm, status, it, rel);
 }

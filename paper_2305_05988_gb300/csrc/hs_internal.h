@@ -107,6 +107,10 @@ struct SolveArgs {
   cudaStream_t stream;
 };
 
+// Doubles of the BiCGStab restart trace section (r_k . r' and a restart flag
+// for k = 0 .. maxit, plus one spare pair).
+inline size_t bicgstab_trace_len(int maxit) { return 2 * ((size_t)maxit + 2); }
+
 // Per-solver workspace size (bytes), excluding nothing: callers add nothing.
 size_t ws_bytes_for(const hs_op* A, hs_solver s, hs_dtype dt, int maxit);
 

@@ -11,6 +11,8 @@
 #include <cmath>
 #include <type_traits>
 
+#include <vector>
+
 #include "hs_internal.h"
 #include "hs_krylov.cuh"
 
@@ -795,8 +797,10 @@ static hs_status cg_core(const hs_op* A, const Coef<T>& cf, double sigma, const 
 
 template <typename T, int OPK, int NDIM>
 static hs_status bicgstab_core(const hs_op* A, const Coef<T>& cf, double sigma, const T* b, T* x, double tol,
-                               int maxit, const Common& cm, T* const v[8], const hs_opts& o, cudaStream_t st) {
+                               int maxit, const Common& cm, T* const v[8], const hs_opts& o, cudaStream_t st,
+                               double* trace = nullptr) {
   BiArgs<T> a = {};
+  a.trace = trace;
   a.g = geom_of(A);
   a.cf = cf;
   a.sigma = sigma;
@@ -866,6 +870,22 @@ hs_status run_cg(const SolveArgs& sa, hs_result* res, double* hist) {
 }
 
 // ---- BiCGStab ---------------------------------------------------------------------
+// Copies the device restart trace (r_k . r' and a restart flag per iteration)
+// into the caller's alpha_trace / restart_iters host arrays.
+static hs_status copy_bicgstab_trace(const double* trace, int maxit, int iters, const hs_opts& o, cudaStream_t st) {
+  const int n = std::min(std::max(iters, 0), maxit) + 1;
+  std::vector<double> h((size_t)2 * n);
+  cudaError_t e = cudaMemcpyAsync(h.data(), trace, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "restart trace read-back");
+  int q = 0;
+  for (int k = 0; k < n; k++) {
+    if (o.alpha_trace) o.alpha_trace[k] = h[2 * k];
+    if (k > 0 && h[2 * k + 1] != 0.0 && o.restart_iters && q < maxit) o.restart_iters[q++] = k;
+  }
+  return HS_OK;
+}
+
 hs_status run_bicgstab(const SolveArgs& sa, hs_result* res, double* hist) {
   return dispatch(sa.dtype, opkind_of(sa.A), sa.A->ndim, [&](auto tag) -> hs_status {
     using Tg = decltype(tag);
@@ -884,10 +904,12 @@ hs_status run_bicgstab(const SolveArgs& sa, hs_result* res, double* hist) {
       ay = c.take<T>(g.N);
       az = c.take<T>(g.N);
     }
+    double* trace = c.take<double>(bicgstab_trace_len(sa.maxit));
     if (!c.ok) {
       set_error("workspace too small for BiCGStab");
       return HS_ERR_WORKSPACE;
     }
+    const bool want_trace = sa.o.alpha_trace || sa.o.restart_iters;
     if (OPK == OP_VARK) {
       hs_status s = setup_vark(A, sa.dtype, D, ax, ay, az, false, sa.stream);
       if (s != HS_OK) return s;
@@ -895,10 +917,15 @@ hs_status run_bicgstab(const SolveArgs& sa, hs_result* res, double* hist) {
     double sigma;
     Coef<T> cf = op_coef<T>(A, D, ax, ay, az, &sigma);
     hs_status s = bicgstab_core<T, OPK, NDIM>(A, cf, sigma, (const T*)sa.b, (T*)sa.x, sa.tol, sa.maxit, cm, v, sa.o,
-                                              sa.stream);
+                                              sa.stream, want_trace ? trace : nullptr);
     if (s != HS_OK) return s;
     Tail t{A, sa.dtype, D, ax, ay, az, sa.b, sa.x, v[6]};
-    return finish_solve(sa, cm, t, res, hist, true);
+    s = finish_solve(sa, cm, t, res, hist, true);
+    if (want_trace && s != HS_ERR_CUDA) {
+      hs_status s2 = copy_bicgstab_trace(trace, sa.maxit, res->iters, sa.o, sa.stream);
+      if (s2 != HS_OK) return s2;
+    }
+    return s;
   });
 }
 

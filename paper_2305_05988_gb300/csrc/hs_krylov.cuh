@@ -388,6 +388,8 @@ struct BiArgs {
   double tol;
   double reps;
   int paper_order;   // Algorithm 2's statement order (BiCGStab-B1)
+  double* trace;     // optional, 2 (maxit + 1) doubles: per iteration k, r_k . r'
+                     // and 1.0 if a restart followed (entry 0: r_0 . r')
 };
 
 // p = r + beta (p_old - omega sigma v_old), or p = r on (re)start.  The
@@ -526,6 +528,10 @@ __device__ BodyOut bicgstab_body(const BiArgs<T>& a, const Team& tm, T* sm, doub
 
   double alpha_n = sqrt(brr);   // r . r' with r' = r / ||r||
   double inv_rn = 1.0 / sqrt(brr);
+  if (tm.lead() && a.trace) {
+    a.trace[0] = alpha_n;
+    a.trace[1] = 0.0;
+  }
   bool restart = true;          // p = r and r' = r/||r|| in the next pass 1
   double beta = 0.0, omega = 0.0;
   int it = 0, status = DS_MAXIT, restarts = 0;
@@ -641,6 +647,10 @@ __device__ BodyOut bicgstab_body(const BiArgs<T>& a, const Team& tm, T* sm, doub
     if (!team_reduce<2>(tm, acc4, rn2, sh)) return BodyOut{DS_TIMEOUT, it, rel, restarts, false};
     rel = sqrt(rn2[1] / bb);
     if (tm.lead() && a.cm.hist) a.cm.hist[it] = rel;
+    if (tm.lead() && a.trace) {
+      a.trace[2 * it] = rn2[0];
+      a.trace[2 * it + 1] = 0.0;
+    }
     if (!finite_d(rel) || !finite_d(rn2[0])) {
       status = DS_NONFINITE;
       break;
@@ -659,6 +669,7 @@ __device__ BodyOut bicgstab_body(const BiArgs<T>& a, const Team& tm, T* sm, doub
       beta = rn2[0] / (alpha_d * omega);
       alpha_n = rn2[0];
     }
+    if (tm.lead() && a.trace && restart) a.trace[2 * it + 1] = 1.0;
   }
   return BodyOut{status, it, rel, restarts, true};
 }

@@ -149,3 +149,22 @@ def upwind_beta(shape, peclet: float = 0.5, direction=(1.0, 0.5, 0.25)):
     m = max(d[i] * h[i] for i in range(nd))
     scale = 2.0 * peclet / m
     return tuple(d[i] * scale for i in range(nd)) + (0.0,) * (3 - nd)
+
+
+def distinct_cells(N: int, count: int, seed: int = 0, stream: int = STREAM_FD) -> np.ndarray:
+    """`count` distinct cell indices in [0, N): floor(U N) for the stream's
+    uniforms in draw order, repeats skipped (the finite-difference cells of the
+    adjoint check)."""
+    if count > N:
+        raise ValueError("more cells than the grid holds")
+    out, seen, off = [], set(), 0
+    while len(out) < count:
+        u = uniform(seed, stream, 4 * count, offset=off)
+        off += 4 * count
+        for c in (u * N).astype(np.int64):
+            if int(c) not in seen:
+                seen.add(int(c))
+                out.append(int(c))
+                if len(out) == count:
+                    break
+    return np.array(out, dtype=np.int64)

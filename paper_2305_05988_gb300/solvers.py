@@ -35,6 +35,8 @@ class SolveInfo:
     history: Optional[np.ndarray] = None
     outer: int = 0
     inner_iters: int = 0
+    alpha_trace: Optional[np.ndarray] = None      # BiCGStab: r_k . r' per iteration (trace=True)
+    restart_iters: Optional[list] = None          # BiCGStab: iterations followed by a restart
 
     @property
     def converged(self) -> bool:
@@ -196,7 +198,7 @@ _SOLVER_FN = {
 }
 
 
-def _solve(solver: int, A: Operator, b: torch.Tensor, x0, tol, maxit, history, inplace=False, **kw):
+def _solve(solver: int, A: Operator, b: torch.Tensor, x0, tol, maxit, history, inplace=False, trace=False, **kw):
     A._vec(b, "b")
     if x0 is None:
         x = torch.zeros_like(b)
@@ -206,6 +208,12 @@ def _solve(solver: int, A: Operator, b: torch.Tensor, x0, tol, maxit, history, i
             raise TypeError("x0 and b must have the same dtype")
         x = x0 if inplace else x0.clone()
     opts = make_opts(**kw)
+    alpha = restarts_at = None
+    if trace:
+        alpha = np.full(int(maxit) + 1, np.nan)
+        restarts_at = np.zeros(max(int(maxit), 1), dtype=np.int32)
+        opts.alpha_trace = alpha.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        opts.restart_iters = restarts_at.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
     res = _lib.hs_result()
     hist = np.full(int(maxit) + 1, np.nan) if history else None
     hptr = hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if hist is not None else None
@@ -224,6 +232,9 @@ def _solve(solver: int, A: Operator, b: torch.Tensor, x0, tol, maxit, history, i
     info = SolveInfo(iters=res.iters, status=_lib.STATUS_NAMES.get(res.status, str(res.status)),
                      status_code=res.status, rel_res=res.rel_res, true_rel_res=res.true_rel_res,
                      restarts=res.restarts, history=hist, outer=res.outer, inner_iters=res.inner_iters)
+    if trace:
+        info.alpha_trace = alpha[: res.iters + 1]
+        info.restart_iters = [int(v) for v in restarts_at[: res.restarts]]
     return x, info
 
 
@@ -285,7 +296,9 @@ def cg_nb(A: Operator, b, x0=None, tol: float = 1e-10, maxit: int = 10000, histo
 def bicgstab(A: Operator, b, x0=None, tol: float = 1e-10, maxit: int = 10000, history: bool = True,
              restart_eps: float = 1e-5, **kw):
     """BiCGStab with Algorithm 2's normalised shadow residual and restart;
-    paper_order=True gives Algorithm 2's statement order (BiCGStab-B1)."""
+    paper_order=True gives Algorithm 2's statement order (BiCGStab-B1);
+    trace=True also returns info.alpha_trace (r_k . r' after each iteration,
+    the value the restart test reads) and info.restart_iters."""
     return _solve(_lib.HS_SOLVER_BICGSTAB, A, b, x0, tol, maxit, history, restart_eps=restart_eps, **kw)
 
 

@@ -221,3 +221,26 @@ def test_gauss_seidel_workspace_sizes(lib):
         assert big.value > gs.value
     lib.hs_op_destroy(lap)
     lib.hs_op_destroy(box)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    # the binding's ctypes structures against the C compiler's layout of the
+    # header's hs_opts and hs_result (size and every field offset)
+    fields = {"hs_opts": _lib.hs_opts, "hs_result": _lib.hs_result}
+    src = ['#include <stddef.h>', '#include <stdio.h>', '#include "hsolve.h"', "int main(void) {"]
+    for sname, cls in fields.items():
+        src.append('printf("%s size %%zu\\n", sizeof(%s));' % (sname, sname))
+        for fname, _ in cls._fields_:
+            src.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (sname, fname, sname, fname))
+    src.append("return 0; }")
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(src))
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(line.split()[:2]): int(line.split()[2]) for line in out if line.strip()}
+    for sname, cls in fields.items():
+        assert got[(sname, "size")] == ctypes.sizeof(cls), sname
+        for fname, _ in cls._fields_:
+            assert got[(sname, fname)] == getattr(cls, fname).offset, (sname, fname)

@@ -51,13 +51,13 @@ def test_batch_matches_oracle_per_system():
     for k, (A_o, b, x, info, bsys) in enumerate(zip(ops_o, bs, xs, infos, systems)):
         assert info.status == "OK", (k, bsys, info)
         xh = x.cpu().numpy()
-        assert A_o.relres(b, xh) <= 1.5 * tol, (k, bsys)
+        assert A_o.relres(b, xh) <= tol * (1 + 1e-3), (k, bsys)
         if bsys.solver == "cg":
             _, it_o, _, _ = oracle.cg(A_o, b, tol=tol, maxit=20000)
         else:
             _, it_o, _, _, _ = oracle.bicgstab(A_o, b, tol=tol, maxit=20000)
         # +-2 where the oracle's own count is stable, else its perturbation window
-        lo, hi, counts = oracle_window(A_o, b, bsys.solver, it_o, tol)
+        lo, hi, counts, _, _ = oracle_window(A_o, b, bsys.solver, it_o, tol)
         assert lo <= info.iters <= hi, (k, bsys, info.iters, counts)
 
 
@@ -95,7 +95,7 @@ def test_batch_sizes_teams_by_work():
     s.synchronize()
     assert all(i.status == "OK" for i in infos)
     A_o = oracle.Operator(shapes[0])
-    assert A_o.relres(bs[0].cpu().numpy(), xs[0].cpu().numpy()) <= 1.5e-8
+    assert A_o.relres(bs[0].cpu().numpy(), xs[0].cpu().numpy()) <= 1e-8 * (1 + 1e-3)
 
 
 def test_batch_poisoned_system_does_not_disturb_neighbours():
@@ -114,7 +114,7 @@ def test_batch_poisoned_system_does_not_disturb_neighbours():
         if k == bad:
             continue
         assert info.status == "OK"
-        assert A_o.relres(b, x.cpu().numpy()) <= 1.5e-8
+        assert A_o.relres(b, x.cpu().numpy()) <= 1e-8 * (1 + 1e-3)
 
 
 def test_batch_zero_rhs_and_maxit():

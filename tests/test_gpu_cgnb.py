@@ -12,7 +12,7 @@ import pytest
 
 import oracle
 from paper_2305_05988_gb300 import inputs
-from parity_util import oracle_window
+from parity_util import iterate_bar, oracle_window, oracle_xdev
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -47,7 +47,7 @@ def test_cg_nb_tolerance_mode(shape, kind):
     assert abs(it_o - it_c) <= 1, (it_o, it_c)
     # +-2 where the oracle's count is stable; var-k systems: the oracle's own
     # perturbation window (CG counts), one wider for CG-NB's different rounding
-    lo, hi, counts = oracle_window(A_o, b, "cg", it_c, tol)
+    lo, hi, counts, _, _ = oracle_window(A_o, b, "cg", it_c, tol)
     lo, hi = min(lo, it_o - 2) - 1, max(hi, it_o + 2) + 1
     assert lo <= info.iters <= hi, (info.iters, it_o, counts)
     assert A_o.relres(b, host(x_g)) <= tol * (1 + 1e-3)
@@ -99,10 +99,15 @@ def test_bicgstab_b1_matches_oracle(shape, kind):
     x_o, it_o, st_o, _, nr_o = oracle.bicgstab_b1(A_o, b, tol=tol, maxit=5000)
     x_g, info = hs.bicgstab(A_g, dev(b), tol=tol, maxit=5000, paper_order=True)
     assert st_o == oracle.OK and info.status == "OK"
-    window = 2 if nr_o == 0 else 2 + int(np.ceil(0.10 * it_o))
-    assert abs(info.iters - it_o) <= window, (info.iters, it_o, nr_o)
+    # +-2 where the oracle's B1 count is stable, else its measured range +-2
+    lo, hi, counts, _, _ = oracle_window(A_o, b, "bicgstab_b1", it_o, tol)
+    assert lo <= info.iters <= hi, (info.iters, counts, nr_o)
     assert A_o.relres(b, host(x_g)) <= tol * (1 + 1e-3)
-    # B1 returns x_{l+1}: the classical iterate after as many iterations
+    # B1 returns x_{l+1}: the classical iterate after as many iterations, to
+    # 1e-8 or, where restarts make the count move, to the classical oracle's
+    # own perturbed-run distance after that many iterations
     x_c, it_c, _, _, _ = oracle.bicgstab(A_o, b, tol=0.0, maxit=info.iters)
     assert it_c == info.iters
-    assert rel(host(x_g), x_c) <= 1e-8 if nr_o == 0 else rel(host(x_g), x_c) <= 1e-5
+    xdev = oracle_xdev(A_o, b, "bicgstab", info.iters, x_c)
+    err = rel(host(x_g), x_c)
+    assert err <= iterate_bar(nr_o == 0, xdev), (err, xdev, nr_o)

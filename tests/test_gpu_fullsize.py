@@ -22,6 +22,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 import paper_2305_05988_gb300 as hs  # noqa: E402
+from parity_util import maxrel  # noqa: E402
 
 N3 = (256, 256, 256)
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "poisson3d_256_counts.json")
@@ -117,38 +118,96 @@ def test_mixed_512_certified_by_oracle():
     assert A_o.relres(b, x.cpu().numpy()) <= 1e-10 * (1 + 1e-3)
 
 
-def test_adjoint_full_size():
+ADJ_GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "adjoint256_grad.json")
+
+
+@pytest.fixture(scope="module")
+def adjoint256():
+    """The 256^3 adjoint workload on the GPU, FP64 and FP32 + refinement:
+    forward and observation solves and the adjoint to 1e-12, then the gradient
+    kernel."""
     shape = N3
-    N = int(np.prod(shape))
     logk = inputs.log_k(shape, 0.5, 0)
     f = inputs.rhs_uniform(shape, 0)
     k = np.exp(logk)
     kt = torch.from_numpy(k).cuda()
     A_g = hs.Operator.diffusion(shape, kt)
     ft = torch.from_numpy(f).cuda()
-    u, _ = hs.cg(A_g, ft, tol=1e-12, maxit=20000)
     k2 = torch.from_numpy(np.exp(inputs.log_k(shape, 0.5, 0, inputs.STREAM_K2))).cuda()
-    u_obs, _ = hs.cg(hs.Operator.diffusion(shape, k2), ft, tol=1e-12, maxit=20000)
-    lam, _ = hs.cg(A_g, (2 * (u - u_obs)).contiguous(), tol=1e-12, maxit=20000)
-    g = hs.grad_logk(A_g, u, lam).cpu().numpy()
-    # the kernel against the oracle's gradient formula on the same fields
-    g_o = oracle.grad_logk(oracle.Operator(shape, oracle.DIFFUSION, k=k), u.cpu().numpy(), lam.cpu().numpy())
-    assert rel(g, g_o) <= 1e-12
-    # central differences of L on a few random cells (seeded).  Written without
-    # cancellation: with A(theta) u = f, the perturbed solution is u + du where
-    # A(theta+-) du = -(A(theta+-) - A(theta)) u (a right-hand side that lives
+    A_obs = hs.Operator.diffusion(shape, k2)
+    out = {"shape": shape, "logk": logk, "k": k, "kt": kt, "A": A_g, "f": ft}
+    for variant in ("fp64", "mixed"):
+        if variant == "fp64":
+            def solve(A, rhs):
+                x, info = hs.cg(A, rhs, tol=1e-12, maxit=20000, history=False)
+                assert info.status == "OK", info
+                return x
+        else:
+            def solve(A, rhs):
+                x, info = hs.solve_mixed(A, rhs, tol=1e-12, maxit=60, inner_maxit=100000, timeout_s=20.0)
+                assert info.status == "OK", info
+                return x
+        u = solve(A_g, ft)
+        u_obs = solve(A_obs, ft)
+        lam = solve(A_g, (2 * (u - u_obs)).contiguous())
+        out[variant] = {"u": u, "u_obs": u_obs, "lam": lam, "g": hs.grad_logk(A_g, u, lam).cpu().numpy(),
+                        "solve": solve}
+    return out
+
+
+def test_adjoint_full_size_kernel_against_oracle_formula(adjoint256):
+    # the gradient kernel against the oracle's gradient formula on the same
+    # fields (both variants' u and lam)
+    A_o = oracle.Operator(N3, oracle.DIFFUSION, k=adjoint256["k"])
+    for variant in ("fp64", "mixed"):
+        v = adjoint256[variant]
+        g_o = oracle.grad_logk(A_o, v["u"].cpu().numpy(), v["lam"].cpu().numpy())
+        assert rel(v["g"], g_o) <= 1e-12, variant
+        assert maxrel(v["g"], g_o) <= 1e-12, variant
+
+
+def test_adjoint_full_size_against_the_oracles_adjoint_gradient(adjoint256):
+    # against the oracle's own FP64 adjoint gradient (its CG solves for u,
+    # u_obs and lam to 1e-12, then its gradient), stored at 64 seeded cells by
+    # tests/golden/make_adjoint256.py.  Both sides' solves leave a forward
+    # error of about cond(A) * 1e-12 <= 1e-7 relative in u and lam.
+    if not os.path.exists(ADJ_GOLDEN):
+        pytest.skip("adjoint golden values not generated")
+    gold = json.load(open(ADJ_GOLDEN))
+    cells = np.array(gold["cells"], dtype=np.int64)
+    assert len(set(cells.tolist())) == 64
+    assert np.array_equal(cells, inputs.distinct_cells(int(np.prod(N3)), 64))
+    g_ref = np.array(gold["grad_at_cells"])
+    for variant in ("fp64", "mixed"):
+        g = adjoint256[variant]["g"]
+        assert np.linalg.norm(g[cells] - g_ref) <= 1e-6 * np.linalg.norm(g_ref), variant
+        assert abs(np.linalg.norm(g) - gold["grad_norm2"]) <= 1e-6 * gold["grad_norm2"], variant
+        u, u_obs = adjoint256[variant]["u"], adjoint256[variant]["u_obs"]
+        loss = torch.sum((u - u_obs) ** 2).item()
+        assert abs(loss - gold["loss"]) <= 1e-6 * gold["loss"], variant
+
+
+@pytest.mark.parametrize("variant", ["fp64", "mixed"])
+def test_adjoint_full_size_central_differences(adjoint256, variant):
+    # central differences of L in log k at 64 distinct seeded cells, written
+    # without cancellation: with A(theta) u = f, the perturbed solution is
+    # u + du where A(theta+-) du = -(A(theta+-) - A(theta)) u (a right-hand side
     # next to the perturbed cell), and L(u + du) - L(u) = du . (du + 2 (u - u_obs)).
-    cells = np.unique((inputs.uniform(0, inputs.STREAM_FD, 16) * N).astype(np.int64))
+    # Each variant solves the perturbed systems with its own solver (FP64 CG,
+    # or FP32 inner + FP64 refinement) to 1e-12.
+    v = adjoint256[variant]
+    shape = adjoint256["shape"]
+    N = int(np.prod(shape))
+    u, u_obs, g, solve = v["u"], v["u_obs"], v["g"], v["solve"]
+    cells = inputs.distinct_cells(N, 64)
     delta = 1e-5
-    lk = torch.from_numpy(logk).cuda()
-    Au = A_g.spmv(u)
+    lk = torch.from_numpy(adjoint256["logk"]).cuda()
+    Au = adjoint256["A"].spmv(u)
     d_obs = 2 * (u - u_obs)
 
     def dloss(lkt):
         A_p = hs.Operator.diffusion(shape, torch.exp(lkt).contiguous())
-        r = (Au - A_p.spmv(u)).contiguous()
-        du, info = hs.cg(A_p, r, tol=1e-12, maxit=20000)
-        assert info.status == "OK"
+        du = solve(A_p, (Au - A_p.spmv(u)).contiguous())
         return torch.sum(du * (du + d_obs)).item()
 
     fd = []
@@ -158,11 +217,12 @@ def test_adjoint_full_size():
         lm[c] -= delta
         fd.append((dloss(lp) - dloss(lm)) / (2 * delta))
     fd = np.array(fd)
-    # over the sampled cells and per cell (floor 1e-3 max |g_FD|): the central
-    # difference error is O(delta^2) relative, the solves' O(1e-12)
+    # the central difference carries O(delta^2) relative truncation and the
+    # solves O(cond * 1e-12): 1e-6 over the cells, and per cell with the floor
+    # 1e-3 max |g_FD| for cells whose gradient nearly vanishes
     assert np.linalg.norm(g[cells] - fd) <= 1e-6 * np.linalg.norm(fd), (g[cells], fd)
     floor = 1e-3 * np.max(np.abs(fd))
-    assert np.all(np.abs(g[cells] - fd) <= 1e-5 * np.maximum(np.abs(fd), floor)), (g[cells], fd)
+    assert np.all(np.abs(g[cells] - fd) <= 1e-6 * np.maximum(np.abs(fd), floor)), (g[cells], fd)
 
 
 def test_batched_512_sampled_against_oracle():
@@ -188,4 +248,4 @@ def test_batched_512_sampled_against_oracle():
             A_o = oracle.Operator(s.shape)
         else:
             A_o = oracle.Operator(s.shape, oracle.UPWIND, inputs.upwind_beta(s.shape, s.peclet))
-        assert A_o.relres(bs[p].cpu().numpy(), xs[p].cpu().numpy()) <= 1e-8 * 1.5, (p, s)
+        assert A_o.relres(bs[p].cpu().numpy(), xs[p].cpu().numpy()) <= 1e-8 * (1 + 1e-3), (p, s)

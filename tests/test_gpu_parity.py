@@ -3,9 +3,16 @@
 Tolerances (restating the targets the solvers are built to):
   * SpMV, FP64: relative 2-norm error <= 1e-13 (a handful of roundings per row)
   * Jacobi / Gauss-Seidel iterates after k sweeps: relative error <= 1e-12
+  * every vector result is also checked element by element: the largest
+    entry-wise error over the largest reference entry (parity_util.maxrel)
+    stays within the same bound, so one wrong node cannot hide in the norm
   * CG / BiCGStab: at the oracle's iteration count, solution relative error
     <= 1e-8; in tolerance mode, iteration counts within +-2 and both true
-    residuals within tol (1 + 1e-3)
+    residuals within tol (1 + 1e-3).  Where the oracle's own count moves
+    under 1e-13 relative changes of b (BiCGStab restarts, strong coefficient
+    contrast) the count window is the oracle's measured range +-2 and the
+    iterate bar is derived from the oracle's own perturbed runs
+    (parity_util.iterate_bar)
   * FP32 paths: relative error <= 2e-6 for SpMV (single rounding of a short sum)
 Grids span several tiles (x tiles of 32, y tiles of 4..16, z chunks) and end in
 ragged tails so that every tile-edge branch runs.
@@ -17,7 +24,7 @@ import pytest
 
 import oracle
 from paper_2305_05988_gb300 import inputs
-from parity_util import oracle_window
+from parity_util import iterate_bar, maxrel, oracle_window
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -64,6 +71,7 @@ def test_spmv_f64(shape, kind):
     y_o = A_o.spmv(x)
     y_g = host(A_g.spmv(dev(x)))
     assert rel(y_g, y_o) <= 1e-13
+    assert maxrel(y_g, y_o) <= 1e-13
 
 
 @pytest.mark.parametrize("shape", [(70, 45), (37, 19, 11)])
@@ -74,6 +82,7 @@ def test_spmv_f32(shape, kind):
     y_o = A_o.spmv(x)
     y_g = host(A_g.spmv(dev(x, torch.float32)))
     assert rel(y_g, y_o) <= 2e-6
+    assert maxrel(y_g, y_o) <= 2e-6
 
 
 @pytest.mark.parametrize("shape", [(70, 45), (37, 19, 11)])
@@ -85,6 +94,7 @@ def test_residual(shape, kind):
     r_o = b - A_o.spmv(x)
     r_g = host(A_g.residual(dev(b), dev(x)))
     assert rel(r_g, r_o) <= 1e-13
+    assert maxrel(r_g, r_o) <= 1e-13
 
 
 # --------------------------------------------------------------------------
@@ -102,6 +112,7 @@ def test_jacobi_fixed_sweeps(shape, kind, sweeps):
     x_g, info = hs.jacobi(A_g, dev(b), dev(x0), maxit=sweeps)
     assert info.status == "OK" and info.iters == sweeps
     assert rel(host(x_g), x_o) <= 1e-12
+    assert maxrel(host(x_g), x_o) <= 1e-12
     assert abs(info.true_rel_res - A_o.relres(b, x_o)) <= 1e-10 * max(1.0, info.true_rel_res)
 
 
@@ -115,6 +126,7 @@ def test_jacobi_tolerance_and_history(shape, kind):
     assert info.iters == it_o
     assert np.allclose(info.history, h_o, rtol=1e-9, atol=0)
     assert rel(host(x_g), x_o) <= 1e-12
+    assert maxrel(host(x_g), x_o) <= 1e-12
 
 
 # --------------------------------------------------------------------------
@@ -135,6 +147,7 @@ def test_gauss_seidel_sweeps(shape, kind, sweeps, mode):
     x_g, info = hs.gauss_seidel(A_g, dev(b), dev(x0), maxit=sweeps, mode=mode)
     assert info.status == "OK" and info.iters == sweeps
     assert rel(host(x_g), x_o) <= 1e-12
+    assert maxrel(host(x_g), x_o) <= 1e-12
 
 
 @pytest.mark.parametrize("blocks", [1, 2, 3, 13])
@@ -153,6 +166,7 @@ def test_gauss_seidel_few_blocks(blocks, mode, sweeps, check_every):
                                 check_every=check_every, max_blocks=blocks)
     assert info.iters == sweeps and info.status == "NOT_CONVERGED", info
     assert rel(host(x_g), x_o) <= 1e-12
+    assert maxrel(host(x_g), x_o) <= 1e-12
 
 
 def test_gauss_seidel_tolerance_history():
@@ -164,6 +178,7 @@ def test_gauss_seidel_tolerance_history():
     assert info.status == "OK" and info.iters == it_o
     assert np.allclose(info.history, h_o, rtol=1e-9)
     assert rel(host(x_g), x_o) <= 1e-12
+    assert maxrel(host(x_g), x_o) <= 1e-12
 
 
 # --------------------------------------------------------------------------
@@ -187,25 +202,25 @@ def krylov_parity(A_o, A_g, b, solver, tol=1e-10, **kw):
     assert info_k.iters == k0
     assert rel(host(x_gk), x_ok) <= 1e-8
     assert np.allclose(info_k.history, h_ok, rtol=1e-7, atol=0)
-    # (2) convergence to the tolerance, certified by the oracle's own SpMV
+    # (2) convergence to the tolerance, certified by the oracle's own SpMV:
+    # the solver stops on the recursive residual <= tol, and the true
+    # residual of the returned iterate differs from it by the drift of the
+    # recursion (below 1e-5 relative on every case here, measured with the
+    # oracle), hence tol (1 + 1e-3)
     x_g, info = gsolve(A_g, dev(b), tol=tol, maxit=20000, **kw)
     assert info.status == "OK"
-    assert info.true_rel_res <= tol * (1 + 1e-3) * 1.5
-    assert A_o.relres(b, host(x_g)) <= tol * 1.5
-    # (3) iteration count within the oracle's own window
-    lo, hi, counts = oracle_window(A_o, b, solver, it_o, tol, **kw)
+    assert info.true_rel_res <= tol * (1 + 1e-3)
+    assert A_o.relres(b, host(x_g)) <= tol * (1 + 1e-3)
+    # (3) iteration count: +-2 where the oracle's own count is stable, else
+    # the oracle's measured range under 1e-13 input noise, +-2
+    lo, hi, counts, stable, xdev = oracle_window(A_o, b, solver, it_o, tol, **kw)
     assert lo <= info.iters <= hi, (info.iters, counts)
-    # (4) at the oracle's iteration count the iterates agree to 1e-8 when the
-    # count is stable; otherwise to the forward error both converged
-    # solutions can carry (they satisfy the same 1e-10 residual bound)
+    # (4) at the oracle's iteration count the iterates agree to 1e-8 (stable
+    # counts) or to the oracle's own perturbed-run distance there
     x_e, info_e = gsolve(A_g, dev(b), tol=0.0, maxit=it_o, **kw)
     assert info_e.iters == it_o
-    stable = (hi - lo) <= 4
     err = rel(host(x_e), x_o)
-    if stable:
-        assert err <= 1e-8, err
-    else:
-        assert err <= 1e-5, err
+    assert err <= iterate_bar(stable, xdev), (err, xdev, stable)
     return info, it_o
 
 
