@@ -124,6 +124,16 @@ typedef struct {
                                may be NULL; receives the iterations after which
                                a restart was taken, in order (res.restarts of
                                them).                                          */
+    int staging;            /* FP32 CG on a 3-D diffusion operator (hs_cg with
+                               HS_F32, and the inner CG of hs_solve_mixed):
+                               0 (default) the register-prefetch tile engine
+                               on stored FP32 coefficient arrays (16 B of
+                               operator data per node, the fastest measured);
+                               1 the stencil planes staged in shared memory by
+                               TMA and the face coefficients formed from k
+                               (4 B per node; 3-D, n_x a multiple of 4,
+                               n_x >= 40, n_y >= 10, n_z >= 3, else
+                               HS_ERR_INVALID)                                  */
 } hs_opts;
 
 typedef struct {
@@ -374,8 +384,21 @@ hs_status hs_batch_team_sizes(const hs_batch *batch, int *teams);
  * on a CUDA error. */
 hs_status hs_diag_wait_timeout(int kind, double timeout_s, void *stream);
 
+/* Diagnostics: the FP64 fused multiply-add rate of the current device in
+ * flop/s (2 flops per FMA), measured on `stream` with independent FMA chains
+ * in every resident thread (best of three timed launches of about 20 ms).
+ * The FP64 solvers are bound by this rate; it is the roofline peak their
+ * flop rates are quoted against.  Allocates 16 bytes of device memory for
+ * the call and synchronises `stream`.  HS_ERR_INVALID for a NULL result
+ * pointer, HS_ERR_CUDA on a CUDA error. */
+hs_status hs_diag_fp64_rate(void *stream, double *flops_per_s);
+
 /* Thread-local message describing the last non-OK status (never NULL). */
 const char *hs_last_error(void);
+
+/* 1 if the last hs_cg / hs_solve_mixed call on this thread ran its FP32
+ * diffusion CG with TMA-staged planes (hs_opts.staging = 1), else 0. */
+int hs_last_staging(void);
 
 /* Library version string. */
 const char *hs_version(void);

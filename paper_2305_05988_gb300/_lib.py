@@ -47,7 +47,8 @@ class hs_opts(ctypes.Structure):
                 ("paper_order", ctypes.c_int),
                 ("sweeps_per_pass", ctypes.c_int),
                 ("alpha_trace", ctypes.POINTER(ctypes.c_double)),
-                ("restart_iters", ctypes.POINTER(ctypes.c_int))]
+                ("restart_iters", ctypes.POINTER(ctypes.c_int)),
+                ("staging", ctypes.c_int)]
 
 
 class hs_result(ctypes.Structure):
@@ -102,7 +103,9 @@ SIGNATURES = {
     "hs_batch_grid": (_i, [_vp]),
     "hs_batch_team_sizes": (_i, [_vp, ctypes.POINTER(_i)]),
     "hs_diag_wait_timeout": (_i, [_i, ctypes.c_double, _vp]),
+    "hs_diag_fp64_rate": (_i, [_vp, ctypes.POINTER(_d)]),
     "hs_last_error": (ctypes.c_char_p, []),
+    "hs_last_staging": (_i, []),
     "hs_version": (ctypes.c_char_p, []),
 }
 

@@ -13,6 +13,9 @@
 namespace hs {
 
 static thread_local char g_err[512] = "no error";
+static thread_local int g_last_staging = 0;
+
+void set_last_staging(int v) { g_last_staging = v; }
 
 void set_error(const char* fmt, ...) {
   va_list ap;
@@ -114,6 +117,10 @@ bool merge_opts(const hs_opts* in, hs_opts* out) {
   if (out->max_blocks < 0) out->max_blocks = 0;
   out->paper_order = out->paper_order ? 1 : 0;
   if (out->sweeps_per_pass < 1) out->sweeps_per_pass = 1;
+  if (out->staging < 0 || out->staging > 1) {
+    set_error("hs_opts.staging must be 0 (register prefetch) or 1 (TMA)");
+    return false;
+  }
   if (out->sweeps_per_pass > 4) out->sweeps_per_pass = 4;
   return true;
 }
@@ -191,6 +198,7 @@ extern "C" {
 
 const char* hs_last_error(void) { return g_err; }
 const char* hs_version(void) { return "hsolve 0.1 (sm_103a)"; }
+int hs_last_staging(void) { return g_last_staging; }
 
 hs_status hs_diag_wait_timeout(int kind, double timeout_s, void* stream) {
   if (kind < 0 || kind > 2) {

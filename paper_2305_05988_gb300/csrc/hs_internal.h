@@ -151,4 +151,15 @@ hs_status setup_vark(const hs_op* A, hs_dtype dt, void* D, void* ax, void* ay, v
 
 int sm_count();
 
+// FP32 CG on a 3-D diffusion operator with TMA-staged planes and
+// coefficients formed from k (hs_cg32v.cu).  cg32v_eligible: the grid and the
+// options allow it.  k_to_f32: k32 = (float) k of the operator.
+bool cg32v_eligible(const hs_op* A, const hs_opts& o);
+hs_status k_to_f32(const hs_op* A, float* k32, cudaStream_t st);
+hs_status cg32v_core(const hs_op* A, const float* k32, const float* b, float* x, double tol, int maxit,
+                     const Common& cm, float* r, float* p0, float* p1, float* w, const hs_opts& o, cudaStream_t st);
+// Thread-local record of whether the last solve staged its stencil planes
+// with TMA (hs_last_staging).
+void set_last_staging(int v);
+
 }  // namespace hs

@@ -855,6 +855,35 @@ hs_status run_cg(const SolveArgs& sa, hs_result* res, double* hist) {
       set_error("workspace too small for CG");
       return HS_ERR_WORKSPACE;
     }
+    set_last_staging(0);
+    if constexpr (std::is_same<T, float>::value && OPK == OP_VARK && NDIM == 3) {
+      if (sa.o.staging == 1 && cg32v_eligible(A, sa.o)) {
+        // TMA-staged FP32 CG with coefficients formed from k (az holds k in
+        // FP32 during the solve; the coefficient arrays are formed afterwards
+        // for the true residual)
+        const float* k32 = (const float*)A->k;
+        if (A->kdt != HS_F32) {
+          hs_status s = k_to_f32(A, az, sa.stream);
+          if (s != HS_OK) return s;
+          k32 = az;
+        }
+        hs_status s = cg32v_core(A, k32, (const float*)sa.b, (float*)sa.x, sa.tol, sa.maxit, cm, r, p0, p1, w, sa.o,
+                                 sa.stream);
+        if (s != HS_OK) return s;
+        set_last_staging(1);
+        if (sa.o.true_residual) {
+          s = setup_vark(A, sa.dtype, D, ax, ay, az, false, sa.stream);
+          if (s != HS_OK) return s;
+        }
+        Tail t{A, sa.dtype, D, ax, ay, az, sa.b, sa.x, w};
+        return finish_solve(sa, cm, t, res, hist, true);
+      }
+    }
+    if (sa.o.staging == 1) {
+      set_error("TMA staging applies to FP32 CG on a 3-D diffusion operator with n_x a multiple of 4, n_x >= 40, "
+                "n_y >= 10, n_z >= 3");
+      return HS_ERR_INVALID;
+    }
     if (OPK == OP_VARK) {
       hs_status s = setup_vark(A, sa.dtype, D, ax, ay, az, false, sa.stream);
       if (s != HS_OK) return s;
@@ -1002,10 +1031,20 @@ hs_status run_mixed(const SolveArgs& sa, hs_result* res, double* hist) {
   }
   cudaStream_t st = sa.stream;
   hs_status s;
+  // FP32 inner CG on a 3-D diffusion operator with staging 1: the TMA-staged
+  // kernel with the face coefficients formed from k (L.D32 then holds k in
+  // FP32); otherwise the register-prefetch engine on stored FP32 coefficients
+  const bool tma = sa.o.inner_solver != HS_SOLVER_BICGSTAB && sa.o.staging == 1 && cg32v_eligible(A, sa.o);
+  if (!tma && sa.o.staging == 1) {
+    set_error("TMA staging requested but this problem does not allow it (3-D diffusion, inner CG, n_x a "
+              "multiple of 4, n_x >= 40)");
+    return HS_ERR_INVALID;
+  }
+  set_last_staging(tma ? 1 : 0);
   if (A->kind == KIND_DIFFUSION) {
     s = setup_vark(A, HS_F64, L.D64, L.ax64, L.ay64, L.az64, false, st);
     if (s != HS_OK) return s;
-    s = setup_vark(A, HS_F32, L.D32, L.ax32, L.ay32, L.az32, false, st);
+    s = tma ? k_to_f32(A, L.D32, st) : setup_vark(A, HS_F32, L.D32, L.ax32, L.ay32, L.az32, false, st);
     if (s != HS_OK) return s;
   }
   const int blocks = (int)std::max<long long>(1, std::min<long long>((g.N + 255) / 256, (long long)sm_count() * 8));
@@ -1051,7 +1090,11 @@ hs_status run_mixed(const SolveArgs& sa, hs_result* res, double* hist) {
     k_r_to_f32<<<blocks, 256, 0, st>>>(L.r64, L.r32, 1.0 / rn, g.N);
     e = cudaMemsetAsync(L.d32, 0, sizeof(float) * (size_t)g.N, st);
     if (e != cudaSuccess) return cuda_fail(e, "mixed: zero correction");
-    s = dispatch(HS_F32, opk, A->ndim, [&](auto tag) -> hs_status {
+    if (tma)
+      s = cg32v_core(A, L.D32, L.r32, L.d32, sa.o.inner_tol, sa.o.inner_maxit, L.inner, L.v32[0], L.v32[1],
+                     L.v32[2], L.v32[3], sa.o, st);
+    else
+      s = dispatch(HS_F32, opk, A->ndim, [&](auto tag) -> hs_status {
       using Tg = decltype(tag);
       using T = typename Tg::T;
       constexpr int OPK = Tg::OPK, NDIM = Tg::NDIM;

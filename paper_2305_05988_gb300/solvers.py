@@ -317,6 +317,15 @@ def diag_wait_timeout(kind: str, timeout_s: float = 0.05) -> str:
     return _lib.STATUS_NAMES.get(st, str(st))
 
 
+def fp64_rate() -> float:
+    """FP64 fused multiply-add rate of the current device in flop/s (the peak
+    the FP64 solvers' flop rates are quoted against)."""
+    v = ctypes.c_double()
+    check(_lib.load().hs_diag_fp64_rate(ctypes.c_void_p(torch.cuda.current_stream().cuda_stream), ctypes.byref(v)),
+          "hs_diag_fp64_rate")
+    return v.value
+
+
 def grad_logk(A: Operator, u: torch.Tensor, lam: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
     """dL/dlog k per cell from the forward solution u and the adjoint lam (float64)."""
     if A.kind != "diffusion":

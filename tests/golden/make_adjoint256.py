@@ -9,7 +9,10 @@ solves A(k) u = f, A(k_obs) u_obs = f and the adjoint A(k) lam = 2 (u - u_obs)
 with its FP64 CG to the relative tolerance 1e-12, then evaluates its per-cell
 gradient formula g = dL/dlog k.  Stored: the 64 cells (the first 64 distinct
 draws of the finite-difference stream, inputs.distinct_cells), g there, the
-2-norm of the whole g, L, the three CG iteration counts and final residuals.
+2-norm of the whole g, L, the three CG iteration counts and final residuals,
+and the solutions u and lam at 1024 further seeded cells with their 2-norms
+(the FP64 oracle solutions the GPU's FP64 and mixed-precision solves are
+compared with).
 
 Calls only the oracle and the seeded input generator.  Run from the repository
 root:  python tests/golden/make_adjoint256.py  (minutes with the OpenMP build
@@ -53,12 +56,20 @@ def main():
         print("lam", it_l, st_l, time.time() - t0, flush=True)
         g = oracle.grad_logk(A, u, lam)
     cells = inputs.distinct_cells(N, 64)
+    # the solutions themselves, sampled: the forward solution u and the adjoint
+    # lam at 1024 distinct cells of a second draw (seed 1 of the same stream)
+    ucells = inputs.distinct_cells(N, 1024, seed=1)
     rec = {
         "workload": ("adjoint256: 256^3 diffusion, log k ~ N(0, 0.5^2) seed 0 stream 2, f ~ U(-1,1) seed 0 "
                      "stream 1, u_obs with k_obs from stream 3, L = sum (u - u_obs)^2; oracle FP64 CG to 1e-12"),
         "cells": [int(c) for c in cells],
         "grad_at_cells": [float(v) for v in g[cells]],
         "grad_norm2": float(np.linalg.norm(g)),
+        "solution_cells": [int(c) for c in ucells],
+        "u_at_cells": [float(v) for v in u[ucells]],
+        "lam_at_cells": [float(v) for v in lam[ucells]],
+        "u_norm2": float(np.linalg.norm(u)),
+        "lam_norm2": float(np.linalg.norm(lam)),
         "loss": float(np.sum((u - u_obs) ** 2)),
         "cg_iters": {"u": it_u, "u_obs": it_o, "lam": it_l},
         "cg_final_rel_res": {"u": float(h_u[-1]), "u_obs": float(h_o[-1]), "lam": float(h_l[-1])},

@@ -83,6 +83,12 @@ def test_gauss_seidel_last_sweep_full_size(rhs):
 
 @pytest.mark.parametrize("solver", ["cg", "bicgstab"])
 def test_krylov_full_size_against_golden_counts(rhs, solver):
+    # the bench's solves against the oracle's counts at 256^3 (written by
+    # tests/golden/make_poisson3d_counts.py, oracle only).  The window is the
+    # oracle's own range under 1e-13 relative changes of b, +-2: for CG that
+    # range is a single count (1040), so the bar is +-2; BiCGStab on the upwind
+    # operator is chaotic here (the oracle alone spans 580-620 iterations), see
+    # test_bicgstab_full_size_restart_trace
     if not os.path.exists(GOLDEN):
         pytest.skip("golden counts not generated")
     golden = json.load(open(GOLDEN))
@@ -98,11 +104,33 @@ def test_krylov_full_size_against_golden_counts(rhs, solver):
         A_o, A_g = oracle.Operator(N3, oracle.UPWIND, beta), hs.Operator.upwind(N3, beta)
         x, info = hs.bicgstab(A_g, bt, tol=1e-10, maxit=20000)
     assert info.status == "OK"
-    # +-2, or when the oracle restarted BiCGStab (absolute restart threshold:
-    # where restarts fire depends on rounding) 2 + 10 %, as in parity_util
-    slack = 2 + (math.ceil(0.10 * g["iters"]) if g.get("restarts", 0) > 0 else 0)
-    assert abs(info.iters - g["iters"]) <= slack, (info.iters, g)
+    counts = g["spread_counts"]
+    assert counts[0] == g["iters"]
+    assert min(counts) - 2 <= info.iters <= max(counts) + 2, (info.iters, counts)
     assert A_o.relres(b, x.cpu().numpy()) <= 1e-10 * (1 + 1e-3)
+
+
+def test_bicgstab_full_size_restart_trace(rhs):
+    # decision by decision against the oracle's trace of the same solve: the
+    # residual histories agree to 1e-7 for the first 20 iterations (after
+    # that BiCGStab on this operator amplifies rounding differences: the
+    # oracle's own runs under 1e-13 input noise part there as well), the first
+    # restart (an iteration where both sides are far from the threshold's
+    # rounding) is taken after the same iteration, and every restart the GPU
+    # takes is one its own r . r' called for
+    if not os.path.exists(GOLDEN):
+        pytest.skip("golden counts not generated")
+    g = json.load(open(GOLDEN))["bicgstab"]
+    b, bt = rhs
+    beta = inputs.upwind_beta(N3, 0.5)
+    x, info = hs.bicgstab(hs.Operator.upwind(N3, beta), bt, tol=1e-10, maxit=20000, trace=True)
+    assert info.status == "OK"
+    h_o = np.array(g["history"])
+    np.testing.assert_allclose(info.history[:20], h_o[:20], rtol=1e-7, atol=0)
+    np.testing.assert_allclose(info.alpha_trace[:20], np.array(g["alpha"])[:20], rtol=1e-6, atol=0)
+    assert info.restart_iters[0] == g["restart_at"][0]
+    below = [k for k in range(1, info.iters) if math.sqrt(abs(info.alpha_trace[k])) < 1e-5]
+    assert below == info.restart_iters
 
 
 def test_mixed_512_certified_by_oracle():
@@ -178,6 +206,17 @@ def test_adjoint_full_size_against_the_oracles_adjoint_gradient(adjoint256):
     assert len(set(cells.tolist())) == 64
     assert np.array_equal(cells, inputs.distinct_cells(int(np.prod(N3)), 64))
     g_ref = np.array(gold["grad_at_cells"])
+    # the solutions themselves against the oracle's: both sides solve to a
+    # relative residual of 1e-12, so each is within cond(A) 1e-12 of the exact
+    # solution; cond(A) <= (12 k_max / h^2) / (3 pi^2 k_min) ~ 0.41 (n+1)^2
+    # k_max / k_min ~ 2e6 for this k field (log k ~ N(0, 0.25), |log k| < 3.3)
+    ucells = np.array(gold["solution_cells"], dtype=np.int64)
+    for variant in ("fp64", "mixed"):
+        for name, ref in (("u", gold["u_at_cells"]), ("lam", gold["lam_at_cells"])):
+            v = adjoint256[variant][name].cpu().numpy()[ucells]
+            err = np.linalg.norm(v - np.array(ref)) / np.linalg.norm(ref)
+            print("adjoint256 %s %s vs oracle: %.3e" % (variant, name, err))
+            assert err <= 2e6 * 1e-12 * 2, (variant, name, err)
     for variant in ("fp64", "mixed"):
         g = adjoint256[variant]["g"]
         assert np.linalg.norm(g[cells] - g_ref) <= 1e-6 * np.linalg.norm(g_ref), variant
