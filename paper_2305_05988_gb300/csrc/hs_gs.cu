@@ -529,6 +529,162 @@ __global__ void __launch_bounds__(gs_threads<NDIM, W>()) k_gs(GsArgs<T> a) {
 }
 
 // ---------------------------------------------------------------------------
+// Small 2-D (and 1-D) grids: one block holds the whole iterate in shared
+// memory and sweeps it along anti-diagonals i + j = d, the node order of the
+// tile kernel's intra-tile wavefront applied to the entire grid.  Sweeps of
+// one direction are pipelined: sweep t works on diagonal s - 2t at step s, so
+// the old-side neighbours of its nodes (diagonal d + 1) still hold sweep
+// t - 1's values and the new-side ones (diagonal d - 1) already hold sweep
+// t's; nodes handled in one step lie on diagonals two apart and never
+// neighbour each other, so one block barrier per step orders everything.  A
+// batch of n sweeps takes n_x + n_y - 1 + 2 (n - 1) steps instead of the
+// n (n_x + n_y - 1) tile-plane steps of the multi-block schedule, with no
+// grid-wide wait.  Thread (i, q) owns column i and the sweeps t = q (mod Q).
+// The update arithmetic is that of gs_tile (gs_old then gs_new).
+// ---------------------------------------------------------------------------
+
+template <typename T, int OPK>
+__device__ __forceinline__ void gs2d_node(const GsArgs<T>& a, T* xs, T bv, int i, int j, bool bw) {
+  const Geom& g = a.g;
+  const int nx = g.nx, ny = g.ny;
+  const int c = j * nx + i;
+  const T vW = i > 0 ? xs[c - 1] : T(0);
+  const T vE = i + 1 < nx ? xs[c + 1] : T(0);
+  const T vS = j > 0 ? xs[c - nx] : T(0);
+  const T vN = j + 1 < ny ? xs[c + nx] : T(0);
+  const OpRaw<T, OPK> o = op_fetch<T, OPK, 2>(a.cf, g, c, i, j, 0);
+  // old side: upper neighbours of a forward sweep, lower ones of a backward
+  const T yold = gs_old<T, OPK, 2>(a.cf, o, bv, bw ? vW : vE, bw ? vS : vN, T(0), bw);
+  xs[c] = gs_new<T, OPK, 2>(a.cf, o, yold, bw ? vE : vW, bw ? vN : vS, T(0), bw);
+}
+
+// nsw sweeps of one direction, pipelined two diagonals apart.  (Loading the
+// right-hand sides one step ahead measured slower: the index arithmetic it
+// adds outweighs the L2 latency it hides.)
+template <typename T, int OPK>
+__device__ void gs2d_batch(const GsArgs<T>& a, T* xs, const T* bsrc, int nsw, bool bw) {
+  const int nx = a.g.nx, ny = a.g.ny;
+  const int Q = blockDim.x / nx;                 // sweep lanes per column
+  const int i = threadIdx.x % nx, q = threadIdx.x / nx;
+  const bool active = q < Q;
+  const int dmax = nx + ny - 2;
+  const int nsteps = dmax + 1 + 2 * (nsw - 1);
+  const int ii = bw ? nx - 1 - i : i;             // the column in the sweep's frame
+  for (int s = 0; s < nsteps; s++) {
+    if (active) {
+      // sweeps t with a node in column i at this step: row s - 2t - i of the
+      // sweep's own frame lies in [0, ny), i.e. t in [t_lo, t_hi]; this
+      // thread takes those with t = q (mod Q)
+      const int t_lo = max(0, (s - i - (ny - 1) + 1) >> 1);
+      const int t_hi = min(nsw - 1, (s - i) >> 1);
+      for (int t = t_lo + (((q - t_lo) % Q) + Q) % Q; t <= t_hi; t += Q) {
+        const int r = s - 2 * t - i;
+        const int jj = bw ? ny - 1 - r : r;
+        gs2d_node<T, OPK>(a, xs, __ldcg(bsrc + jj * nx + ii), ii, jj, bw);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Relative residual ||b - A x|| / ||b|| of the iterate in shared memory,
+// through the Jacobi form as gs_residual.
+template <typename T, int OPK>
+__device__ double gs2d_residual(const GsArgs<T>& a, const T* xs, const T* bsrc, double* sh, double bb) {
+  const Geom& g = a.g;
+  double acc[1] = {0.0};
+  for (int c = threadIdx.x; c < (int)g.N; c += blockDim.x) {
+    const int i = c % g.nx, j = c / g.nx;
+    Nbr<T> nb;
+    nb.c = xs[c];
+    nb.w = i > 0 ? xs[c - 1] : T(0);
+    nb.e = i + 1 < g.nx ? xs[c + 1] : T(0);
+    nb.s = j > 0 ? xs[c - g.nx] : T(0);
+    nb.n = j + 1 < g.ny ? xs[c + g.nx] : T(0);
+    nb.b = nb.t = T(0);
+    const OpRaw<T, OPK> o = op_fetch<T, OPK, 2>(a.cf, g, c, i, j, 0);
+    T d = jacobi_apply<T, OPK, 2>(a.cf, o, nb, __ldcg(bsrc + c)) - nb.c;
+    if constexpr (OPK == OP_VARK) d = d / o.d;
+    acc[0] += widen(d) * widen(d);
+  }
+  block_sum<1>(acc, sh);
+  const double sc = (OPK == OP_VARK) ? 1.0 : a.dscale2;
+  return sqrt(acc[0] * sc / bb);
+}
+
+template <typename T, int OPK>
+__global__ void __launch_bounds__(1024) k_gs2d(GsArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ double sh[32 * MAX_SCAL];
+  T* xs = reinterpret_cast<T*>(smraw);
+  const int N = (int)a.g.N;
+  const T* bsrc = (OPK == OP_VARK) ? a.b : a.bD;
+  double acc[1] = {0.0};
+  for (int c = threadIdx.x; c < N; c += blockDim.x) {
+    const T bv = a.b[c];
+    if (OPK != OP_VARK) a.bD[c] = bv * a.invd;
+    acc[0] += widen(bv) * widen(bv);
+    xs[c] = a.x[c];
+  }
+  block_sum<1>(acc, sh);   // its barriers also publish bD and xs to the block
+  const double bb = acc[0];
+  Ctrl* ctrl = a.cm.ctrl;
+  if (bb == 0.0) {
+    for (int c = threadIdx.x; c < N; c += blockDim.x) a.x[c] = T(0);
+    if (threadIdx.x == 0) {
+      a.cm.hist[0] = 0.0;
+      ctrl->iters = 0;
+      ctrl->rel_res = 0.0;
+      atomicCAS(&ctrl->status, 0, (int)DS_CONVERGED);
+    }
+    return;
+  }
+  int done = 0, status = DS_CONVERGED;
+  double rel = -1.0;
+  if (a.tol > 0.0) {
+    rel = gs2d_residual<T, OPK>(a, xs, bsrc, sh, bb);
+    if (threadIdx.x == 0) a.cm.hist[0] = rel;
+    status = !(rel > a.tol) ? (isfinite(rel) ? DS_CONVERGED : DS_NONFINITE) : DS_MAXIT;
+  }
+  if (!(a.tol > 0.0) || status == DS_MAXIT) {
+    while (done < a.maxit) {
+      const int nb = (a.tol > 0.0) ? min(a.check_every, a.maxit - done) : a.maxit - done;
+      if (a.mode == HS_GS_SYMMETRIC) {
+        for (int q = 0; q < nb; q++) {
+          gs2d_batch<T, OPK>(a, xs, bsrc, 1, false);
+          gs2d_batch<T, OPK>(a, xs, bsrc, 1, true);
+        }
+      } else {
+        gs2d_batch<T, OPK>(a, xs, bsrc, nb, a.mode == HS_GS_BACKWARD);
+      }
+      done += nb;
+      if (a.tol > 0.0) {
+        rel = gs2d_residual<T, OPK>(a, xs, bsrc, sh, bb);
+        if (threadIdx.x == 0) {
+          for (int q = done - nb + 1; q < done; q++) a.cm.hist[q] = nan("");  // not evaluated
+          a.cm.hist[done] = rel;
+        }
+        if (!isfinite(rel)) {
+          status = DS_NONFINITE;
+          break;
+        }
+        if (rel <= a.tol) {
+          status = DS_CONVERGED;
+          break;
+        }
+        status = DS_MAXIT;
+      }
+    }
+  }
+  for (int c = threadIdx.x; c < N; c += blockDim.x) a.x[c] = xs[c];
+  if (threadIdx.x == 0) {
+    ctrl->iters = done;
+    ctrl->rel_res = rel;
+    atomicCAS(&ctrl->status, 0, status);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
 
@@ -687,6 +843,83 @@ static hs_status gs_run_t(const SolveArgs& sa, hs_result* res, double* hist) {
   return finish_solve_pub(sa, cm, D, ax, ay, az, a.bD, res, hist, sa.tol > 0.0);
 }
 
+// Largest iterate the single-block 2-D path holds in shared memory.
+constexpr size_t GS2D_SMEM_MAX = 200 * 1024;
+
+template <typename T>
+static bool gs2d_applies(const hs_op* A, const hs_opts& o) {
+  if (A->ndim > 2 || A->n[0] > 1024) return false;
+  if (o.max_blocks > 1) return false;   // a caller asking for several blocks gets the tile schedule
+  const size_t N = (size_t)(A->n[0] * A->n[1]);
+  return N * sizeof(T) <= GS2D_SMEM_MAX;
+}
+
+template <typename T, int OPK>
+static hs_status gs2d_run_t(const SolveArgs& sa, hs_result* res, double* hist) {
+  const hs_op* A = sa.A;
+  Geom g = geom_of(A);
+  Carve c{sa.ws, 0, sa.ws_bytes, true};
+  Common cm = carve_common(c, sa.maxit);
+  GsArgs<T> a = {};
+  a.bD = c.take<T>(g.N);
+  T *D = nullptr, *ax = nullptr, *ay = nullptr, *az = nullptr;
+  if (OPK == OP_VARK) {
+    // the workspace sizing reserves the tile tables first; the coefficient
+    // arrays follow them in both layouts
+    int nt, P;
+    gs_counts(A, &nt, &P);
+    c.take<int>((size_t)nt + P + 1);
+    c.take<unsigned>((size_t)nt);
+    c.take<unsigned long long>(1);
+    D = c.take<T>(g.N);
+    ax = c.take<T>(g.N);
+    ay = c.take<T>(g.N);
+    az = c.take<T>(g.N);
+  }
+  if (!c.ok) {
+    set_error("workspace too small for Gauss-Seidel");
+    return HS_ERR_WORKSPACE;
+  }
+  hs_status s = init_ctrl(cm, sa.o, sa.stream);
+  if (s != HS_OK) return s;
+  if (OPK == OP_VARK) {
+    s = setup_vark(A, sa.dtype, D, ax, ay, az, true, sa.stream);
+    if (s != HS_OK) return s;
+    a.cf.D = D;
+    a.cf.ax = ax;
+    a.cf.ay = ay;
+    a.cf.az = az;
+    a.dscale2 = 1.0;
+  } else {
+    a.cf = gs_jacobi_coef<T>(A, &a.invd, &a.dscale2);
+  }
+  a.g = g;
+  a.b = (const T*)sa.b;
+  a.x = (T*)sa.x;
+  a.cm = cm;
+  a.maxit = sa.maxit;
+  a.mode = sa.o.gs_mode;
+  a.check_every = sa.o.check_every;
+  a.tol = sa.tol;
+  const size_t smem = (size_t)g.N * sizeof(T);
+  auto kern = k_gs2d<T, OPK>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 1));
+  if (e != cudaSuccess) return cuda_fail(e, "shared-memory attribute");
+  // Q sweep lanes per column: as many whole columns of threads as fit,
+  // rounded up to whole warps (the block reductions use full-warp shuffles;
+  // the few extra threads have q = Q and stay idle in the sweeps)
+  const int nx = g.nx;
+  const int threads = std::min(1024, (((1024 / nx) * nx + 31) / 32) * 32);
+  kern<<<1, threads, smem, sa.stream>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "Gauss-Seidel launch");
+  if (OPK == OP_VARK && sa.o.true_residual) {
+    s = setup_vark(A, sa.dtype, D, ax, ay, az, false, sa.stream);
+    if (s != HS_OK) return s;
+  }
+  return finish_solve_pub(sa, cm, D, ax, ay, az, a.bD, res, hist, sa.tol > 0.0);
+}
+
 // Warp 0 waits for a sweep count that nothing publishes (diagnostic).
 __global__ void k_diag_gs(Ctrl* ctrl, const unsigned* flag) {
   if (threadIdx.x < 32) gs_poll(threadIdx.x == 0, flag, 1u, ctrl);
@@ -709,6 +942,7 @@ hs_status run_gauss_seidel(const SolveArgs& sa, hs_result* res, double* hist) {
   const bool deep = sa.o.gs_mode == HS_GS_SYMMETRIC || per_batch < 4;
 #define HS_GS(TT, OK)                                                                         \
   if (opk == OK) {                                                                            \
+    if (!d3 && gs2d_applies<TT>(sa.A, sa.o)) return gs2d_run_t<TT, OK>(sa, res, hist);          \
     if (!d3) return gs_run_t<TT, OK, 2, 0>(sa, res, hist);                                    \
     return deep ? gs_run_t<TT, OK, 3, 1>(sa, res, hist) : gs_run_t<TT, OK, 3, 0>(sa, res, hist); \
   }

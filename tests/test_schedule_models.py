@@ -211,3 +211,72 @@ def test_gs27_ring_schedule_equals_sequential_sweeps(shape, G, batches):
 def test_gs27_model_detects_a_dropped_upper_wait():
     errs = [_model_gs27((9, 3, 11), 5, [(3, False)], seed=s, drop_upper_wait=True) for s in range(4)]
     assert max(errs) > 1e-6
+
+
+# ---------------------------------------------------------------------------
+# Single-block shared-memory Gauss-Seidel for small 2-D grids (k_gs2d): sweep
+# t works on anti-diagonal s - 2t at step s; thread (i, q) owns column i and
+# the sweeps t = q (mod Q).  The model transcribes the kernel's index
+# arithmetic and checks coverage and the order of every dependency.
+# ---------------------------------------------------------------------------
+
+def gs2d_schedule(nx, ny, nsw, threads, bw):
+    Q = threads // nx
+    dmax = nx + ny - 2
+    visit = {}
+    for s in range(dmax + 1 + 2 * (nsw - 1)):
+        for tid in range(threads):
+            i, q = tid % nx, tid // nx
+            if q >= Q:
+                continue
+            t_lo = max(0, (s - i - (ny - 1) + 1) >> 1)
+            t_hi = min(nsw - 1, (s - i) >> 1)
+            t = t_lo + (((q - t_lo) % Q) + Q) % Q
+            while t <= t_hi:
+                r = s - 2 * t - i
+                assert 0 <= r < ny
+                node = (t, nx - 1 - i if bw else i, ny - 1 - r if bw else r)
+                assert node not in visit, "node visited twice"
+                visit[node] = s
+                t += Q
+    return visit
+
+
+@pytest.mark.parametrize("nx,ny,nsw,threads", [(5, 4, 3, 20), (7, 1, 5, 21), (1, 1, 4, 32), (3, 9, 6, 30),
+                                               (70, 45, 4, 980), (33, 1, 7, 1023), (1, 5, 3, 1024),
+                                               (40, 30, 9, 1000)])
+@pytest.mark.parametrize("bw", [False, True])
+def test_gs2d_wavefront_schedule(nx, ny, nsw, threads, bw):
+    visit = gs2d_schedule(nx, ny, nsw, threads, bw)
+    assert len(visit) == nsw * nx * ny
+    for (t, i, j), s in visit.items():
+        new_side = [(i - 1, j), (i, j - 1)] if not bw else [(i + 1, j), (i, j + 1)]
+        old_side = [(i + 1, j), (i, j + 1)] if not bw else [(i - 1, j), (i, j - 1)]
+        for a, b in new_side:
+            if 0 <= a < nx and 0 <= b < ny:
+                assert visit[(t, a, b)] < s          # already updated in this sweep
+        for a, b in old_side:
+            if 0 <= a < nx and 0 <= b < ny:
+                assert visit[(t, a, b)] > s          # not yet overwritten by this sweep
+                if t > 0:
+                    assert visit[(t - 1, a, b)] < s  # the previous sweep's value is there
+        if t > 0:
+            assert visit[(t - 1, i, j)] < s
+
+
+def test_gs2d_schedule_model_catches_one_diagonal_shift():
+    # sweeps one diagonal apart instead of two: a node reads a neighbour that
+    # a later sweep updates in the same step
+    nx, ny, nsw = 6, 5, 3
+    visit = {}
+    for s in range(nx + ny - 1 + (nsw - 1)):
+        for t in range(nsw):
+            for i in range(nx):
+                r = s - t - i
+                if 0 <= r < ny:
+                    visit[(t, i, r)] = s
+    with pytest.raises(AssertionError):
+        for (t, i, j), s in visit.items():
+            for a, b in [(i + 1, j), (i, j + 1)]:
+                if a < nx and b < ny and t > 0:
+                    assert visit[(t - 1, a, b)] < s
