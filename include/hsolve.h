@@ -53,7 +53,9 @@ typedef enum {
     HS_ERR_BREAKDOWN = -3,   /* a Krylov denominator vanished (e.g. p.Ap <= 0)     */
     HS_ERR_NONFINITE = -4,   /* NaN or Inf appeared in a reduction                 */
     HS_ERR_TIMEOUT = -5,     /* a bounded device-side wait ran out                 */
-    HS_ERR_WORKSPACE = -6    /* workspace missing, misaligned or too small         */
+    HS_ERR_WORKSPACE = -6,   /* workspace missing, misaligned or too small         */
+    HS_ERR_BOUNDS = -7       /* debug builds only: a kernel computed an index
+                                outside a vector (the access was skipped)         */
 } hs_status;
 
 typedef enum { HS_F64 = 0, HS_F32 = 1 } hs_dtype;

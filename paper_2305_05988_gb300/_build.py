@@ -17,7 +17,11 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 ROOT = os.path.dirname(PKG)
 INCLUDE = os.path.join(ROOT, "include")
-BUILD = os.path.join(PKG, "_build")
+# HSOLVE_DEBUG=1 selects the debug variant (-DHS_DEBUG: bounds checks in the
+# tile engines that report HS_ERR_BOUNDS instead of touching memory), built
+# into its own directory so that it never replaces the release library.
+DEBUG = os.environ.get("HSOLVE_DEBUG", "") not in ("", "0")
+BUILD = os.path.join(PKG, "_build_debug" if DEBUG else "_build")
 LIB = os.path.join(BUILD, "libhsolve.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -60,6 +64,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         obj = os.path.join(BUILD, os.path.splitext(os.path.basename(src))[0] + ".o")
         objs.append(obj)
         extra = os.environ.get("HSOLVE_NVCC_FLAGS", "").split()   # e.g. -DHS_CG_MAXNREG=80
+        if DEBUG:
+            extra = extra + ["-DHS_DEBUG"]
         cmd = [cc] + ARCH + NVCC_FLAGS + extra + ["-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
@@ -76,7 +82,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         msg = "\n".join("%s:\n%s" % (s, t) for s, t in failed)
         raise RuntimeError("nvcc failed:\n" + msg)
     tmp = LIB + ".%d.tmp" % os.getpid()
-    subprocess.run([cc] + ARCH + ["-shared", "-o", tmp] + objs, check=True)
+    subprocess.run([cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-ldl"], check=True)
     os.replace(tmp, LIB)
     return LIB
 

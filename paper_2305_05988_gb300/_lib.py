@@ -20,9 +20,11 @@ HS_ERR_BREAKDOWN = -3
 HS_ERR_NONFINITE = -4
 HS_ERR_TIMEOUT = -5
 HS_ERR_WORKSPACE = -6
+HS_ERR_BOUNDS = -7
 
 STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", -1: "ERR_INVALID", -2: "ERR_CUDA", -3: "ERR_BREAKDOWN",
-                -4: "ERR_NONFINITE", -5: "ERR_TIMEOUT", -6: "ERR_WORKSPACE"}
+                -4: "ERR_NONFINITE", -5: "ERR_TIMEOUT", -6: "ERR_WORKSPACE",
+                -7: "ERR_BOUNDS"}
 
 HS_F64, HS_F32 = 0, 1
 HS_SOLVER_JACOBI, HS_SOLVER_GAUSS_SEIDEL, HS_SOLVER_CG, HS_SOLVER_BICGSTAB, HS_SOLVER_MIXED, HS_SOLVER_CG_NB = 0, 1, 2, 3, 4, 5

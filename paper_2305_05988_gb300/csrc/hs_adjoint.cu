@@ -73,6 +73,7 @@ static hs_status launch_grad(const hs_op* A, const double* u, const double* lam,
 
 extern "C" hs_status hs_diffusion_grad_logk(const hs_op* A, const double* u, const double* lam, double* g,
                                             void* stream) {
+  hs::NvtxRange range("hs_diffusion_grad_logk");
   if (!A || !u || !lam || !g) {
     hs::set_error("NULL argument");
     return HS_ERR_INVALID;

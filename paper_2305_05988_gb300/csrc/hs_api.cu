@@ -165,6 +165,9 @@ typedef hs_status (*runner_t)(const SolveArgs&, hs_result*, double*);
 static hs_status solve_common(runner_t run, hs_solver which, const hs_op* A, hs_dtype dt, const void* b, void* x,
                               double tol, int maxit, const hs_opts* opts, void* ws, size_t ws_bytes, void* stream,
                               hs_result* res, double* hist) {
+  static const char* const names[] = {"hs_jacobi", "hs_gauss_seidel", "hs_cg", "hs_bicgstab", "hs_solve_mixed",
+                                      "hs_cg_nb"};
+  NvtxRange range(which >= 0 && which <= 5 ? names[which] : "hs_solve");
   hs_result local;
   hs_result* r = res ? res : &local;
   fill_res(r);
@@ -313,6 +316,7 @@ void hs_op_destroy(hs_op* op) { delete op; }
 int64_t hs_op_size(const hs_op* op) { return op ? op->n[0] * op->n[1] * op->n[2] : 0; }
 
 hs_status hs_spmv(const hs_op* A, hs_dtype dtype, const void* x, void* y, void* stream) {
+  NvtxRange range("hs_spmv");
   if (!A || !x || !y) { set_error("NULL argument"); return HS_ERR_INVALID; }
   if (dtype != HS_F64 && dtype != HS_F32) { set_error("bad dtype"); return HS_ERR_INVALID; }
   if (x == y) { set_error("x and y must not alias"); return HS_ERR_INVALID; }
@@ -321,6 +325,7 @@ hs_status hs_spmv(const hs_op* A, hs_dtype dtype, const void* x, void* y, void* 
 }
 
 hs_status hs_residual(const hs_op* A, hs_dtype dtype, const void* b, const void* x, void* r, void* stream) {
+  NvtxRange range("hs_residual");
   if (!A || !b || !x || !r) { set_error("NULL argument"); return HS_ERR_INVALID; }
   if (dtype != HS_F64 && dtype != HS_F32) { set_error("bad dtype"); return HS_ERR_INVALID; }
   if (r == x || r == b) { set_error("r must not alias b or x"); return HS_ERR_INVALID; }

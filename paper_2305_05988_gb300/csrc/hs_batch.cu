@@ -522,6 +522,7 @@ extern "C" hs_status hs_batch_workspace_size(hs_batch* B, size_t* bytes) {
 
 extern "C" hs_status hs_batch_solve(hs_batch* B, const double* const* b, double* const* x, double tol, int maxit,
                                     const hs_opts* opts, void* ws, size_t ws_bytes, void* stream, hs_result* res) {
+  hs::NvtxRange range("hs_batch_solve");
   if (!B || !b || !x || !res) {
     set_error("NULL argument");
     return HS_ERR_INVALID;

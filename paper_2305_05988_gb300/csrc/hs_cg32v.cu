@@ -306,7 +306,7 @@ __device__ bool tma_pass(const Engine<BY>& E, const float beta, const float ap, 
         St = reinterpret_cast<const float*>(E.slot_ptr(qz + 1));
         vt = src(St, cpos);
       }
-      if (inside) {
+      if (inside && HS_IN_BOUNDS(idx, g.N)) {
         const float* K0 = Sc + L::HBA / 4;
         const float kc = K0[cpos];
         const float fW = hW ? face(kc, K0[cpos - 1], fx) : kc * a.ihx;
@@ -602,7 +602,9 @@ hs_status cg32v_core(const hs_op* A, const float* k32, const float* b, float* x,
   s = plan_persistent(k_cg32v<BY>, 32 * (BY + 1), smem, g, BY, true, &grid, &a.tl, o, 1);
   if (s != HS_OK) return s;
   void* args[] = {&a};
-  return launch_coop((const void*)k_cg32v<BY>, grid, 32 * (BY + 1), args, smem, st);
+  s = launch_coop((const void*)k_cg32v<BY>, grid, 32 * (BY + 1), args, smem, st);
+  if (s != HS_OK) return s;
+  return hs_dbg_take(st);
 }
 
 }  // namespace hs

@@ -281,6 +281,8 @@ static hs_status cg_nb_t(const SolveArgs& sa, hs_result* res, double* hist) {
   void* args[] = {&a};
   s = launch_coop((const void*)k_cg_nb<T, OPK, NDIM>, grid, 32 * by, args, smem, sa.stream);
   if (s != HS_OK) return s;
+  s = hs_dbg_take(sa.stream);
+  if (s != HS_OK) return s;
   return finish_solve_pub(sa, cm, D, ax, ay, az, a.w[0], res, hist, true);
 }
 

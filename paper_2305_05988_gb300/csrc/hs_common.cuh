@@ -7,6 +7,26 @@
 
 namespace hs {
 
+// ---------------------------------------------------------------------------
+// Debug builds (-DHS_DEBUG): every global index the tile engines compute is
+// checked against the vector length before it is used; a bad index is
+// recorded (1 + index, first one wins) in a word of this translation unit and
+// the access is skipped -- no trap, no assert, the kernel runs on.  The host
+// launchers read and clear the word after each solve (hs_dbg_take) and return
+// HS_ERR_BOUNDS.  In release builds HS_IN_BOUNDS is constant true.
+// ---------------------------------------------------------------------------
+#ifdef HS_DEBUG
+static __device__ unsigned long long hs_dbg_word;
+__device__ __forceinline__ bool hs_in_bounds(long long idx, long long n) {
+  if (idx >= 0 && idx < n) return true;
+  atomicCAS(&hs_dbg_word, 0ull, 1ull + (unsigned long long)idx);
+  return false;
+}
+#define HS_IN_BOUNDS(idx, n) hs_in_bounds((long long)(idx), (long long)(n))
+#else
+#define HS_IN_BOUNDS(idx, n) true
+#endif
+
 // Operator kinds as compiled into kernels.
 // OP_BOX27: the HPCG 27-point system (diagonal 27, -1 on the 26 neighbours of
 // the 3x3x3 box), applied through separable box sums (3-D only).

@@ -216,7 +216,8 @@ __device__ __forceinline__ void gs_tile(const GsArgs<T>& a, T* sm, int tile, boo
       if (e < TOT) {
         const int ii = e % SX, jj = (e / SX) % SY, kk = e / (SX * SY);
         const int gi = i0 + ii - 1, gj = j0 + jj - 1, gk = k0 + kk - ZOFF;
-        if (gi >= 0 && gi < g.nx && gj >= 0 && gj < g.ny && gk >= 0 && gk < g.nz)
+        if (gi >= 0 && gi < g.nx && gj >= 0 && gj < g.ny && gk >= 0 && gk < g.nz &&
+            HS_IN_BOUNDS((long long)gk * g.plane + (long long)gj * g.nx + gi, g.N))
           v[u] = __ldcg(a.x + (long long)gk * g.plane + (long long)gj * g.nx + gi);
       }
     }
@@ -307,7 +308,7 @@ __device__ __forceinline__ void gs_tile(const GsArgs<T>& a, T* sm, int tile, boo
   for (int e = threadIdx.x; e < TX * TY * TZ; e += blockDim.x) {
     int ii = e % TX, jj = (e / TX) % TY, kk = e / (TX * TY);
     int gi = i0 + ii, gj2 = j0 + jj, gk2 = k0 + kk;
-    if (gi < g.nx && gj2 < g.ny && gk2 < g.nz)
+    if (gi < g.nx && gj2 < g.ny && gk2 < g.nz && HS_IN_BOUNDS((long long)gk2 * g.plane + (long long)gj2 * g.nx + gi, g.N))
       a.x[(long long)gk2 * g.plane + (long long)gj2 * g.nx + gi] = sm[((kk + ZOFF) * SY + (jj + 1)) * SX + ii + 1];
   }
   __syncthreads();
@@ -548,6 +549,7 @@ __device__ __forceinline__ void gs2d_node(const GsArgs<T>& a, T* xs, T bv, int i
   const Geom& g = a.g;
   const int nx = g.nx, ny = g.ny;
   const int c = j * nx + i;
+  if (!HS_IN_BOUNDS(c, g.N)) return;
   const T vW = i > 0 ? xs[c - 1] : T(0);
   const T vE = i + 1 < nx ? xs[c + 1] : T(0);
   const T vS = j > 0 ? xs[c - nx] : T(0);
@@ -580,7 +582,7 @@ __device__ void gs2d_batch(const GsArgs<T>& a, T* xs, const T* bsrc, int nsw, bo
       for (int t = t_lo + (((q - t_lo) % Q) + Q) % Q; t <= t_hi; t += Q) {
         const int r = s - 2 * t - i;
         const int jj = bw ? ny - 1 - r : r;
-        gs2d_node<T, OPK>(a, xs, __ldcg(bsrc + jj * nx + ii), ii, jj, bw);
+        if (HS_IN_BOUNDS(jj * nx + ii, a.g.N)) gs2d_node<T, OPK>(a, xs, __ldcg(bsrc + jj * nx + ii), ii, jj, bw);
       }
     }
     __syncthreads();
@@ -840,6 +842,8 @@ static hs_status gs_run_t(const SolveArgs& sa, hs_result* res, double* hist) {
     hs_status s = setup_vark(A, sa.dtype, D, ax, ay, az, false, sa.stream);
     if (s != HS_OK) return s;
   }
+  hs_status sd = hs_dbg_take(sa.stream);
+  if (sd != HS_OK) return sd;
   return finish_solve_pub(sa, cm, D, ax, ay, az, a.bD, res, hist, sa.tol > 0.0);
 }
 
@@ -917,6 +921,8 @@ static hs_status gs2d_run_t(const SolveArgs& sa, hs_result* res, double* hist) {
     s = setup_vark(A, sa.dtype, D, ax, ay, az, false, sa.stream);
     if (s != HS_OK) return s;
   }
+  s = hs_dbg_take(sa.stream);
+  if (s != HS_OK) return s;
   return finish_solve_pub(sa, cm, D, ax, ay, az, a.bD, res, hist, sa.tol > 0.0);
 }
 

@@ -5,6 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <string>
 
 #include "../../include/hsolve.h"
@@ -32,8 +34,40 @@ namespace hs {
 // diagonal 27 and -1 for each face (7) or box (27) neighbour, unscaled.
 enum { KIND_LAPLACIAN = 0, KIND_UPWIND = 1, KIND_DIFFUSION = 2, KIND_HPCG7 = 3, KIND_HPCG27 = 4 };
 
+// An NVTX range around each public call (header-only NVTX 3: a no-op unless
+// a profiler is attached), so that profiles and ncu's --nvtx filters can pick
+// out one solve: "hs_cg", "hs_bicgstab", ...
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 void set_error(const char* fmt, ...);
 hs_status cuda_fail(cudaError_t e, const char* what);
+
+// Debug builds: the bounds-check word of the calling translation unit
+// (hs_common.cuh), read and cleared after `st` has drained; HS_ERR_BOUNDS if
+// a check fired.  Release builds: HS_OK.
+static inline hs_status hs_dbg_take(cudaStream_t st) {
+#ifdef HS_DEBUG
+  unsigned long long w = 0;
+  cudaError_t e = cudaMemcpyFromSymbolAsync(&w, hs_dbg_word, sizeof(w), 0, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "debug word read-back");
+  if (w) {
+    const unsigned long long zero = 0;
+    cudaMemcpyToSymbolAsync(hs_dbg_word, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, st);
+    cudaStreamSynchronize(st);
+    set_error("debug bounds check: global index %lld out of range", (long long)(w - 1));
+    return HS_ERR_BOUNDS;
+  }
+#else
+  (void)st;
+#endif
+  return HS_OK;
+}
 
 inline int opkind_of(const hs_op* A) {
   if (A->kind == KIND_DIFFUSION) return OP_VARK;

@@ -547,7 +547,7 @@ hs_status run_spmv(const hs_op* A, hs_dtype dt, const void* x, void* y, cudaStre
     Tiling tl = choose_tiling(g, by, 0, false, 0, cx_st<OPK>());
     k_spmv<T, OPK, NDIM><<<tl.items(), 32 * by, slab_bytes<T>(by, cx_st<OPK>()), st>>>(g, tl, cf, (T)sigma, (const T*)x, (T*)y);
     cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? HS_OK : cuda_fail(e, "spmv launch");
+    return e == cudaSuccess ? hs_dbg_take(st) : cuda_fail(e, "spmv launch");
   });
 }
 
@@ -563,7 +563,7 @@ hs_status run_residual_plain(const hs_op* A, hs_dtype dt, const void* b, const v
     else
       k_sub_from<float><<<blocks, 256, 0, st>>>((const float*)b, (float*)r, g.N);
     cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? HS_OK : cuda_fail(e, "residual launch");
+    return e == cudaSuccess ? hs_dbg_take(st) : cuda_fail(e, "residual launch");
   }
   return dispatch(dt, opkind_of(A), A->ndim, [&](auto tag) -> hs_status {
     using Tg = decltype(tag);
@@ -577,7 +577,7 @@ hs_status run_residual_plain(const hs_op* A, hs_dtype dt, const void* b, const v
     k_residual<T, OPK, NDIM><<<tl.items(), 32 * by, slab_bytes<T>(by, cx_st<OPK>()), st>>>(g, tl, cf, (T)sigma, (const T*)b,
                                                                                (const T*)x, (T*)r, nullptr);
     cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? HS_OK : cuda_fail(e, "residual launch");
+    return e == cudaSuccess ? hs_dbg_take(st) : cuda_fail(e, "residual launch");
   });
 }
 
@@ -652,6 +652,10 @@ struct Tail {
 
 static hs_status finish_solve(const SolveArgs& sa, const Common& cm, const Tail& t, hs_result* res, double* hist,
                               bool want_hist) {
+  {
+    hs_status sd = hs_dbg_take(sa.stream);
+    if (sd != HS_OK) return sd;
+  }
   if (sa.o.true_residual) {
     hs_status s = residual_norms(t.A, t.dt, t.D, t.ax, t.ay, t.az, t.b, t.x, t.rbuf, &cm.ctrl->aux[0], cm.partials,
                                  sa.stream);

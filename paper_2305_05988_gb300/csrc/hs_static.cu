@@ -28,6 +28,7 @@ void* g_scratch_dev[kMaxDevices] = {nullptr};
 
 extern "C" hs_status hs_cg_static(const hs_op* A, hs_dtype dtype, const void* b, void* x, double tol, int maxit,
                                   const hs_opts* opts, void* stream, hs_result* res, double* hist) {
+  hs::NvtxRange range("hs_cg_static");
   if (res) {
     res->iters = 0;
     res->status = HS_ERR_INVALID;

@@ -162,15 +162,20 @@ __device__ __forceinline__ void zmarch_item(const Geom& g, const Tiling& tl, int
       r0[c] = SR{};
       h0[c] = SR{};
       if (NDIM == 3 && inside[c] && z0 > 0) {
-        SR rb = src.fetch(col[c] + (long long)(z0 - 1) * P);
-        vb[c] = src.make(rb, col[c] + (long long)(z0 - 1) * P, false);
+        if (HS_IN_BOUNDS(col[c] + (long long)(z0 - 1) * P, g.N)) {
+          SR rb = src.fetch(col[c] + (long long)(z0 - 1) * P);
+          vb[c] = src.make(rb, col[c] + (long long)(z0 - 1) * P, false);
+        }
       }
-      if (inside[c]) r0[c] = src.fetch(col[c] + (long long)z0 * P);
-      if (hin[c]) h0[c] = src.fetch(hcol[c] + (long long)z0 * P);
-      if (inside[c]) kown[c] = sink.fetch(col[c] + (long long)z0 * P, ii[c], j, z0);
+      if (inside[c] && HS_IN_BOUNDS(col[c] + (long long)z0 * P, g.N)) r0[c] = src.fetch(col[c] + (long long)z0 * P);
+      if (hin[c] && HS_IN_BOUNDS(hcol[c] + (long long)z0 * P, g.N)) h0[c] = src.fetch(hcol[c] + (long long)z0 * P);
+      if (inside[c] && HS_IN_BOUNDS(col[c] + (long long)z0 * P, g.N))
+        kown[c] = sink.fetch(col[c] + (long long)z0 * P, ii[c], j, z0);
       if (NDIM == 3 && z0 + 1 < g.nz) {
-        if (inside[c]) rown[c] = src.fetch(col[c] + (long long)(z0 + 1) * P);
-        if (hin[c] && z0 + 1 < z1) rhal[c] = src.fetch(hcol[c] + (long long)(z0 + 1) * P);
+        if (inside[c] && HS_IN_BOUNDS(col[c] + (long long)(z0 + 1) * P, g.N))
+          rown[c] = src.fetch(col[c] + (long long)(z0 + 1) * P);
+        if (hin[c] && z0 + 1 < z1 && HS_IN_BOUNDS(hcol[c] + (long long)(z0 + 1) * P, g.N))
+          rhal[c] = src.fetch(hcol[c] + (long long)(z0 + 1) * P);
       }
     }
 #pragma unroll
@@ -196,9 +201,12 @@ __device__ __forceinline__ void zmarch_item(const Geom& g, const Tiling& tl, int
     if (NDIM == 3) {
 #pragma unroll
       for (int c = 0; c < CX; c++) {
-        if (inside[c] && k + 2 < g.nz && k + 2 <= z1) rown2[c] = src.fetch(col[c] + (long long)(k + 2) * P);
-        if (hin[c] && k + 2 < z1) rhal2[c] = src.fetch(hcol[c] + (long long)(k + 2) * P);
-        if (inside[c] && k + 1 < z1) kown2[c] = sink.fetch(col[c] + (long long)(k + 1) * P, ii[c], j, k + 1);
+        if (inside[c] && k + 2 < g.nz && k + 2 <= z1 && HS_IN_BOUNDS(col[c] + (long long)(k + 2) * P, g.N))
+          rown2[c] = src.fetch(col[c] + (long long)(k + 2) * P);
+        if (hin[c] && k + 2 < z1 && HS_IN_BOUNDS(hcol[c] + (long long)(k + 2) * P, g.N))
+          rhal2[c] = src.fetch(hcol[c] + (long long)(k + 2) * P);
+        if (inside[c] && k + 1 < z1 && HS_IN_BOUNDS(col[c] + (long long)(k + 1) * P, g.N))
+          kown2[c] = sink.fetch(col[c] + (long long)(k + 1) * P, ii[c], j, k + 1);
       }
 #pragma unroll
       for (int c = 0; c < CX; c++) {
@@ -227,7 +235,7 @@ __device__ __forceinline__ void zmarch_item(const Geom& g, const Tiling& tl, int
         nb.n = slab<T, CX>(sm, by, buf, ly + 2, sx);
         nb.b = vb[c];
         nb.t = vt[c];
-        sink(col[c] + (long long)k * P, nb, kown[c], ii[c], j, k);
+        if (HS_IN_BOUNDS(col[c] + (long long)k * P, g.N)) sink(col[c] + (long long)k * P, nb, kown[c], ii[c], j, k);
       }
     }
     __syncthreads();
@@ -318,8 +326,8 @@ __device__ __forceinline__ void zmarch_box(const Geom& g, const Tiling& tl, int 
     rown = SR{};
     rhal = SR{};
     if (kk >= 0 && kk < g.nz) {
-      if (inside) rown = src.fetch(col + (long long)kk * P);
-      if (hin) rhal = src.fetch(hcol + (long long)kk * P);
+      if (inside && HS_IN_BOUNDS(col + (long long)kk * P, g.N)) rown = src.fetch(col + (long long)kk * P);
+      if (hin && HS_IN_BOUNDS(hcol + (long long)kk * P, g.N)) rhal = src.fetch(hcol + (long long)kk * P);
     }
   };
 
@@ -332,7 +340,7 @@ __device__ __forceinline__ void zmarch_box(const Geom& g, const Tiling& tl, int 
   SR rn, hn;
   fetch_plane(z0 + 1, rn, hn);          // plane z0 + 1, staged in the first step
   KR kown = KR{};
-  if (inside) kown = sink.fetch(col + (long long)z0 * P, i, j, z0);
+  if (inside && HS_IN_BOUNDS(col + (long long)z0 * P, g.N)) kown = sink.fetch(col + (long long)z0 * P, i, j, z0);
   T Pc = plane_P(z0, rb, hb, true, vc);
 
   for (int k = z0; k < z1; k++) {
@@ -340,7 +348,8 @@ __device__ __forceinline__ void zmarch_box(const Geom& g, const Tiling& tl, int 
     SR rn2, hn2;
     fetch_plane(k + 2 < z1 + 1 ? k + 2 : g.nz, rn2, hn2);
     KR kown2 = KR{};
-    if (inside && k + 1 < z1) kown2 = sink.fetch(col + (long long)(k + 1) * P, i, j, k + 1);
+    if (inside && k + 1 < z1 && HS_IN_BOUNDS(col + (long long)(k + 1) * P, g.N))
+      kown2 = sink.fetch(col + (long long)(k + 1) * P, i, j, k + 1);
     T vt;
     const T Pn = plane_P(k + 1, rn, hn, k + 1 < z1, vt);
     if (inside) {
@@ -348,7 +357,7 @@ __device__ __forceinline__ void zmarch_box(const Geom& g, const Tiling& tl, int 
       nb.c = vc;
       nb.box = (Pm + Pc) + Pn;
       nb.w = nb.e = nb.s = nb.n = nb.b = nb.t = T(0);
-      sink(col + (long long)k * P, nb, kown, i, j, k);
+      if (HS_IN_BOUNDS(col + (long long)k * P, g.N)) sink(col + (long long)k * P, nb, kown, i, j, k);
     }
     Pm = Pc;
     Pc = Pn;
@@ -392,6 +401,11 @@ __device__ __forceinline__ OpRaw<T, OPK> op_fetch(const Coef<T>& cf, const Geom&
                                                   int k) {
   OpRaw<T, OPK> r{};
   if constexpr (OPK == OP_VARK) {
+#ifdef HS_DEBUG
+    if (!HS_IN_BOUNDS(idx, g.N) || (i + 1 < g.nx && !HS_IN_BOUNDS(idx + 1, g.N)) ||
+        (j + 1 < g.ny && !HS_IN_BOUNDS(idx + g.nx, g.N)) || (NDIM == 3 && k + 1 < g.nz && !HS_IN_BOUNDS(idx + g.plane, g.N)))
+      return r;
+#endif
     r.d = __ldg(cf.D + idx);
     r.xl = __ldg(cf.ax + idx);
     r.xu = (i + 1 < g.nx) ? __ldg(cf.ax + idx + 1) : T(0);
