@@ -62,12 +62,13 @@ BYTES = {
 FLOPS = {"spmv": 10.0, "jacobi": 9.0, "gauss_seidel": 9.0, "cg": 19.0, "bicgstab": 48.0}
 
 # DRAM bytes per unknown and iteration measured by ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum) on the 200^3 case of the same step (every vector is
-# 64 MB there, above the 129 MB L2 with the solver state; CG 825 iterations,
-# BiCGStab 452, Jacobi 20 sweeps in one launch each).  Traffic grows with unknowns x
-# iterations (each pass streams every vector), so a launch at 256^3 moves
-# this figure x N x iterations.  Re-measure whenever the kernel changes.
-TRAFFIC_B_PER_UNIT = {"cg": 72.6, "bicgstab": 137.0, "jacobi": 24.5}
+# dram__bytes_write.sum) on short launches of the same kernels at 256^3
+# (profiles/fp64_and_traffic_poisson3d_256.md: CG and BiCGStab 10 iterations,
+# Jacobi 20 sweeps, one launch per capture; the start-up residual pass is
+# subtracted).  Traffic grows with unknowns x iterations (each pass streams
+# every vector), so a launch of the step moves this figure x N x iterations.
+# Re-measure whenever the kernel changes.
+TRAFFIC_B_PER_UNIT = {"cg": 74.3, "bicgstab": 135.1, "jacobi": 24.9}
 # FP64 pipe: 2 FMA lanes per SM per clock (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on
 # peak_sustained = 2 per SM per cycle) x 2 flops x 152 SMs.
 FP64_FLOPS_PER_CLK = 2 * 2 * 152
@@ -422,7 +423,8 @@ def run_ours(args, rank, world, dist):
                                            "clock sampled in the timed region)" % (clk / 1e6),
                     "frac_of_derived": round(tflops / fp64_derived, 4),
                     "traffic": (round(TRAFFIC_B_PER_UNIT[dom] * N * its) if dom in TRAFFIC_B_PER_UNIT else None),
-                    "traffic_source": "ncu DRAM bytes per unknown-iteration at 200^3 x N x iterations",
+                    "traffic_source": "ncu DRAM bytes per unknown-iteration of a 10-iteration launch at 256^3 "
+                                      "x N x iterations",
                     "flops_per_unknown_iter": FLOPS[dom], "iters": its, "launch_ms": round(dt, 3),
                     "hbm": {"achieved": round(hbm_gbs, 1), "peak": peak, "unit": "GB/s",
                             "frac": round(hbm_gbs / peak, 4), "peak_source": peak_kind,
