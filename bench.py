@@ -735,7 +735,7 @@ def adjoint_timing(n, dev, tmo):
     shape = (n, n, n)
     logk = torch.from_numpy(inputs.log_k(shape, 0.5, 0)).to(dev).requires_grad_(True)
     f = torch.from_numpy(inputs.rhs_uniform(shape, 0)).to(dev).requires_grad_(True)
-    k2 = torch.from_numpy(np.exp(inputs.log_k(shape, 0.5, 0, inputs.STREAM_K2))).to(dev)
+    k2 = hs.exp_logk(torch.from_numpy(inputs.log_k(shape, 0.5, 0, inputs.STREAM_K2)).to(dev))
     u_obs = hs.cg(hs.Operator.diffusion(shape, k2), f.detach(), tol=1e-12, maxit=200000, history=False,
                   timeout_s=max(tmo, 10.0))[0]
     stream = torch.cuda.current_stream(dev)

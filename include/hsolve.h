@@ -291,6 +291,17 @@ hs_status hs_solve_mixed(const hs_op *A, const double *b, double *x, double tol,
 hs_status hs_diffusion_grad_logk(const hs_op *A, const double *u, const double *lam, double *g,
                                  void *stream);
 
+/* k_i = exp(logk_i) for i < n: the diffusion coefficient field from the
+ * log-coefficients in which hs_diffusion_grad_logk differentiates (the inverse
+ * problem parametrises k > 0 by log k; not in the paper).  logk, k: FP64
+ * device vectors of n elements; k may be logk itself (in place) but must not
+ * overlap it otherwise.  exp overflows to +inf above log k = 709.78 and
+ * underflows to 0 below about -745; neither is a valid coefficient for
+ * hs_op_diffusion, so callers keep log k well inside that range.
+ * Asynchronous on `stream`.  HS_ERR_INVALID: n < 0, NULL vectors with n > 0,
+ * partial overlap. */
+hs_status hs_exp_logk(const double *logk, double *k, int64_t n, void *stream);
+
 /* ---- conjugate gradient without any allocation --------------------------
  * The paper has no counterpart to this entry point; it exists for callers
  * that cannot allocate device memory themselves -- for example a plug-in

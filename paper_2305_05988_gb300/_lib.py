@@ -93,6 +93,7 @@ SIGNATURES = {
     "hs_solve_mixed": (_i, [_vp, _vp, _vp, _d, _i, ctypes.POINTER(hs_opts), _vp, _sz, _vp,
                             ctypes.POINTER(hs_result), ctypes.POINTER(_d)]),
     "hs_diffusion_grad_logk": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "hs_exp_logk": (_i, [_vp, _vp, ctypes.c_int64, _vp]),
     "hs_cg_static": (_i, [_vp, _i, _vp, _vp, _d, _i, ctypes.POINTER(hs_opts), _vp,
                           ctypes.POINTER(hs_result), ctypes.POINTER(_d)]),
     "hs_batch_create": (_i, [_i, ctypes.POINTER(_vp), ctypes.POINTER(_i), ctypes.POINTER(_vp)]),

@@ -69,7 +69,31 @@ static hs_status launch_grad(const hs_op* A, const double* u, const double* lam,
   return e == cudaSuccess ? HS_OK : cuda_fail(e, "gradient launch");
 }
 
+// k_i = exp(log k_i): the diffusion coefficient from its logarithm, the
+// parametrisation in which the gradient above is taken.
+__global__ void __launch_bounds__(256) k_exp_logk(const double* logk, double* k, long long n) {
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x)
+    k[idx] = exp(logk[idx]);
+}
+
 }  // namespace hs
+
+extern "C" hs_status hs_exp_logk(const double* logk, double* k, int64_t n, void* stream) {
+  if (n < 0 || (n > 0 && (!logk || !k))) {
+    hs::set_error("hs_exp_logk: NULL vector or negative length");
+    return HS_ERR_INVALID;
+  }
+  if (n == 0) return HS_OK;
+  if (k != logk && ((k < logk && k + n > logk) || (logk < k && logk + n > k))) {
+    hs::set_error("hs_exp_logk: k overlaps logk without being the same array");
+    return HS_ERR_INVALID;
+  }
+  int blocks = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, (long long)hs::sm_count() * 16));
+  hs::k_exp_logk<<<blocks, 256, 0, (cudaStream_t)stream>>>(logk, k, (long long)n);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? HS_OK : hs::cuda_fail(e, "exp(log k) launch");
+}
 
 extern "C" hs_status hs_diffusion_grad_logk(const hs_op* A, const double* u, const double* lam, double* g,
                                             void* stream) {

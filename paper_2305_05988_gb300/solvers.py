@@ -343,6 +343,24 @@ def grad_logk(A: Operator, u: torch.Tensor, lam: torch.Tensor, out: Optional[tor
     return g
 
 
+def exp_logk(logk: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """k = exp(logk) on the GPU (hs_exp_logk): the diffusion coefficient field
+    from its logarithm.  logk: contiguous float64 CUDA tensor."""
+    if not isinstance(logk, torch.Tensor) or not logk.is_cuda or logk.dtype != torch.float64:
+        raise TypeError("logk must be a float64 CUDA tensor")
+    if not logk.is_contiguous():
+        raise ValueError("logk must be contiguous")
+    if out is None:
+        out = torch.empty_like(logk)
+    elif out.shape != logk.shape or out.dtype != torch.float64 or not out.is_contiguous() or out.device != logk.device:
+        raise ValueError("out must be a contiguous float64 tensor shaped like logk on its device")
+    with torch.cuda.device(logk.device):
+        st = torch.cuda.current_stream(logk.device).cuda_stream
+        check(_lib.load().hs_exp_logk(ctypes.c_void_p(logk.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                      logk.numel(), ctypes.c_void_p(st)), "hs_exp_logk")
+    return out
+
+
 class DiffusionSolve(torch.autograd.Function):
     """u = A(exp(logk))^{-1} f for the variable-coefficient diffusion operator,
     differentiable in logk and f.  The backward pass solves the adjoint system
@@ -351,7 +369,7 @@ class DiffusionSolve(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, logk, f, shape, tol=1e-12, mixed=False, maxit=100000):
-        k = torch.exp(logk.detach()).contiguous()
+        k = exp_logk(logk.detach().contiguous())
         A = Operator.diffusion(shape, k)
         fd = f.detach().contiguous()
         if mixed:

@@ -194,6 +194,19 @@ def test_diag_wait_validation(lib):
     assert lib.hs_diag_wait_timeout(2, float("nan"), None) == _lib.HS_ERR_INVALID
 
 
+def test_exp_logk_validation(lib):
+    # rejected (or, for n = 0, finished) before anything reaches the GPU
+    vp = ctypes.c_void_p
+    assert lib.hs_exp_logk(vp(4096), vp(8192), -1, None) == _lib.HS_ERR_INVALID
+    assert lib.hs_exp_logk(None, vp(8192), 10, None) == _lib.HS_ERR_INVALID
+    assert lib.hs_exp_logk(vp(4096), None, 10, None) == _lib.HS_ERR_INVALID
+    assert lib.hs_exp_logk(None, None, 0, None) == _lib.HS_OK
+    # partial overlap (k starts 8 elements into logk's 10)
+    assert lib.hs_exp_logk(vp(4096), vp(4096 + 64), 10, None) == _lib.HS_ERR_INVALID
+    assert lib.hs_exp_logk(vp(4096 + 64), vp(4096), 10, None) == _lib.HS_ERR_INVALID
+    assert b"overlap" in lib.hs_last_error()
+
+
 def test_gauss_seidel_workspace_sizes(lib):
     # GS keeps b / a_ii (one vector) plus its schedule: tile-plane tables,
     # per-tile sweep counts and a claim counter (7-point), or per-block

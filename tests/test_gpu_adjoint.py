@@ -83,3 +83,34 @@ def test_gradient_requires_diffusion_operator():
     u = torch.zeros(64, dtype=torch.float64, device="cuda")
     with pytest.raises(ValueError):
         hs.grad_logk(A, u, u)
+
+
+def test_exp_logk_against_libm_and_in_place():
+    # k = exp(log k) on the GPU against numpy's exp: both are within an ulp of
+    # the exact exponential, so they differ by at most 2 ulp (4.5e-16 relative)
+    N = 100003                        # not a multiple of the block size
+    logk = inputs.normal(5, inputs.STREAM_K, N, 1.0) * 3.0
+    logk[:4] = [0.0, -700.0, 700.0, 1e-300]
+    lt = dev(logk)
+    k = hs.exp_logk(lt).cpu().numpy()
+    ref = np.exp(logk)
+    assert np.all(np.abs(k - ref) <= 4.5e-16 * ref)
+    assert k[0] == 1.0 and k[3] == 1.0
+    hs.exp_logk(lt, out=lt)           # in place
+    assert np.array_equal(lt.cpu().numpy(), k)
+    with pytest.raises(TypeError):
+        hs.exp_logk(lt.float())
+
+
+def test_diffusion_solve_forms_k_in_the_library():
+    # the differentiable solve's operator uses exp(log k) from hs_exp_logk:
+    # its solution equals a solve on that coefficient field
+    shape = (20, 17, 9)
+    N = int(np.prod(shape))
+    logk = dev(inputs.normal(6, inputs.STREAM_K, N, 0.5))
+    f = dev(inputs.uniform_pm1(7, 1, N))
+    u = hs.diffusion_solve(logk, f, shape, tol=1e-12)
+    A = hs.Operator.diffusion(shape, hs.exp_logk(logk))
+    u2, info = hs.cg(A, f, tol=1e-12, maxit=100000, history=False)
+    assert info.status == "OK"
+    assert torch.equal(u, u2)

@@ -157,8 +157,10 @@ def adjoint256():
     shape = N3
     logk = inputs.log_k(shape, 0.5, 0)
     f = inputs.rhs_uniform(shape, 0)
-    k = np.exp(logk)
-    kt = torch.from_numpy(k).cuda()
+    # k = exp(log k) formed by the library, as DiffusionSolve does; the
+    # oracle's side takes numpy's exp (the two differ by at most an ulp)
+    kt = hs.exp_logk(torch.from_numpy(logk).cuda())
+    k = kt.cpu().numpy()
     A_g = hs.Operator.diffusion(shape, kt)
     ft = torch.from_numpy(f).cuda()
     k2 = torch.from_numpy(np.exp(inputs.log_k(shape, 0.5, 0, inputs.STREAM_K2))).cuda()
@@ -245,7 +247,7 @@ def test_adjoint_full_size_central_differences(adjoint256, variant):
     d_obs = 2 * (u - u_obs)
 
     def dloss(lkt):
-        A_p = hs.Operator.diffusion(shape, torch.exp(lkt).contiguous())
+        A_p = hs.Operator.diffusion(shape, hs.exp_logk(lkt))
         du = solve(A_p, (Au - A_p.spmv(u)).contiguous())
         return torch.sum(du * (du + d_obs)).item()
 
