@@ -136,6 +136,14 @@ typedef struct {
                                (4 B per node; 3-D, n_x a multiple of 4,
                                n_x >= 40, n_y >= 10, n_z >= 3, else
                                HS_ERR_INVALID)                                  */
+    int inner_fixed_tol;    /* mixed precision (hs_solve_mixed and the mixed
+                               batch): 0 (default) a refinement step whose
+                               FP64 relative residual rel_k is already near
+                               tol stops its inner solve early, at the inner
+                               relative tolerance max(inner_tol,
+                               0.5 tol / rel_k), which is all the step needs
+                               to reach tol; 1: every inner solve runs to
+                               inner_tol                                       */
 } hs_opts;
 
 typedef struct {

@@ -50,7 +50,8 @@ class hs_opts(ctypes.Structure):
                 ("sweeps_per_pass", ctypes.c_int),
                 ("alpha_trace", ctypes.POINTER(ctypes.c_double)),
                 ("restart_iters", ctypes.POINTER(ctypes.c_int)),
-                ("staging", ctypes.c_int)]
+                ("staging", ctypes.c_int),
+                ("inner_fixed_tol", ctypes.c_int)]
 
 
 class hs_result(ctypes.Structure):

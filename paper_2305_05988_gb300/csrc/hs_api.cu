@@ -116,6 +116,7 @@ bool merge_opts(const hs_opts* in, hs_opts* out) {
   if (out->tile_planes < 0) out->tile_planes = 0;
   if (out->max_blocks < 0) out->max_blocks = 0;
   out->paper_order = out->paper_order ? 1 : 0;
+  out->inner_fixed_tol = out->inner_fixed_tol ? 1 : 0;
   if (out->sweeps_per_pass < 1) out->sweeps_per_pass = 1;
   if (out->staging < 0 || out->staging > 1) {
     set_error("hs_opts.staging must be 0 (register prefetch) or 1 (TMA)");

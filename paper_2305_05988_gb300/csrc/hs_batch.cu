@@ -399,6 +399,8 @@ static hs_status fill_mixed(hs_batch* B, int s, const double* b, double* x, doub
   d.max_outer = maxit;
   d.tol = tol;
   d.restart_eps = o.restart_eps;
+  d.inner_tol = o.inner_tol;
+  d.inner_fixed = o.inner_fixed_tol;
   d.g = p.g;
   d.tl = p.tl;
   d.cf = op_coef<double>(A, D, ax, ay, az, &d.sigma);

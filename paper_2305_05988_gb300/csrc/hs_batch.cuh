@@ -52,6 +52,9 @@ struct MxSys {
   int max_outer;         // refinement steps
   double tol;            // FP64 relative residual
   double restart_eps;    // inner BiCGStab restart threshold for a unit-norm right-hand side
+  double inner_tol;      // inner relative tolerance (tightest)
+  int inner_fixed;       // 1: every inner solve to inner_tol; 0: a step near tol stops earlier
+  int pad_;
   Geom g;
   Tiling tl;             // tiling of the FP64 residual pass
   Coef<double> cf;       // FP64 operator (scaled form, A = sigma * cf)

@@ -103,8 +103,18 @@ __device__ void mx_body(MxSys& a, const Team& tm, unsigned char* smraw, double* 
     // inner FP32 solve of A d = r32; BiCGStab's absolute restart threshold
     // is applied to the unit-norm right-hand side, as in the standalone
     // mixed solver: scale it by ||r32||
-    if constexpr (BI) {
-      if (threadIdx.x == 0) a.bi.reps = a.restart_eps * sqrt(s2[0]) * scale;
+    // a step close to tol stops its inner solve once tol is within reach
+    // (the same decision in every block of the team: rel is team-reduced)
+    {
+      const double itol = a.inner_fixed ? a.inner_tol : inner_tol_for(a.inner_tol, a.tol, rel);
+      if (threadIdx.x == 0) {
+        if constexpr (BI) {
+          a.bi.reps = a.restart_eps * sqrt(s2[0]) * scale;
+          a.bi.tol = itol;
+        } else {
+          a.cg.tol = itol;
+        }
+      }
       __syncthreads();
     }
     BodyOut io;

@@ -145,6 +145,15 @@ struct SolveArgs {
 // for k = 0 .. maxit, plus one spare pair).
 inline size_t bicgstab_trace_len(int maxit) { return 2 * ((size_t)maxit + 2); }
 
+// Inner relative tolerance of one mixed-precision refinement step whose FP64
+// relative residual is rel: the step has to bring the residual from rel to
+// tol, so its inner solve needs tol / rel at most; half of that leaves room
+// for the FP32 rounding of the correction.  Never tighter than inner_tol.
+__host__ __device__ inline double inner_tol_for(double inner_tol, double tol, double rel) {
+  const double need = rel > 0.0 ? 0.5 * tol / rel : 0.0;
+  return need > inner_tol ? need : inner_tol;
+}
+
 // Per-solver workspace size (bytes), excluding nothing: callers add nothing.
 size_t ws_bytes_for(const hs_op* A, hs_solver s, hs_dtype dt, int maxit);
 

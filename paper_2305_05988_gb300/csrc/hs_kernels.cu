@@ -1089,13 +1089,18 @@ hs_status run_mixed(const SolveArgs& sa, hs_result* res, double* hist) {
       break;
     }
     if (outer == max_outer) break;
-    // FP32 correction solve on the normalised residual
+    // FP32 correction solve on the normalised residual.  The step needs the
+    // inner residual only down to tol / rel (the FP64 residual after the
+    // update is rel times the inner one, plus the FP32 rounding of the
+    // correction): a last step close to tol stops its inner solve there
+    // (with a factor 2 of margin) instead of running to inner_tol.
+    const double itol = sa.o.inner_fixed_tol ? sa.o.inner_tol : inner_tol_for(sa.o.inner_tol, sa.tol, rel);
     const double rn = sqrt(nrm[0]);
     k_r_to_f32<<<blocks, 256, 0, st>>>(L.r64, L.r32, 1.0 / rn, g.N);
     e = cudaMemsetAsync(L.d32, 0, sizeof(float) * (size_t)g.N, st);
     if (e != cudaSuccess) return cuda_fail(e, "mixed: zero correction");
     if (tma)
-      s = cg32v_core(A, L.D32, L.r32, L.d32, sa.o.inner_tol, sa.o.inner_maxit, L.inner, L.v32[0], L.v32[1],
+      s = cg32v_core(A, L.D32, L.r32, L.d32, itol, sa.o.inner_maxit, L.inner, L.v32[0], L.v32[1],
                      L.v32[2], L.v32[3], sa.o, st);
     else
       s = dispatch(HS_F32, opk, A->ndim, [&](auto tag) -> hs_status {
@@ -1108,12 +1113,12 @@ hs_status run_mixed(const SolveArgs& sa, hs_result* res, double* hist) {
         double sigma;
         Coef<T> cf = op_coef<T>(A, L.D32, L.ax32, L.ay32, L.az32, &sigma);
         if (use_bicg)
-          return bicgstab_core<T, OPK, NDIM>(A, cf, sigma, L.r32, L.d32, sa.o.inner_tol, sa.o.inner_maxit, L.inner,
+          return bicgstab_core<T, OPK, NDIM>(A, cf, sigma, L.r32, L.d32, itol, sa.o.inner_maxit, L.inner,
                                              L.v32, sa.o, st);
         if constexpr (OPK == OP_NONSYM) {
           return HS_ERR_INVALID;
         } else {
-          return cg_core<T, OPK, NDIM>(A, cf, sigma, L.r32, L.d32, sa.o.inner_tol, sa.o.inner_maxit, L.inner,
+          return cg_core<T, OPK, NDIM>(A, cf, sigma, L.r32, L.d32, itol, sa.o.inner_maxit, L.inner,
                                        L.v32[0], L.v32[1], L.v32[2], L.v32[3], sa.o, st);
         }
       }

@@ -181,7 +181,7 @@ def make_opts(**kw) -> _lib.hs_opts:
             v = _GS_MODES[v]
         if k == "inner_solver" and isinstance(v, str):
             v = {"cg": _lib.HS_SOLVER_CG, "bicgstab": _lib.HS_SOLVER_BICGSTAB}[v]
-        if k in ("true_residual", "use_graph", "paper_order"):
+        if k in ("true_residual", "use_graph", "paper_order", "inner_fixed_tol"):
             v = int(bool(v))
         if not hasattr(o, k):
             raise TypeError("unknown solver option %r" % k)

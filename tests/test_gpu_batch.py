@@ -203,6 +203,28 @@ def test_batch_mixed_matches_standalone_mixed_counts():
     assert torch.linalg.norm(xb[0] - xs).item() <= 1e-8 * torch.linalg.norm(xs).item()
 
 
+def test_batch_mixed_adaptive_inner_tolerance():
+    # the mixed batch applies the same rule as the standalone refinement: a
+    # step close to tol runs its inner solve only to 0.5 tol / rel; fewer inner
+    # iterations in total, every system still certified by the oracle
+    systems = small_batch(12, 36, seed=17)
+    ops_o, ops_g, bs, _ks = build_mixed(systems, vark_every=3)
+    batch = hs.Batch(ops_g, ["mixed"] * len(ops_g))
+    tol = 1e-10
+    s = torch.cuda.Stream()
+    runs = {}
+    for fixed in (1, 0):
+        with torch.cuda.stream(s):
+            xs, infos = batch.solve([dev(b) for b in bs], tol=tol, maxit=30, inner_tol=1e-4, inner_maxit=20000,
+                                    inner_fixed_tol=fixed)
+        s.synchronize()
+        for A_o, b, x, info in zip(ops_o, bs, xs, infos):
+            assert info.status == "OK", info
+            assert A_o.relres(b, x.cpu().numpy()) <= tol * (1 + 1e-3)
+        runs[fixed] = infos
+    assert sum(i.inner_iters for i in runs[0]) <= sum(i.inner_iters for i in runs[1])
+
+
 def test_batch_mixed_poisoned_and_all_or_none():
     systems = small_batch(12, 20, seed=17)
     ops_o, ops_g, bs, _ = build_mixed(systems)

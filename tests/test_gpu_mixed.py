@@ -99,3 +99,26 @@ def test_mixed_zero_rhs_and_errors():
     U_o, U_g, _ = ops((20, 14), "up")
     with pytest.raises(hs.solvers._lib.HsError):
         hs.solve_mixed(U_g, dev(inputs.uniform_pm1(36, 1, U_o.N)), inner_solver="cg")
+
+
+@pytest.mark.parametrize("inner", ["cg", "bicgstab"])
+def test_last_step_stops_its_inner_solve_at_what_tol_needs(inner):
+    # inner_fixed_tol = 0 (default): a refinement step with FP64 relative
+    # residual rel runs its inner solve to max(inner_tol, 0.5 tol / rel) only.
+    # Every step before the first one where that bound exceeds inner_tol is
+    # the same computation in both modes (bitwise equal histories); the
+    # adaptive run takes no more inner iterations, and both are certified.
+    shape = (64, 48, 40)
+    A_o, A_g, _k = ops(shape, "vark")
+    b = inputs.uniform_pm1(37, 1, A_o.N)
+    tol, itol = 1e-10, 1e-4
+    xf, f = hs.solve_mixed(A_g, dev(b), tol=tol, maxit=30, inner_tol=itol, inner_solver=inner, inner_fixed_tol=1)
+    xa, a = hs.solve_mixed(A_g, dev(b), tol=tol, maxit=30, inner_tol=itol, inner_solver=inner)
+    assert f.status == "OK" and a.status == "OK"
+    for x in (xf, xa):
+        assert A_o.relres(b, x.cpu().numpy()) <= tol * (1 + 1e-3)
+    k = next(k for k in range(len(f.history)) if 0.5 * tol / f.history[k] > itol)
+    assert np.array_equal(a.history[:k + 1], f.history[:k + 1]), (a.history, f.history)
+    assert a.inner_iters <= f.inner_iters, (a.inner_iters, f.inner_iters)
+    print("inner iterations: fixed %d (%d steps), adaptive %d (%d steps)" % (f.inner_iters, f.outer, a.inner_iters,
+                                                                            a.outer))
