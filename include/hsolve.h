@@ -144,6 +144,22 @@ typedef struct {
                                0.5 tol / rel_k), which is all the step needs
                                to reach tol; 1: every inner solve runs to
                                inner_tol                                       */
+    int gs_schedule;        /* lexicographic Gauss-Seidel on 3-D grids: 0
+                               (default) the pencil schedule for batches of
+                               four or more sweeps of one direction on
+                               constant-coefficient operators with between
+                               12 pencils per SM and one pencil per resident
+                               warp, the tile schedule otherwise; 1 the tile
+                               schedule (tiles of
+                               32 x 8 x 8 or 32 x 16 x 16 nodes swept along
+                               point hyperplanes in shared memory, ordered by
+                               per-tile sweep counts); 2 the pencil schedule
+                               (one warp per 8 x 4 x-lines streaming two nodes
+                               per substep, neighbour lines by warp shuffles,
+                               ordered by per-pencil progress counts; 3-D
+                               Laplacian / upwind operators only, else
+                               HS_ERR_INVALID).  Both give bitwise the same
+                               iterates.                                       */
 } hs_opts;
 
 typedef struct {

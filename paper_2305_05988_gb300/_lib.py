@@ -51,7 +51,8 @@ class hs_opts(ctypes.Structure):
                 ("alpha_trace", ctypes.POINTER(ctypes.c_double)),
                 ("restart_iters", ctypes.POINTER(ctypes.c_int)),
                 ("staging", ctypes.c_int),
-                ("inner_fixed_tol", ctypes.c_int)]
+                ("inner_fixed_tol", ctypes.c_int),
+                ("gs_schedule", ctypes.c_int)]
 
 
 class hs_result(ctypes.Structure):

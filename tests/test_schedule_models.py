@@ -280,3 +280,276 @@ def test_gs2d_schedule_model_catches_one_diagonal_shift():
             for a, b in [(i + 1, j), (i, j + 1)]:
                 if a < nx and b < ny and t > 0:
                     assert visit[(t - 1, a, b)] < s
+
+
+# ---------------------------------------------------------------- 7-point pencils
+
+def _model_gsp(shape, PY, PZ, W, dirs, seed, CH=3, PF=2, PFO=3, short_need=0, drop_old_side=False):
+    """The pencil schedule of the 7-point Gauss-Seidel kernel (hs_gs.cu,
+    k_gsp).  A warp owns PY x PZ x-lines (lane = jl + PY kl) and sweeps them
+    two nodes (a pair) per substep, lane (jl, kl) on sweep-frame pair u - D at
+    substep u, D = jl + kl in the sweep's mirrored frame.  Neighbour lines of
+    the pencil come from the lanes' registers as shuffles (new side: the
+    neighbour's last computed pair; old side: the neighbour's next old pair);
+    lines of other pencils from global memory, loaded PF substeps ahead, after
+    waiting (per chunk of CH substeps) until the new-side pencils have
+    published enough pairs of this sweep and the old-side pencils of the
+    previous one.  Own-line old values are loaded PFO substeps ahead.  Stores
+    become visible to other warps only at the chunk's publish; a load of
+    another warp's line must see published data that nobody rewrites before
+    the load is used.  Returns (model result, sequential result)."""
+    nx, ny, nz = shape
+    nJ, nK = -(-ny // PY), -(-nz // PZ)
+    NP, NQ, Dmax = nJ * nK, -(-nx // 2), (PY - 1) + (PZ - 1)
+    NU = NQ + Dmax
+    rng = np.random.default_rng(seed)
+    x0 = rng.uniform(-1, 1, (nx, ny, nz))
+    bD = rng.uniform(-1, 1, (nx, ny, nz))
+    cxl, cxu, cyl, cyu, czl, czu = rng.uniform(0.02, 0.16, 6)
+
+    def at(x, i, j, k):
+        return x[i, j, k] if 0 <= i < nx and 0 <= j < ny and 0 <= k < nz else 0.0
+
+    # sequential reference: the same two-part update, old side then new side
+    ref = x0.copy()
+    for bw in dirs:
+        rng_k = range(nz - 1, -1, -1) if bw else range(nz)
+        for k in rng_k:
+            for j in (range(ny - 1, -1, -1) if bw else range(ny)):
+                for i in (range(nx - 1, -1, -1) if bw else range(nx)):
+                    s = 1 if bw else -1          # step towards the new side
+                    ox, nxv = at(ref, i - s, j, k), at(ref, i + s, j, k)
+                    oy, nyv = at(ref, i, j - s, k), at(ref, i, j + s, k)
+                    oz, nzv = at(ref, i, j, k - s), at(ref, i, j, k + s)
+                    co = (cxl, cyl, czl) if bw else (cxu, cyu, czu)
+                    cn = (cxu, cyu, czu) if bw else (cxl, cyl, czl)
+                    y = co[0] * ox + bD[i, j, k]
+                    y = co[1] * oy + y
+                    y = co[2] * oz + y
+                    y = cn[0] * nxv + y
+                    y = cn[1] * nyv + y
+                    y = cn[2] * nzv + y
+                    ref[i, j, k] = y
+
+    X = x0.copy()                 # globally visible values
+    owner = {}                    # address -> warp that last stored it
+    pend = {}                     # warp -> {address: value} stored, not yet published
+    stamp = {}                    # address -> count of stores issued
+    prog = [0] * NP
+    state = {"stores": 0}
+
+    def store(w, addr, v):
+        pend[w][addr] = v
+        stamp[addr] = stamp.get(addr, 0) + 1
+        owner[addr] = w
+
+    def load(w, addr):
+        # (value, address, stamp at issue): own pending stores are seen in
+        # program order; another warp's unpublished store is a hazard
+        if addr in pend[w]:
+            return (pend[w][addr], addr, stamp.get(addr, 0))
+        for w2, pe in pend.items():
+            assert w2 == w or addr not in pe, "read of another warp's unpublished store at %s" % (addr,)
+        return (X[addr], addr, stamp.get(addr, 0))
+
+    def use(w, ld):
+        v, addr, st0 = ld
+        if addr is not None and owner.get(addr, w) != w:
+            assert stamp.get(addr, 0) == st0, "value at %s rewritten while in flight" % (addr,)
+        return v
+
+    ZERO = (0.0, None, 0)
+
+    def warp(w):
+        pend[w] = {}
+        per = -(-NP // W)                       # consecutive pencils per warp
+        mine = list(range(w * per, min(NP, (w + 1) * per)))
+        for t, bw in enumerate(dirs):
+            for p in (reversed(mine) if bw else mine):
+                J, K = p % nJ, p // nJ
+                s = 1 if bw else -1                      # step towards the new side
+                newn = [(J + s, K), (J, K + s)]
+                oldn = [(J - s, K), (J, K - s)]
+                newp = [q[0] + nJ * q[1] for q in newn if 0 <= q[0] < nJ and 0 <= q[1] < nK]
+                oldp = [q[0] + nJ * q[1] for q in oldn if 0 <= q[0] < nJ and 0 <= q[1] < nK]
+                same_dir = t > 0 and dirs[t - 1] == bw
+                lanes = []
+                for l in range(PY * PZ):
+                    jl, kl = l % PY, l // PY
+                    jm, km = (PY - 1 - jl, PZ - 1 - kl) if bw else (jl, kl)
+                    j, k = J * PY + jl, K * PZ + kl
+                    lanes.append(dict(jl=jl, kl=kl, jm=jm, km=km, D=jm + km, j=j, k=k,
+                                      valid=j < ny and k < nz))
+
+                def pos(qq):
+                    # sweep-frame pair qq -> (first, second) x positions, None outside
+                    if qq < 0 or qq >= NQ:
+                        return (None, None)
+                    q = NQ - 1 - qq if bw else qq
+                    a, b = (2 * q + 1, 2 * q) if bw else (2 * q, 2 * q + 1)
+                    return (a if a < nx else None, b if b < nx else None)
+
+                def ld_pair(wq, qq, j, k):
+                    if not (0 <= j < ny and 0 <= k < nz):
+                        return (ZERO, ZERO)
+                    a, b = pos(qq)
+                    return tuple(load(wq, (i, j, k)) if i is not None else ZERO for i in (a, b))
+
+                # registers: per lane dicts keyed by sweep-frame pair
+                for L in lanes:
+                    L["O"], L["B"], L["NY"], L["NZ"], L["OY"], L["OZ"] = {}, {}, {}, {}, {}, {}
+                    L["last"] = (0.0, 0.0)
+
+                def issue(L, u):
+                    # loads issued at substep u (prologue: u < 0 covers the window)
+                    if not L["valid"]:
+                        return
+                    j, k, D = L["j"], L["k"], L["D"]
+                    qo = u - D + PFO                     # own old pair
+                    if 0 <= qo < NQ:
+                        L["O"][qo] = ld_pair(w, qo, j, k)
+                        a, b = pos(qo)
+                        L["B"][qo] = tuple((bD[i, j, k], None, 0) if i is not None else ZERO for i in (a, b))
+                    qb = u - D + PF                      # pencil-boundary pairs
+                    if 0 <= qb < NQ:
+                        if L["jm"] == 0:
+                            L["NY"][qb] = ld_pair(w, qb, j + s, k)
+                        if L["km"] == 0:
+                            L["NZ"][qb] = ld_pair(w, qb, j, k + s)
+                        if L["jm"] == PY - 1:
+                            L["OY"][qb] = ld_pair(w, qb, j - s, k)
+                        if L["km"] == PZ - 1:
+                            L["OZ"][qb] = ld_pair(w, qb, j, k - s)
+
+                def ready(c):
+                    need = min(NQ, (c + 1) * CH + PF - short_need)
+                    if any(prog[q] < t * NQ + need for q in newp):
+                        return False
+                    if t > 0 and not drop_old_side:
+                        tgt = (t - 1) * NQ + need if same_dir else t * NQ
+                        if any(prog[q] < tgt for q in oldp):
+                            return False
+                    return prog[p] >= t * NQ                 # the pencil's previous sweep
+
+                nchunks = -(-NU // CH)
+                for c in range(nchunks):
+                    while not ready(c):
+                        yield False
+                    if c == 0:
+                        for L in lanes:
+                            for u in range(-max(PF, PFO), 0):
+                                issue(L, u)
+                    for u in range(c * CH, min((c + 1) * CH, NU)):
+                        snap = [dict(last=L["last"]) for L in lanes]
+                        for L in lanes:
+                            # the old pair a lane processes next: its new-side
+                            # neighbour line processes that pair now
+                            qn = u - L["D"] + 1
+                            L["onx_shared"] = L["O"].get(qn, (ZERO, ZERO)) if L["valid"] else (ZERO, ZERO)
+                        for idx, L in enumerate(lanes):
+                            qq = u - L["D"]
+                            if not (L["valid"] and 0 <= qq < NQ):
+                                continue
+                            jl, kl = L["jl"], L["kl"]
+                            # lane offsets of the new-side / old-side neighbour lines
+                            dyn = 1 if bw else -1
+                            if L["jm"] == 0:
+                                ny_ = tuple(use(w, v) for v in L["NY"].pop(qq))
+                            else:
+                                ny_ = snap[idx + dyn]["last"]
+                            if L["km"] == 0:
+                                nz_ = tuple(use(w, v) for v in L["NZ"].pop(qq))
+                            else:
+                                nz_ = snap[idx + dyn * PY]["last"]
+                            if L["jm"] == PY - 1:
+                                oy = tuple(use(w, v) for v in L["OY"].pop(qq))
+                            else:
+                                oy = tuple(use(w, v) for v in lanes[idx - dyn]["onx_shared"])
+                            if L["km"] == PZ - 1:
+                                oz = tuple(use(w, v) for v in L["OZ"].pop(qq))
+                            else:
+                                oz = tuple(use(w, v) for v in lanes[idx - dyn * PY]["onx_shared"])
+                            ocur = tuple(use(w, v) for v in L["O"].pop(qq))
+                            onx = tuple(use(w, v) for v in L["O"].get(qq + 1, (ZERO, ZERO)))
+                            bq = tuple(v[0] for v in L["B"].pop(qq))
+                            co = (cxl, cyl, czl) if bw else (cxu, cyu, czu)
+                            cn = (cxu, cyu, czu) if bw else (cxl, cyl, czl)
+                            a, b = pos(qq)
+                            # first node: x old = this pair's second, x new = previous pair's second
+                            y = co[0] * ocur[1] + bq[0]
+                            y = co[1] * oy[0] + y
+                            y = co[2] * oz[0] + y
+                            y = cn[0] * L["last"][1] + y
+                            y = cn[1] * ny_[0] + y
+                            na = cn[2] * nz_[0] + y if a is not None else 0.0
+                            y = co[0] * onx[0] + bq[1]
+                            y = co[1] * oy[1] + y
+                            y = co[2] * oz[1] + y
+                            y = cn[0] * na + y
+                            y = cn[1] * ny_[1] + y
+                            nb = cn[2] * nz_[1] + y if b is not None else 0.0
+                            L["newlast"] = (na, nb)
+                            j, k = L["j"], L["k"]
+                            if a is not None:
+                                store(w, (a, j, k), na)
+                            if b is not None:
+                                store(w, (b, j, k), nb)
+                        for L in lanes:
+                            if "newlast" in L:
+                                L["last"] = L.pop("newlast")
+                            issue(L, u)
+                        yield True
+                    # publish: stores become visible, then the progress count
+                    for addr, v in pend[w].items():
+                        X[addr] = v
+                    pend[w].clear()
+                    u_end = min((c + 1) * CH, NU)
+                    prog[p] = t * NQ + max(0, min(NQ, u_end - Dmax))
+                    yield True
+
+    gens = {w: warp(w) for w in range(W)}
+    rr = random.Random(seed)
+    live = set(gens)
+    stall = 0
+    while live:
+        w = rr.choice(sorted(live))
+        try:
+            moved = next(gens[w])
+        except StopIteration:
+            live.discard(w)
+            stall = 0
+            continue
+        stall = 0 if moved else stall + 1
+        assert stall < 200 * len(live) + 1000, "no warp can proceed (deadlock)"
+    return X, ref
+
+
+@pytest.mark.parametrize("shape,PY,PZ,W,dirs", [
+    ((9, 7, 5), 4, 2, 3, [0, 0, 0]),
+    ((8, 9, 6), 4, 2, 100, [0, 0]),
+    ((11, 6, 7), 2, 2, 4, [1, 1]),
+    ((7, 5, 9), 4, 2, 2, [0, 1, 0, 1]),
+    ((10, 8, 4), 4, 4, 1, [0, 0, 1]),
+    ((5, 3, 3), 8, 4, 5, [0, 1]),
+])
+def test_gsp_pencil_schedule_equals_sequential_sweeps(shape, PY, PZ, W, dirs):
+    for seed in range(3):
+        X, ref = _model_gsp(shape, PY, PZ, W, dirs, seed)
+        assert np.array_equal(X, ref), (shape, PY, PZ, W, dirs, seed, np.max(np.abs(X - ref)))
+
+
+@pytest.mark.parametrize("kw", [dict(short_need=2, CH=1), dict(drop_old_side=True)])
+def test_gsp_model_detects_a_weakened_wait(kw):
+    # waiting for two pairs too few (with one substep per chunk, so that the
+    # producers publish every pair; a published count is that of the pencil's
+    # last line, PZ - 1 = 1 pair behind the line a y-boundary lane reads, so
+    # one pair less is still safe), or not at all on the old side, must show
+    # up as a wrong value or a hazard in some interleaving
+    caught = 0
+    for seed in range(12):
+        try:
+            X, ref = _model_gsp((9, 8, 6), 4, 2, 6, [0, 0, 0], seed, **kw)
+            caught += int(not np.array_equal(X, ref))
+        except AssertionError:
+            caught += 1
+    assert caught > 0
