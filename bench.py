@@ -518,6 +518,10 @@ def summaries(extras):
                            "inner_iters": m["mixed"]["inner_iters"], "speedup": m["speedup"],
                            "mixed_true_rel_res": m["mixed"]["true_rel_res"],
                            "rel_err_vs_gpu_fp64_cg": m["mixed"]["rel_err_vs_fp64_solution"]}
+        if "rel_err_vs_oracle_4096_cells" in m["mixed"]:
+            out["mixed512"]["rel_err_vs_oracle"] = {"mixed": m["mixed"]["rel_err_vs_oracle_4096_cells"],
+                                                    "fp64_cg": m["fp64_cg"]["rel_err_vs_oracle_4096_cells"],
+                                                    "sample": "4096 seeded cells of the oracle's FP64 CG solution"}
     bt = extras.get("batched")
     if bt:
         out["batched512"] = {"fp64_s": round(bt["batched"]["ms"] / 1e3, 3),
@@ -720,6 +724,17 @@ def mixed_comparison(n, dev, tmo):
                     "true_rel_res": im.true_rel_res, "status": im.status, "inner_tol": 1e-4,
                     "rel_err_vs_fp64_solution": err}
     out["speedup"] = round(t64 / tmx, 3)
+    # error against the FP64 oracle's own solution of this system, sampled at
+    # the cells stored by tests/golden/make_mixed512.py (512^3 only)
+    gold_path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden", "mixed512_solution.json")
+    if n == 512 and os.path.exists(gold_path):
+        with open(gold_path) as fh:
+            gold = json.load(fh)
+        cells = torch.tensor(gold["cells"], dtype=torch.long, device=dev)
+        ref = torch.tensor(gold["x_at_cells"], dtype=torch.float64, device=dev)
+        rn = torch.linalg.norm(ref).item()
+        out["fp64_cg"]["rel_err_vs_oracle_4096_cells"] = (torch.linalg.norm(x[cells] - ref) / rn).item()
+        out["mixed"]["rel_err_vs_oracle_4096_cells"] = (torch.linalg.norm(xm[cells] - ref) / rn).item()
     del A, k, b, x, xm
     torch.cuda.empty_cache()
     return out
