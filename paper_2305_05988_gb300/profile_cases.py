@@ -3,7 +3,7 @@
     python -m paper_2305_05988_gb300.profile_cases CASE [N] [ITERS]
 
 CASE picks the kernel: spmv, jacobi, gs, cg, bicgstab, cg_nb (7-point, FP64,
-N^3 grid, b ~ U(-1, 1)); cg32v (FP32 CG on variable-coefficient diffusion,
+N^3 grid, b ~ U(-1, 1)); jacobi32 (the same in FP32); cg32v (FP32 CG on variable-coefficient diffusion,
 log k ~ N(0, 1), stored coefficients), cg32v_tma (the same with TMA-staged
 planes); gs2d (Gauss-Seidel on the N^2 Laplacian); hpcg27_spmv, hpcg27_jacobi,
 hpcg27_cg, hpcg27_bicgstab, hpcg27_gs (symmetric) and hpcg7_cg (the HPCG
@@ -40,6 +40,11 @@ def main(argv):
                "cg": lambda: hs.cg(A, b, tol=0.0, maxit=iters, history=False, **kw),
                "bicgstab": lambda: hs.bicgstab(A, b, tol=0.0, maxit=iters, history=False, **kw),
                "cg_nb": lambda: hs.cg_nb(A, b, tol=0.0, maxit=iters, history=False, **kw)}[case]
+    elif case == "jacobi32":
+        shape = (n, n, n)
+        b = torch.from_numpy(inputs.rhs_uniform(shape, 0)).float().cuda()
+        A = hs.Operator.laplacian(shape)
+        run = lambda: hs.jacobi(A, b, maxit=iters, **kw)  # noqa: E731
     elif case in ("cg32v", "cg32v_tma"):
         shape = (n, n, n)
         k = torch.from_numpy(np.exp(inputs.log_k(shape, 1.0, 0))).cuda()
