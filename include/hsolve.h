@@ -98,7 +98,8 @@ typedef struct {
                                (default 1; needs a non-default stream)          */
     int tile_rows;          /* stencil tiles of the Jacobi / CG / BiCGStab /
                                mixed solvers: rows of 32 nodes per tile = warps
-                               per block, 4, 8 or 16; 0 = built-in heuristic   */
+                               per block, 4 to 16 (other values: the built-in
+                               heuristic, 8 rows on 3-D grids)                 */
     int tile_planes;        /* z planes per work item of those tiles; 0 = the
                                built-in cost model                             */
     int max_blocks;         /* cap on the persistent grid (blocks); 0 = all

@@ -703,10 +703,10 @@ inline int rows_per_tile(const Geom& g) {
   return 8;
 }
 
-// Rows per tile: the caller's choice (hs_opts.tile_rows in {4, 8, 16}) or the
+// Rows per tile: the caller's choice (hs_opts.tile_rows, 4 to 16) or the
 // heuristic above.
 inline int rows_for(const Geom& g, const hs_opts& o) {
-  if (o.tile_rows == 4 || o.tile_rows == 8 || o.tile_rows == 16) return o.tile_rows;
+  if (o.tile_rows >= 4 && o.tile_rows <= 16) return o.tile_rows;
   return rows_per_tile(g);
 }
 
