@@ -6,7 +6,7 @@ import re
 
 import pytest
 
-from paper_2305_05988_gb300 import _build, _lib
+from paper_2305_05988_gb300 import _build, _lib, solvers
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -122,6 +122,13 @@ def test_solver_rejects_bad_arguments_without_touching_the_gpu(lib):
     st = lib.hs_bicgstab(op, 0, ctypes.c_void_p(0x1000), ctypes.c_void_p(0x2000), 1e-8, 3, ctypes.byref(o),
                          ctypes.c_void_p(0x100000), 1 << 30, None, ctypes.byref(res), None)
     assert st == _lib.HS_ERR_INVALID
+    # option values outside their ranges
+    for field, bad in (("gs_schedule", 3), ("gs_schedule", -1), ("staging", 2), ("gs_mode", 5)):
+        o = solvers.make_opts()
+        setattr(o, field, bad)
+        st = lib.hs_gauss_seidel(op, 0, ctypes.c_void_p(0x1000), ctypes.c_void_p(0x2000), 0.0, 3, ctypes.byref(o),
+                                 ctypes.c_void_p(0x100000), 1 << 30, None, ctypes.byref(res), None)
+        assert st == _lib.HS_ERR_INVALID, (field, bad)
     lib.hs_op_destroy(op)
 
 
