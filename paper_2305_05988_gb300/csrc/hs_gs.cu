@@ -25,6 +25,13 @@
 // A backward sweep mirrors every direction.  The symmetric method (forward
 // then backward per iteration) alternates directions inside one batch; a
 // sweep then starts only after the previous one has passed every tile plane.
+//
+// Two other schedules live here as well: the pencil schedule (k_gsp, one warp
+// per 8 x 4 x-lines, neighbour lines exchanged by warp shuffles, per-pencil
+// progress counts; pipelined batches on 3-D constant-coefficient operators)
+// and, for small 1-/2-D grids, one block sweeping the whole iterate in shared
+// memory along anti-diagonals (k_gs2d).  All three apply the same two-part
+// update to every node (gs_old, then gs_new).
 #include <math.h>
 
 #include <algorithm>
