@@ -286,6 +286,34 @@ hs_status hs_bicgstab(const hs_op *A, hs_dtype dtype, const void *b, void *x, do
                       int maxit, const hs_opts *opts, void *ws, size_t ws_bytes, void *stream,
                       hs_result *res, double *hist);
 
+/* Asynchronous forms of the four solvers, for CUDA-graph capture: the same
+ * arguments, validation and workspace as hs_jacobi / hs_gauss_seidel / hs_cg /
+ * hs_bicgstab, but nothing on the host waits for the GPU.  The call validates
+ * its arguments (returning HS_ERR_INVALID / HS_ERR_WORKSPACE at once, as the
+ * synchronous calls do), enqueues the solve on `stream` and returns HS_OK;
+ * the solver's outcome is written by a kernel at the end of the work into
+ * res_dev (DEVICE memory, one hs_result, 8-byte aligned, may be NULL) and the
+ * residual history into hist_dev (DEVICE memory, maxit + 1 doubles, may be
+ * NULL; entries up to res.iters are written, as in the synchronous form).
+ * Every step of these calls is stream-ordered (kernel launches and
+ * device-to-device copies only), so a call can be captured in a CUDA graph
+ * and the graph replayed with new contents of b and x; the workspace, vectors
+ * and result buffers must then stay allocated.  Not available: the BiCGStab
+ * trace options (alpha_trace, restart_iters: HS_ERR_INVALID) and the debug
+ * build's bounds report, which synchronises. */
+hs_status hs_jacobi_async(const hs_op *A, hs_dtype dtype, const void *b, void *x, double tol, int maxit,
+                          const hs_opts *opts, void *ws, size_t ws_bytes, void *stream, hs_result *res_dev,
+                          double *hist_dev);
+hs_status hs_gauss_seidel_async(const hs_op *A, hs_dtype dtype, const void *b, void *x, double tol,
+                                int maxit, const hs_opts *opts, void *ws, size_t ws_bytes, void *stream,
+                                hs_result *res_dev, double *hist_dev);
+hs_status hs_cg_async(const hs_op *A, hs_dtype dtype, const void *b, void *x, double tol, int maxit,
+                      const hs_opts *opts, void *ws, size_t ws_bytes, void *stream, hs_result *res_dev,
+                      double *hist_dev);
+hs_status hs_bicgstab_async(const hs_op *A, hs_dtype dtype, const void *b, void *x, double tol,
+                            int maxit, const hs_opts *opts, void *ws, size_t ws_bytes, void *stream,
+                            hs_result *res_dev, double *hist_dev);
+
 /* Mixed-precision iterative refinement.  Not in the paper (which is FP64
  * throughout); it gets the FP64 answer of A x = b at FP32 cost on a GPU whose
  * FP32 pipe is 64x its FP64 pipe.  Each refinement step computes the FP64

@@ -92,6 +92,10 @@ SIGNATURES = {
                    ctypes.POINTER(hs_result), ctypes.POINTER(_d)]),
     "hs_bicgstab": (_i, [_vp, _i, _vp, _vp, _d, _i, ctypes.POINTER(hs_opts), _vp, _sz, _vp,
                          ctypes.POINTER(hs_result), ctypes.POINTER(_d)]),
+    "hs_jacobi_async": (_i, [_vp, _i, _vp, _vp, _d, _i, ctypes.POINTER(hs_opts), _vp, _sz, _vp, _vp, _vp]),
+    "hs_gauss_seidel_async": (_i, [_vp, _i, _vp, _vp, _d, _i, ctypes.POINTER(hs_opts), _vp, _sz, _vp, _vp, _vp]),
+    "hs_cg_async": (_i, [_vp, _i, _vp, _vp, _d, _i, ctypes.POINTER(hs_opts), _vp, _sz, _vp, _vp, _vp]),
+    "hs_bicgstab_async": (_i, [_vp, _i, _vp, _vp, _d, _i, ctypes.POINTER(hs_opts), _vp, _sz, _vp, _vp, _vp]),
     "hs_solve_mixed": (_i, [_vp, _vp, _vp, _d, _i, ctypes.POINTER(hs_opts), _vp, _sz, _vp,
                             ctypes.POINTER(hs_result), ctypes.POINTER(_d)]),
     "hs_diffusion_grad_logk": (_i, [_vp, _vp, _vp, _vp, _vp]),

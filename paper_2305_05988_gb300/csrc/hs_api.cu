@@ -198,6 +198,48 @@ static hs_status solve_common(runner_t run, hs_solver which, const hs_op* A, hs_
   return s;
 }
 
+// The asynchronous form: validated like the synchronous calls (errors are
+// returned at once), then everything is enqueued on the stream and the result
+// and the history are written by a kernel into device memory.
+static hs_status solve_async(runner_t run, hs_solver which, const hs_op* A, hs_dtype dt, const void* b, void* x,
+                             double tol, int maxit, const hs_opts* opts, void* ws, size_t ws_bytes, void* stream,
+                             hs_result* res_dev, double* hist_dev) {
+  static const char* const names[] = {"hs_jacobi_async", "hs_gauss_seidel_async", "hs_cg_async",
+                                      "hs_bicgstab_async", "hs_solve_mixed", "hs_cg_nb_async"};
+  NvtxRange range(which >= 0 && which <= 5 ? names[which] : "hs_solve_async");
+  hs_opts o;
+  if (!merge_opts(opts, &o)) return HS_ERR_INVALID;
+  if (o.alpha_trace || o.restart_iters) {
+    set_error("the BiCGStab trace is read back to the host: not available in the asynchronous form");
+    return HS_ERR_INVALID;
+  }
+  if (res_dev && !aligned(res_dev, 8)) {
+    set_error("res must be an 8-byte aligned device pointer");
+    return HS_ERR_INVALID;
+  }
+  hs_status s = check_solve(A, dt, b, x, tol, maxit, ws, ws_bytes, which, o);
+  if (s != HS_OK) return s;
+  SolveArgs a;
+  a.A = A;
+  a.dtype = dt;
+  a.b = b;
+  a.x = x;
+  a.tol = tol;
+  a.maxit = maxit;
+  a.o = o;
+  a.ws = (char*)ws;
+  a.ws_bytes = ws_bytes;
+  a.stream = (cudaStream_t)stream;
+  a.async_dev = true;
+  a.res_dev = res_dev;
+  a.hist_dev = hist_dev;
+  cudaError_t e = cudaGetLastError();  // clear stale errors from unrelated work
+  (void)e;
+  hs_result scratch;
+  fill_res(&scratch);
+  return run(a, &scratch, nullptr);
+}
+
 }  // namespace hs
 
 using namespace hs;
@@ -395,6 +437,37 @@ hs_status hs_bicgstab(const hs_op* A, hs_dtype dtype, const void* b, void* x, do
                       const hs_opts* opts, void* ws, size_t ws_bytes, void* stream, hs_result* res, double* hist) {
   return solve_common(run_bicgstab, HS_SOLVER_BICGSTAB, A, dtype, b, x, tol, maxit, opts, ws, ws_bytes, stream, res,
                       hist);
+}
+
+hs_status hs_jacobi_async(const hs_op* A, hs_dtype dtype, const void* b, void* x, double tol, int maxit,
+                          const hs_opts* opts, void* ws, size_t ws_bytes, void* stream, hs_result* res_dev,
+                          double* hist_dev) {
+  return solve_async(run_jacobi, HS_SOLVER_JACOBI, A, dtype, b, x, tol, maxit, opts, ws, ws_bytes, stream, res_dev,
+                     hist_dev);
+}
+
+hs_status hs_gauss_seidel_async(const hs_op* A, hs_dtype dtype, const void* b, void* x, double tol, int maxit,
+                                const hs_opts* opts, void* ws, size_t ws_bytes, void* stream, hs_result* res_dev,
+                                double* hist_dev) {
+  return solve_async(run_gauss_seidel, HS_SOLVER_GAUSS_SEIDEL, A, dtype, b, x, tol, maxit, opts, ws, ws_bytes, stream,
+                     res_dev, hist_dev);
+}
+
+hs_status hs_cg_async(const hs_op* A, hs_dtype dtype, const void* b, void* x, double tol, int maxit,
+                      const hs_opts* opts, void* ws, size_t ws_bytes, void* stream, hs_result* res_dev,
+                      double* hist_dev) {
+  if (A && opkind_of(A) == OP_NONSYM) {
+    set_error("CG needs a symmetric operator (Laplacian or diffusion)");
+    return HS_ERR_INVALID;
+  }
+  return solve_async(run_cg, HS_SOLVER_CG, A, dtype, b, x, tol, maxit, opts, ws, ws_bytes, stream, res_dev, hist_dev);
+}
+
+hs_status hs_bicgstab_async(const hs_op* A, hs_dtype dtype, const void* b, void* x, double tol, int maxit,
+                            const hs_opts* opts, void* ws, size_t ws_bytes, void* stream, hs_result* res_dev,
+                            double* hist_dev) {
+  return solve_async(run_bicgstab, HS_SOLVER_BICGSTAB, A, dtype, b, x, tol, maxit, opts, ws, ws_bytes, stream,
+                     res_dev, hist_dev);
 }
 
 }  // extern "C"

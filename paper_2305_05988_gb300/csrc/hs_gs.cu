@@ -1070,6 +1070,46 @@ static void tile_counts(const hs_op* A, int* ntx, int* nty, int* ntz) {
   *ntz = (int)((A->n[2] + GsTile<NDIM, W>::TZ - 1) / GsTile<NDIM, W>::TZ);
 }
 
+// Tile-plane tables on the device: off[S] = number of tiles on planes below S
+// (S = I + J + K; off[P] = all tiles), then the tile ids of each plane in
+// increasing id order.  With a x b x c tiles, the tiles (I, J) of one z layer
+// on plane u number
+//   N2(u) = max(0, min(u, a - 1) - max(0, u - b + 1) + 1)   (u >= 0),
+// a plane's tiles sum N2 over the layers, and a tile's rank inside its plane
+// counts the layers below it and the rows J' < J of its own layer that reach
+// the plane.  Computed on the device (no host staging), so a solve can be
+// captured in a CUDA graph.
+__device__ __forceinline__ int gs_n2(int u, int a, int b) {
+  if (u < 0) return 0;
+  const int lo = u - b + 1 > 0 ? u - b + 1 : 0;
+  const int hi = u < a - 1 ? u : a - 1;
+  return hi >= lo ? hi - lo + 1 : 0;
+}
+
+__global__ void k_gs_plane_off(int a, int b, int c, int P, int* off) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q <= P; q += gridDim.x * blockDim.x) {
+    int sum = 0;
+    for (int sp = 0; sp < q; sp++)
+      for (int k = 0; k < c; k++) sum += gs_n2(sp - k, a, b);
+    off[q] = sum;
+  }
+}
+
+__global__ void k_gs_plane_tiles(int a, int b, int c, const int* off, int* tiles) {
+  const int nt = a * b * c;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+    const int I = t % a, J = (t / a) % b, K = t / (a * b);
+    const int S = I + J + K;
+    int rank = 0;
+    for (int k = 0; k < K; k++) rank += gs_n2(S - k, a, b);
+    for (int j = 0; j < J; j++) {
+      const int i = S - K - j;
+      rank += (i >= 0 && i < a) ? 1 : 0;
+    }
+    tiles[off[S] + rank] = t;
+  }
+}
+
 // Tile count and tile planes of the larger table (the W = 0 shape has the
 // smaller tiles in every direction).
 static void gs_counts(const hs_op* A, int* ntiles, int* P) {
@@ -1141,33 +1181,14 @@ static hs_status gs_run_t(const SolveArgs& sa, hs_result* res, double* hist) {
     set_error("workspace too small for Gauss-Seidel");
     return HS_ERR_WORKSPACE;
   }
-  // tile planes: offsets then tile ids grouped by I + J + K
-  std::vector<int> host((size_t)ntiles + P + 1);
+  // tile planes: offsets then tile ids grouped by I + J + K (device kernels)
+  k_gs_plane_off<<<(P + 1 + 127) / 128, 128, 0, sa.stream>>>(ntx, nty, ntz, P, tabs);
+  k_gs_plane_tiles<<<(ntiles + 255) / 256, 256, 0, sa.stream>>>(ntx, nty, ntz, tabs, tabs + P + 1);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "tile tables");
   {
-    std::vector<int> cnt(P + 1, 0);
-    for (int t = 0; t < ntiles; t++) {
-      int I = t % ntx, J = (t / ntx) % nty, K = t / (ntx * nty);
-      cnt[I + J + K + 1]++;
-    }
-    for (int s = 0; s < P; s++) cnt[s + 1] += cnt[s];
-    for (int s = 0; s <= P; s++) host[s] = cnt[s];
-    std::vector<int> fill(cnt.begin(), cnt.end() - 1);
-    for (int t = 0; t < ntiles; t++) {
-      int I = t % ntx, J = (t / ntx) % nty, K = t / (ntx * nty);
-      host[P + 1 + fill[I + J + K]++] = t;
-    }
-  }
-  cudaError_t e = cudaMemcpyAsync(tabs, host.data(), host.size() * sizeof(int), cudaMemcpyHostToDevice, sa.stream);
-  if (e != cudaSuccess) return cuda_fail(e, "tile table upload");
-  {
-    double t = sa.o.timeout_s > 0 ? sa.o.timeout_s : 2.0;
-    Ctrl h = {};
-    h.timeout_ns = (unsigned long long)(t * 1e9);
-    h.rel_res = -1.0;
-    e = cudaMemcpyAsync(cm.ctrl, &h, sizeof(Ctrl), cudaMemcpyHostToDevice, sa.stream);
-    if (e != cudaSuccess) return cuda_fail(e, "control init");
-    e = cudaStreamSynchronize(sa.stream);  // host staging buffers go out of scope below
-    if (e != cudaSuccess) return cuda_fail(e, "control init");
+    hs_status si = init_ctrl(cm, sa.o, sa.stream);
+    if (si != HS_OK) return si;
   }
   if (OPK == OP_VARK) {
     hs_status s = setup_vark(A, sa.dtype, D, ax, ay, az, true, sa.stream);
@@ -1273,13 +1294,8 @@ static hs_status gsp_run_t(const SolveArgs& sa, hs_result* res, double* hist) {
   const size_t vb = 2 * sizeof(T);
   const bool vec = g.nx % 2 == 0 && ((uintptr_t)sa.x % vb) == 0 && ((uintptr_t)a.bD % vb) == 0;
   {
-    double t = sa.o.timeout_s > 0 ? sa.o.timeout_s : 2.0;
-    Ctrl h = {};
-    h.timeout_ns = (unsigned long long)(t * 1e9);
-    h.rel_res = -1.0;
-    cudaError_t e = cudaMemcpyAsync(cm.ctrl, &h, sizeof(Ctrl), cudaMemcpyHostToDevice, sa.stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(sa.stream);  // h goes out of scope below
-    if (e != cudaSuccess) return cuda_fail(e, "control init");
+    hs_status si = init_ctrl(cm, sa.o, sa.stream);
+    if (si != HS_OK) return si;
   }
   a.cf = gs_jacobi_coef<T>(A, &a.invd, &a.dscale2);
   a.g = g;

@@ -139,6 +139,11 @@ struct SolveArgs {
   char* ws;
   size_t ws_bytes;
   cudaStream_t stream;
+  // asynchronous form (hs_*_async): the result and the history are written
+  // by a kernel into device memory and nothing on the host waits
+  bool async_dev = false;
+  hs_result* res_dev = nullptr;
+  double* hist_dev = nullptr;
 };
 
 // Doubles of the BiCGStab restart trace section (r_k . r' and a restart flag

@@ -650,11 +650,56 @@ struct Tail {
   void* rbuf;                     // scratch vector of N elements
 };
 
+// The asynchronous tail: the control block becomes an hs_result in device
+// memory and the history is copied device to device, all on the stream.
+__global__ void k_finalize_dev(const Ctrl* c, int maxit, int true_res, int want_hist, const double* hsrc,
+                               double* hdst, hs_result* out) {
+  const int iters = c->iters;
+  if (threadIdx.x == 0 && out) {
+    hs_result r;
+    r.iters = iters;
+    r.rel_res = c->rel_res;
+    r.restarts = c->restarts;
+    r.outer = 0;
+    r.inner_iters = 0;
+    r.true_rel_res = -1.0;
+    if (true_res) {
+      const double rr = c->aux[0], bb = c->aux[1];
+      r.true_rel_res = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+      if (r.rel_res < 0.0) r.rel_res = r.true_rel_res;
+    }
+    switch (c->status) {
+      case DS_CONVERGED: r.status = HS_OK; break;
+      case DS_MAXIT: r.status = HS_NOT_CONVERGED; break;
+      case DS_BREAKDOWN: r.status = HS_ERR_BREAKDOWN; break;
+      case DS_NONFINITE: r.status = HS_ERR_NONFINITE; break;
+      case DS_TIMEOUT: r.status = HS_ERR_TIMEOUT; break;
+      default: r.status = HS_ERR_CUDA; break;
+    }
+    *out = r;
+  }
+  if (hdst && want_hist) {
+    const int n = (iters < maxit ? iters : maxit) + 1;
+    for (int q = threadIdx.x; q < n; q += blockDim.x) hdst[q] = hsrc[q];
+  }
+}
+
 static hs_status finish_solve(const SolveArgs& sa, const Common& cm, const Tail& t, hs_result* res, double* hist,
                               bool want_hist) {
   {
     hs_status sd = hs_dbg_take(sa.stream);
     if (sd != HS_OK) return sd;
+  }
+  if (sa.async_dev) {
+    if (sa.o.true_residual) {
+      hs_status s = residual_norms(t.A, t.dt, t.D, t.ax, t.ay, t.az, t.b, t.x, t.rbuf, &cm.ctrl->aux[0], cm.partials,
+                                   sa.stream);
+      if (s != HS_OK) return s;
+    }
+    k_finalize_dev<<<1, 256, 0, sa.stream>>>(cm.ctrl, sa.maxit, sa.o.true_residual ? 1 : 0, want_hist ? 1 : 0, cm.hist,
+                                             sa.hist_dev, sa.res_dev);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? HS_OK : cuda_fail(e, "result kernel");
   }
   if (sa.o.true_residual) {
     hs_status s = residual_norms(t.A, t.dt, t.D, t.ax, t.ay, t.az, t.b, t.x, t.rbuf, &cm.ctrl->aux[0], cm.partials,

@@ -317,6 +317,67 @@ def diag_wait_timeout(kind: str, timeout_s: float = 0.05) -> str:
     return _lib.STATUS_NAMES.get(st, str(st))
 
 
+_ASYNC_FN = {"jacobi": ("hs_jacobi_async", _lib.HS_SOLVER_JACOBI),
+             "gauss_seidel": ("hs_gauss_seidel_async", _lib.HS_SOLVER_GAUSS_SEIDEL),
+             "cg": ("hs_cg_async", _lib.HS_SOLVER_CG),
+             "bicgstab": ("hs_bicgstab_async", _lib.HS_SOLVER_BICGSTAB)}
+
+
+class AsyncSolve:
+    """A solve enqueued on the current stream with nothing on the host waiting
+    (hs_jacobi_async / hs_gauss_seidel_async / hs_cg_async / hs_bicgstab_async):
+    the outcome and the history land in device buffers owned by this object,
+    so launch() can be captured in a CUDA graph and replayed after new values
+    are copied into b and x.  b and x are used in place; the object keeps its
+    own workspace.  result() copies the outcome to the host (synchronising)."""
+
+    def __init__(self, solver: str, A: Operator, b: torch.Tensor, x: torch.Tensor, tol: float = 1e-10,
+                 maxit: int = 10000, history: bool = False, **kw):
+        if solver not in _ASYNC_FN:
+            raise ValueError("solver must be one of %s" % sorted(_ASYNC_FN))
+        A._vec(b, "b")
+        A._vec(x, "x")
+        if x.dtype != b.dtype or x.device != b.device:
+            raise TypeError("x and b must have the same dtype and device")
+        if solver == "gauss_seidel" and "mode" in kw:
+            kw["gs_mode"] = kw.pop("mode")
+        self.fn, code = _ASYNC_FN[solver]
+        self.A, self.b, self.x = A, b, x
+        self.tol, self.maxit = float(tol), int(maxit)
+        self.opts = make_opts(**kw)
+        size = ctypes.c_size_t()
+        with torch.cuda.device(b.device):
+            check(_lib.load().hs_workspace_size(A._op, code, _DT[b.dtype], ctypes.byref(self.opts), self.maxit,
+                                                ctypes.byref(size)), "hs_workspace_size")
+        self.ws = torch.empty(max(size.value, 256), dtype=torch.uint8, device=b.device)
+        self.res = torch.zeros(ctypes.sizeof(_lib.hs_result), dtype=torch.uint8, device=b.device)
+        self.hist = torch.full((self.maxit + 1,), float("nan"), dtype=torch.float64, device=b.device) if history \
+            else None
+
+    def launch(self, stream=None):
+        """Enqueue the solve on `stream` (default: the current stream)."""
+        lib = _lib.load()
+        with torch.cuda.device(self.b.device):
+            st = (stream or torch.cuda.current_stream(self.b.device)).cuda_stream
+            status = getattr(lib, self.fn)(self.A._op, _DT[self.b.dtype], ctypes.c_void_p(self.b.data_ptr()),
+                                           ctypes.c_void_p(self.x.data_ptr()), self.tol, self.maxit,
+                                           ctypes.byref(self.opts), ctypes.c_void_p(self.ws.data_ptr()),
+                                           self.ws.numel(), ctypes.c_void_p(st), ctypes.c_void_p(self.res.data_ptr()),
+                                           ctypes.c_void_p(self.hist.data_ptr()) if self.hist is not None else None)
+        check(status, self.fn)
+
+    def result(self) -> SolveInfo:
+        """The outcome of the last completed launch (copies it to the host)."""
+        raw = self.res.cpu().numpy().tobytes()
+        r = _lib.hs_result.from_buffer_copy(raw)
+        hist = None
+        if self.hist is not None:
+            hist = self.hist[: min(r.iters, self.maxit) + 1].cpu().numpy()
+        return SolveInfo(iters=r.iters, status=_lib.STATUS_NAMES.get(r.status, str(r.status)), status_code=r.status,
+                         rel_res=r.rel_res, true_rel_res=r.true_rel_res, restarts=r.restarts, history=hist,
+                         outer=r.outer, inner_iters=r.inner_iters)
+
+
 def fp64_rate() -> float:
     """FP64 fused multiply-add rate of the current device in flop/s (the peak
     the FP64 solvers' flop rates are quoted against)."""

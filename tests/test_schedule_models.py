@@ -553,3 +553,47 @@ def test_gsp_model_detects_a_weakened_wait(kw):
         except AssertionError:
             caught += 1
     assert caught > 0
+
+
+# ---------------------------------------------------------------- tile-plane tables
+
+def _gs_tables_closed_form(a, b, c):
+    """The device's tile-plane tables (hs_gs.cu, k_gs_plane_off and
+    k_gs_plane_tiles) transcribed: offsets from the count of tiles (I, J) of one
+    layer on plane u, and each tile's rank inside its plane."""
+    def n2(u):
+        if u < 0:
+            return 0
+        lo, hi = max(0, u - b + 1), min(u, a - 1)
+        return hi - lo + 1 if hi >= lo else 0
+    P = a + b + c - 2
+    off = [sum(n2(sp - k) for sp in range(q) for k in range(c)) for q in range(P + 1)]
+    tiles = [None] * (a * b * c)
+    for t in range(a * b * c):
+        I, J, K = t % a, (t // a) % b, t // (a * b)
+        S = I + J + K
+        rank = sum(n2(S - k) for k in range(K)) + sum(1 for j in range(J) if 0 <= S - K - j < a)
+        tiles[off[S] + rank] = t
+    return off, tiles
+
+
+def _gs_tables_counting_sort(a, b, c):
+    P = a + b + c - 2
+    # plain counting sort by plane, ids increasing within a plane
+    planes = {}
+    for t in range(a * b * c):
+        I, J, K = t % a, (t // a) % b, t // (a * b)
+        planes.setdefault(I + J + K, []).append(t)
+    off, tiles, acc = [], [], 0
+    for s in range(P + 1):
+        off.append(acc)
+        acc += len(planes.get(s, []))
+        tiles += planes.get(s, [])
+    return off, tiles
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (8, 32, 32), (3, 5, 2), (1, 7, 4), (6, 1, 9), (4, 4, 4), (2, 16, 1)])
+def test_gs_tile_tables_closed_form_equals_counting_sort(shape):
+    off, tiles = _gs_tables_closed_form(*shape)
+    off2, tiles2 = _gs_tables_counting_sort(*shape)
+    assert off == off2 and tiles == tiles2
