@@ -465,6 +465,12 @@ def diffusion_solve(logk: torch.Tensor, f: torch.Tensor, shape, tol: float = 1e-
     return DiffusionSolve.apply(logk, f, tuple(shape), tol, mixed, maxit)
 
 
+def batch_solve(ops, solvers, bs, xs=None, tol: float = 1e-8, maxit: int = 20000, stream=None, **kw):
+    """Solve many independent systems with one persistent kernel (a Batch built
+    for these operators and solvers, then Batch.solve); returns (xs, infos)."""
+    return Batch(ops, solvers).solve(bs, xs, tol=tol, maxit=maxit, stream=stream, **kw)
+
+
 class Batch:
     """Many independent systems solved by one persistent kernel (CUDA graph).
 

@@ -242,3 +242,27 @@ def test_batch_mixed_poisoned_and_all_or_none():
             assert info.status == "OK" and A_o.relres(b, x.cpu().numpy()) <= 1e-10 * (1 + 1e-3)
     with pytest.raises(hs.HsError):
         hs.Batch(ops_g[:2], ["mixed", "cg"])
+
+
+def test_batch_solve_function():
+    # the one-call form: builds the batch and solves; each system against the oracle
+    shapes = [(20, 18), (12, 10, 9), (30, 7), (9, 9, 9)]
+    ops_o, ops_g, bs, sol = [], [], [], []
+    for q, shape in enumerate(shapes):
+        if q % 2 == 0:
+            ops_o.append(oracle.Operator(shape))
+            ops_g.append(hs.Operator.laplacian(shape))
+            sol.append("cg")
+        else:
+            beta = inputs.upwind_beta(shape, 0.5)
+            ops_o.append(oracle.Operator(shape, oracle.UPWIND, beta))
+            ops_g.append(hs.Operator.upwind(shape, beta))
+            sol.append("bicgstab")
+        bs.append(inputs.uniform_pm1(70 + q, 1, int(np.prod(shape))))
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        xs, infos = hs.batch_solve(ops_g, sol, [dev(b) for b in bs], tol=1e-10, maxit=5000)
+    s.synchronize()
+    for A_o, b, x, info in zip(ops_o, bs, xs, infos):
+        assert info.status == "OK"
+        assert A_o.relres(b, x.cpu().numpy()) <= 1e-10 * (1 + 1e-3)
