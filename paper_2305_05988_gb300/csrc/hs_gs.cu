@@ -560,9 +560,10 @@ __global__ void __launch_bounds__(gs_threads<NDIM, W>()) k_gs(GsArgs<T> a) {
 // earliest unfinished (sweep, pencil) item only ever waits on finished items:
 // no deadlock.  Sweeps overlap (a pencil starts sweep t + 1 while pencils
 // above it are still in sweep t) when every warp owns one pencil; the
-// automatic choice takes this schedule only then.  No block barrier inside a sweep: each warp runs on its
-// own.  The update arithmetic is that of gs_tile (gs_old then gs_new), so
-// iterates are bitwise those of the tile schedule.
+// automatic choice takes this schedule only then.  No block barrier inside
+// a sweep: each warp runs on its own.  The update arithmetic is that of
+// gs_tile (gs_old then gs_new), so iterates are bitwise those of the tile
+// schedule.
 // ---------------------------------------------------------------------------
 
 constexpr int GSP_PY = 8, GSP_PZ = 4;   // lines per pencil (one warp)
