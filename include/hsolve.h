@@ -158,7 +158,8 @@ typedef struct {
                                (one warp per 8 x 4 x-lines streaming two nodes
                                per substep, neighbour lines by warp shuffles,
                                ordered by per-pencil progress counts; 3-D
-                               Laplacian / upwind operators only, else
+                               constant-coefficient 7-point operators only:
+                               Laplacian, upwind, HPCG 7-point; else
                                HS_ERR_INVALID).  Both give bitwise the same
                                iterates.                                       */
 } hs_opts;
