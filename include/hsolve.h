@@ -145,13 +145,19 @@ typedef struct {
                                0.5 tol / rel_k), which is all the step needs
                                to reach tol; 1: every inner solve runs to
                                inner_tol                                       */
-    int gs_schedule;        /* lexicographic Gauss-Seidel on 3-D grids: 0
-                               (default) the pencil schedule for batches of
+    int gs_schedule;        /* lexicographic Gauss-Seidel: 0 (default) on
+                               3-D grids the pencil schedule for batches of
                                four or more sweeps of one direction on
                                constant-coefficient operators with between
                                12 pencils per SM and one pencil per resident
-                               warp, the tile schedule otherwise; 1 the tile
-                               schedule (tiles of
+                               warp, the tile schedule otherwise; on 1-/2-D
+                               grids whose iterate fits shared memory, for
+                               such pipelined batches one thread-block
+                               cluster (8 CTAs, rows split over them,
+                               distributed shared memory), else (single
+                               sweeps, symmetric, max_blocks = 1, fewer than
+                               16 rows) one block; 1 the tile schedule on
+                               every grid (tiles of
                                32 x 8 x 8 or 32 x 16 x 16 nodes swept along
                                point hyperplanes in shared memory, ordered by
                                per-tile sweep counts); 2 the pencil schedule
@@ -160,8 +166,10 @@ typedef struct {
                                ordered by per-pencil progress counts; 3-D
                                constant-coefficient 7-point operators only:
                                Laplacian, upwind, HPCG 7-point; else
-                               HS_ERR_INVALID).  Both give bitwise the same
-                               iterates.                                       */
+                               HS_ERR_INVALID); 3 one thread-block cluster
+                               (2-D grids of at least 16 rows that fit, no
+                               max_blocks; else HS_ERR_INVALID).  All give
+                               bitwise the same iterates.                      */
 } hs_opts;
 
 typedef struct {

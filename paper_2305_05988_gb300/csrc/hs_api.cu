@@ -123,8 +123,8 @@ bool merge_opts(const hs_opts* in, hs_opts* out) {
     return false;
   }
   if (out->sweeps_per_pass > 4) out->sweeps_per_pass = 4;
-  if (out->gs_schedule < 0 || out->gs_schedule > 2) {
-    set_error("hs_opts.gs_schedule must be 0 (automatic), 1 (tiles) or 2 (pencils)");
+  if (out->gs_schedule < 0 || out->gs_schedule > 3) {
+    set_error("hs_opts.gs_schedule must be 0 (automatic), 1 (tiles), 2 (pencils) or 3 (one cluster)");
     return false;
   }
   return true;

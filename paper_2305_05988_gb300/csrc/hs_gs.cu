@@ -32,6 +32,7 @@
 // and, for small 1-/2-D grids, one block sweeping the whole iterate in shared
 // memory along anti-diagonals (k_gs2d).  All three apply the same two-part
 // update to every node (gs_old, then gs_new).
+#include <cooperative_groups.h>
 #include <math.h>
 
 #include <algorithm>
@@ -1061,6 +1062,187 @@ __global__ void __launch_bounds__(1024) k_gs2d(GsArgs<T> a) {
 }
 
 // ---------------------------------------------------------------------------
+// Small 2-D grids on one thread-block cluster: the iterate is split by rows
+// over the cluster's CTAs (CTA c holds rows [c R, (c + 1) R) in its shared
+// memory), the anti-diagonal wavefront and sweep pipelining of k_gs2d run
+// unchanged, a node's south / north neighbour in another CTA is read from
+// that CTA's shared memory through the cluster's distributed shared memory,
+// and the cluster barrier replaces the block barrier after each step.  The
+// same update (gs2d_node's gs_old then gs_new) on every node, so the iterates
+// are bitwise those of the one-block kernel.
+// ---------------------------------------------------------------------------
+
+constexpr int GS2DC_CTAS = 8;   // CTAs per cluster (portable cluster size)
+
+template <typename T, int OPK>
+__device__ __forceinline__ void gs2dc_node(const GsArgs<T>& a, T* xs, const T* xlo, const T* xhi, int r0, int r1,
+                                           T bv, int i, int j, bool bw) {
+  const Geom& g = a.g;
+  const int nx = g.nx, ny = g.ny;
+  const int cl = (j - r0) * nx + i;   // local index in this CTA's rows
+  const T vW = i > 0 ? xs[cl - 1] : T(0);
+  const T vE = i + 1 < nx ? xs[cl + 1] : T(0);
+  // rows j - 1 and j + 1: this CTA's, or the last row of the CTA below /
+  // the first row of the CTA above (distributed shared memory)
+  const T vS = j == 0 ? T(0) : (j - 1 >= r0 ? xs[cl - nx] : xlo[i]);
+  const T vN = j + 1 >= ny ? T(0) : (j + 1 < r1 ? xs[cl + nx] : xhi[i]);
+  const OpRaw<T, OPK> o = op_fetch<T, OPK, 2>(a.cf, g, (long long)j * nx + i, i, j, 0);
+  const T yold = gs_old<T, OPK, 2>(a.cf, o, bv, bw ? vW : vE, bw ? vS : vN, T(0), bw);
+  xs[cl] = gs_new<T, OPK, 2>(a.cf, o, yold, bw ? vE : vW, bw ? vN : vS, T(0), bw);
+}
+
+// Deterministic sum over the cluster: each CTA's block sum, then rank 0 adds
+// the CTAs' partials in rank order and every CTA reads the total.
+template <typename T>
+__device__ double gs2dc_sum(double v, double* sh, double* slot) {
+  namespace cgr = cooperative_groups;
+  cgr::cluster_group cl = cgr::this_cluster();
+  double acc[1] = {v};
+  block_sum<1>(acc, sh);
+  if (threadIdx.x == 0) slot[0] = acc[0];
+  cl.sync();
+  if (cl.block_rank() == 0 && threadIdx.x == 0) {
+    double t = 0.0;
+    for (unsigned r = 0; r < cl.num_blocks(); r++) t += *cl.map_shared_rank(slot, r);
+    slot[1] = t;
+  }
+  cl.sync();
+  const double total = *cl.map_shared_rank(slot + 1, 0);
+  cl.sync();   // rank 0's slot may be reused only after everyone has read it
+  return total;
+}
+
+template <typename T, int OPK>
+__global__ void __launch_bounds__(1024) k_gs2dc(GsArgs<T> a) {
+  namespace cgr = cooperative_groups;
+  cgr::cluster_group cl = cgr::this_cluster();
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ double sh[32 * MAX_SCAL];
+  __shared__ double slot[2];
+  T* xs = reinterpret_cast<T*>(smraw);
+  const Geom& g = a.g;
+  const int nx = g.nx, ny = g.ny;
+  const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  const int R = (ny + C - 1) / C;
+  const int r0 = min(ny, rank * R), r1 = min(ny, r0 + R);
+  const int nloc = (r1 - r0) * nx;
+  // the neighbouring CTAs' rows next to ours (only read when they exist)
+  const T* xlo = rank > 0 ? cl.map_shared_rank(xs, rank - 1) + (R - 1) * nx : xs;
+  const T* xhi = rank + 1 < C ? cl.map_shared_rank(xs, rank + 1) : xs;
+  const T* bsrc = (OPK == OP_VARK) ? a.b : a.bD;
+  double acc = 0.0;
+  for (int q = threadIdx.x; q < nloc; q += blockDim.x) {
+    const long long gi = (long long)r0 * nx + q;
+    const T bv = a.b[gi];
+    if (OPK != OP_VARK) a.bD[gi] = bv * a.invd;
+    acc += widen(bv) * widen(bv);
+    xs[q] = a.x[gi];
+  }
+  __syncthreads();
+  const double bb = gs2dc_sum<T>(acc, sh, slot);   // its cluster barriers also publish xs
+  Ctrl* ctrl = a.cm.ctrl;
+  const bool lead = rank == 0 && threadIdx.x == 0;
+  if (bb == 0.0) {
+    for (int q = threadIdx.x; q < nloc; q += blockDim.x) a.x[(long long)r0 * nx + q] = T(0);
+    if (lead) {
+      a.cm.hist[0] = 0.0;
+      ctrl->iters = 0;
+      ctrl->rel_res = 0.0;
+      atomicCAS(&ctrl->status, 0, (int)DS_CONVERGED);
+    }
+    return;
+  }
+  // relative residual of the iterate through the Jacobi form (own rows)
+  auto residual = [&]() {
+    double r = 0.0;
+    for (int q = threadIdx.x; q < nloc; q += blockDim.x) {
+      const int i = q % nx, j = r0 + q / nx;
+      Nbr<T> nb;
+      nb.c = xs[q];
+      nb.w = i > 0 ? xs[q - 1] : T(0);
+      nb.e = i + 1 < nx ? xs[q + 1] : T(0);
+      nb.s = j == 0 ? T(0) : (j - 1 >= r0 ? xs[q - nx] : xlo[i]);
+      nb.n = j + 1 >= ny ? T(0) : (j + 1 < r1 ? xs[q + nx] : xhi[i]);
+      nb.b = nb.t = T(0);
+      const long long gi = (long long)j * nx + i;
+      const OpRaw<T, OPK> o = op_fetch<T, OPK, 2>(a.cf, g, gi, i, j, 0);
+      T d = jacobi_apply<T, OPK, 2>(a.cf, o, nb, __ldcg(bsrc + gi)) - nb.c;
+      if constexpr (OPK == OP_VARK) d = d / o.d;
+      r += widen(d) * widen(d);
+    }
+    const double sc = (OPK == OP_VARK) ? 1.0 : a.dscale2;
+    return sqrt(gs2dc_sum<T>(r, sh, slot) * sc / bb);
+  };
+  // nsw sweeps of one direction, pipelined two diagonals apart
+  auto batch = [&](int nsw, bool bw) {
+    const int Q = blockDim.x / nx;
+    const int i = threadIdx.x % nx, q = threadIdx.x / nx;
+    const bool active = q < Q;
+    const int nsteps = (nx + ny - 2) + 1 + 2 * (nsw - 1);
+    const int ii = bw ? nx - 1 - i : i;
+    // this CTA's rows in the sweep's frame
+    const int f0 = bw ? ny - r1 : r0, f1 = bw ? ny - r0 : r1;
+    for (int s = 0; s < nsteps; s++) {
+      if (active && f1 > f0) {
+        const int t_lo = max(0, (s - i - f1 + 2) >> 1);
+        const int t_hi = min(nsw - 1, (s - i - f0) >> 1);
+        for (int t = t_lo + (((q - t_lo) % Q) + Q) % Q; t <= t_hi; t += Q) {
+          const int r = s - 2 * t - i;
+          if (r < f0 || r >= f1) continue;
+          const int jj = bw ? ny - 1 - r : r;
+          gs2dc_node<T, OPK>(a, xs, xlo, xhi, r0, r1, __ldcg(bsrc + (long long)jj * nx + ii), ii, jj, bw);
+        }
+      }
+      cl.sync();
+    }
+  };
+  int done = 0, status = DS_CONVERGED;
+  double rel = -1.0;
+  if (a.tol > 0.0) {
+    rel = residual();
+    if (lead) a.cm.hist[0] = rel;
+    status = !(rel > a.tol) ? (isfinite(rel) ? DS_CONVERGED : DS_NONFINITE) : DS_MAXIT;
+  }
+  if (!(a.tol > 0.0) || status == DS_MAXIT) {
+    while (done < a.maxit) {
+      const int nb = (a.tol > 0.0) ? min(a.check_every, a.maxit - done) : a.maxit - done;
+      if (a.mode == HS_GS_SYMMETRIC) {
+        for (int q = 0; q < nb; q++) {
+          batch(1, false);
+          batch(1, true);
+        }
+      } else {
+        batch(nb, a.mode == HS_GS_BACKWARD);
+      }
+      done += nb;
+      if (a.tol > 0.0) {
+        rel = residual();
+        if (lead) {
+          for (int q = done - nb + 1; q < done; q++) a.cm.hist[q] = nan("");  // not evaluated
+          a.cm.hist[done] = rel;
+        }
+        if (!isfinite(rel)) {
+          status = DS_NONFINITE;
+          break;
+        }
+        if (rel <= a.tol) {
+          status = DS_CONVERGED;
+          break;
+        }
+        status = DS_MAXIT;
+      }
+    }
+  }
+  for (int q = threadIdx.x; q < nloc; q += blockDim.x) a.x[(long long)r0 * nx + q] = xs[q];
+  if (lead) {
+    ctrl->iters = done;
+    ctrl->rel_res = rel;
+    atomicCAS(&ctrl->status, 0, status);
+  }
+  cl.sync();   // no CTA leaves while another may still read its rows
+}
+
+// ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
 
@@ -1406,6 +1588,94 @@ static hs_status gs2d_run_t(const SolveArgs& sa, hs_result* res, double* hist) {
   return finish_solve_pub(sa, cm, D, ax, ay, az, a.bD, res, hist, sa.tol > 0.0);
 }
 
+// The cluster form: 2-D grids of at least two rows per CTA whose rows fit the
+// CTAs' shared memory, unless the caller caps the grid (max_blocks = 1: one
+// block; more: the tile schedule).
+template <typename T>
+static bool gs2dc_applies(const hs_op* A, const hs_opts& o) {
+  if (A->ndim != 2 || A->n[0] > 1024 || o.max_blocks != 0) return false;
+  const long long nx = A->n[0], ny = A->n[1];
+  if (ny < 2 * GS2DC_CTAS) return false;
+  const long long R = (ny + GS2DC_CTAS - 1) / GS2DC_CTAS;
+  return (size_t)(R * nx) * sizeof(T) <= GS2D_SMEM_MAX;
+}
+
+template <typename T, int OPK>
+static hs_status gs2dc_run_t(const SolveArgs& sa, hs_result* res, double* hist) {
+  const hs_op* A = sa.A;
+  Geom g = geom_of(A);
+  Carve c{sa.ws, 0, sa.ws_bytes, true};
+  Common cm = carve_common(c, sa.maxit);
+  GsArgs<T> a = {};
+  a.bD = c.take<T>(g.N);
+  T *D = nullptr, *ax = nullptr, *ay = nullptr, *az = nullptr;
+  if (OPK == OP_VARK) {
+    // the same layout as the other schedules: tile tables, then coefficients
+    int nt, P;
+    gs_counts(A, &nt, &P);
+    c.take<int>((size_t)nt + P + 1);
+    c.take<unsigned>((size_t)nt);
+    c.take<unsigned long long>(1);
+    D = c.take<T>(g.N);
+    ax = c.take<T>(g.N);
+    ay = c.take<T>(g.N);
+    az = c.take<T>(g.N);
+  }
+  if (!c.ok) {
+    set_error("workspace too small for Gauss-Seidel");
+    return HS_ERR_WORKSPACE;
+  }
+  hs_status s = init_ctrl(cm, sa.o, sa.stream);
+  if (s != HS_OK) return s;
+  if (OPK == OP_VARK) {
+    s = setup_vark(A, sa.dtype, D, ax, ay, az, true, sa.stream);
+    if (s != HS_OK) return s;
+    a.cf.D = D;
+    a.cf.ax = ax;
+    a.cf.ay = ay;
+    a.cf.az = az;
+    a.dscale2 = 1.0;
+  } else {
+    a.cf = gs_jacobi_coef<T>(A, &a.invd, &a.dscale2);
+  }
+  a.g = g;
+  a.b = (const T*)sa.b;
+  a.x = (T*)sa.x;
+  a.cm = cm;
+  a.maxit = sa.maxit;
+  a.mode = sa.o.gs_mode;
+  a.check_every = sa.o.check_every;
+  a.tol = sa.tol;
+  const int nx = g.nx, ny = g.ny;
+  const int R = (ny + GS2DC_CTAS - 1) / GS2DC_CTAS;
+  const size_t smem = (size_t)R * nx * sizeof(T);
+  auto kern = k_gs2dc<T, OPK>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_fail(e, "shared-memory attribute");
+  const int threads = std::min(1024, (((1024 / nx) * nx + 31) / 32) * 32);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(GS2DC_CTAS);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = sa.stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = GS2DC_CTAS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, kern, a);
+  if (e != cudaSuccess) return cuda_fail(e, "Gauss-Seidel cluster launch");
+  if (OPK == OP_VARK && sa.o.true_residual) {
+    s = setup_vark(A, sa.dtype, D, ax, ay, az, false, sa.stream);
+    if (s != HS_OK) return s;
+  }
+  s = hs_dbg_take(sa.stream);
+  if (s != HS_OK) return s;
+  return finish_solve_pub(sa, cm, D, ax, ay, az, a.bD, res, hist, sa.tol > 0.0);
+}
+
 // Warp 0 waits for a sweep count that nothing publishes (diagnostic).
 __global__ void k_diag_gs(Ctrl* ctrl, const unsigned* flag) {
   if (threadIdx.x < 32) gs_poll(threadIdx.x == 0, flag, 1u, ctrl);
@@ -1421,15 +1691,26 @@ hs_status run_gauss_seidel(const SolveArgs& sa, hs_result* res, double* hist) {
   const int opk = opkind_of(sa.A);
   const bool d3 = sa.A->ndim >= 3;
   if (opk == OP_BOX27) return run_gauss_seidel27(sa, res, hist);
-  // batches of four or more sweeps of one direction pipeline (small tiles);
-  // single sweeps and symmetric batches are bound by the tile-plane chain
-  // (large tiles, fewer planes)
+  // batches of four or more sweeps of one direction pipeline (small tiles;
+  // on small 2-D grids one cluster: 128^2, 5.6 against 19 us per sweep with
+  // one block); single sweeps and symmetric batches are bound by the chain of
+  // steps (large tiles, fewer planes; on small 2-D grids one block, whose
+  // barrier is cheaper than the cluster's: 383 against 588 us per symmetric
+  // iteration at 128^2)
   const int per_batch = sa.tol > 0.0 ? sa.o.check_every : sa.maxit;
   const bool deep = sa.o.gs_mode == HS_GS_SYMMETRIC || per_batch < 4;
   const bool pencils = gsp_applies(sa.A, sa);
   if (sa.o.gs_schedule == 2 && !pencils) {
     set_error("the pencil schedule needs a 3-D Laplacian or upwind operator");
     return HS_ERR_INVALID;
+  }
+  if (sa.o.gs_schedule == 3) {
+    const bool fits = sa.dtype == HS_F64 ? gs2dc_applies<double>(sa.A, sa.o) : gs2dc_applies<float>(sa.A, sa.o);
+    if (!fits) {
+      set_error("the cluster schedule needs a 2-D grid of at least 16 rows whose rows fit 8 CTAs' shared memory, "
+                "n_x <= 1024, and no max_blocks");
+      return HS_ERR_INVALID;
+    }
   }
   // automatic choice: pencils for pipelined batches of one direction when
   // every pencil has a warp of its own (247 against 313 us per sweep at
@@ -1440,7 +1721,11 @@ hs_status run_gauss_seidel(const SolveArgs& sa, hs_result* res, double* hist) {
   const bool use_pencils = pencils && (sa.o.gs_schedule == 2 || (sa.o.gs_schedule == 0 && !deep));
 #define HS_GS(TT, OK)                                                                         \
   if (opk == OK) {                                                                            \
-    if (!d3 && gs2d_applies<TT>(sa.A, sa.o)) return gs2d_run_t<TT, OK>(sa, res, hist);          \
+    if (!d3 && (sa.o.gs_schedule == 3 || (sa.o.gs_schedule == 0 && !deep)) &&                  \
+        gs2dc_applies<TT>(sa.A, sa.o))                                                        \
+      return gs2dc_run_t<TT, OK>(sa, res, hist);                                              \
+    if (!d3 && sa.o.gs_schedule != 1 && gs2d_applies<TT>(sa.A, sa.o))                         \
+      return gs2d_run_t<TT, OK>(sa, res, hist);                                               \
     if (!d3) return gs_run_t<TT, OK, 2, 0>(sa, res, hist);                                    \
     if constexpr (OK != OP_VARK) {                                                            \
       if (use_pencils && (sa.o.gs_schedule == 2 || gsp_fits<TT, OK>(sa.A, sa.o)))                \

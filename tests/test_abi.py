@@ -123,7 +123,7 @@ def test_solver_rejects_bad_arguments_without_touching_the_gpu(lib):
                          ctypes.c_void_p(0x100000), 1 << 30, None, ctypes.byref(res), None)
     assert st == _lib.HS_ERR_INVALID
     # option values outside their ranges
-    for field, bad in (("gs_schedule", 3), ("gs_schedule", -1), ("staging", 2), ("gs_mode", 5)):
+    for field, bad in (("gs_schedule", 4), ("gs_schedule", -1), ("staging", 2), ("gs_mode", 5)):
         o = solvers.make_opts()
         setattr(o, field, bad)
         st = lib.hs_gauss_seidel(op, 0, ctypes.c_void_p(0x1000), ctypes.c_void_p(0x2000), 0.0, 3, ctypes.byref(o),

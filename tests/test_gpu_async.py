@@ -38,6 +38,7 @@ CASES = [
     ("gauss_seidel", "lap", (64, 33, 40), dict(tol=0.0, maxit=9)),                      # tiles
     ("gauss_seidel", "up", (37, 19, 11), dict(tol=0.0, maxit=3, mode="symmetric")),     # tiles
     ("gauss_seidel", "lap", (45, 38), dict(tol=1e-3, maxit=2000, history=True)),        # one block
+    ("gauss_seidel", "lap", (64, 48), dict(tol=0.0, maxit=6)),                          # one cluster
     ("cg", "lap", (64, 33, 40), dict(tol=1e-10, maxit=5000, history=True)),
     ("cg", "lap", (70, 45), dict(tol=1e-10, maxit=5000, history=True)),
     ("bicgstab", "up", (64, 33, 40), dict(tol=1e-10, maxit=5000, history=True)),
@@ -70,6 +71,7 @@ def test_async_form_equals_synchronous_call(solver, kind, shape, kw):
     ("gauss_seidel", "lap", (64, 33, 40), dict(tol=0.0, maxit=6)),
     ("gauss_seidel", "lap", (64, 33, 40), dict(tol=0.0, maxit=6, gs_schedule=2)),
     ("gauss_seidel", "up", (37, 19, 11), dict(tol=0.0, maxit=2, mode="symmetric")),
+    ("gauss_seidel", "lap", (64, 48), dict(tol=0.0, maxit=6)),
     ("jacobi", "lap", (64, 33, 40), dict(tol=0.0, maxit=30)),
 ])
 def test_async_solve_captured_in_a_cuda_graph(solver, kind, shape, kw):

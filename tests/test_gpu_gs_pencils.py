@@ -105,4 +105,4 @@ def test_pencil_schedule_only_for_3d_constant_coefficients():
     with pytest.raises(hs.HsError):
         hs.gauss_seidel(A2, dev(inputs.uniform_pm1(27, 1, 1200)), maxit=2, gs_schedule=2)
     with pytest.raises(hs.HsError):
-        hs.gauss_seidel(A2, dev(inputs.uniform_pm1(27, 1, 1200)), maxit=2, gs_schedule=3)
+        hs.gauss_seidel(A2, dev(inputs.uniform_pm1(27, 1, 1200)), maxit=2, gs_schedule=4)

@@ -597,3 +597,46 @@ def test_gs_tile_tables_closed_form_equals_counting_sort(shape):
     off, tiles = _gs_tables_closed_form(*shape)
     off2, tiles2 = _gs_tables_counting_sort(*shape)
     assert off == off2 and tiles == tiles2
+
+
+# ---------------------------------------------------------------- 2-D GS on a cluster
+
+def _gs2dc_work(nx, ny, C, nsw, bw, s, i):
+    """(sweep, row) pairs CTA by CTA for column i at step s, with the index
+    arithmetic of k_gs2dc (rows split over C CTAs, the t range of each CTA's
+    rows in the sweep's frame)."""
+    R = -(-ny // C)
+    out = []
+    for rank in range(C):
+        r0, r1 = min(ny, rank * R), min(ny, rank * R + R)
+        f0, f1 = (ny - r1, ny - r0) if bw else (r0, r1)
+        if f1 <= f0:
+            continue
+        t_lo = max(0, (s - i - f1 + 2) >> 1)
+        t_hi = min(nsw - 1, (s - i - f0) >> 1)
+        for t in range(t_lo, t_hi + 1):
+            r = s - 2 * t - i
+            if f0 <= r < f1:
+                jj = ny - 1 - r if bw else r
+                assert r0 <= jj < r1
+                out.append((t, r))
+    return out
+
+
+@pytest.mark.parametrize("nx,ny,C,nsw", [(8, 16, 8, 3), (5, 17, 8, 4), (12, 40, 8, 1), (3, 23, 4, 6), (128, 128, 8, 5)])
+@pytest.mark.parametrize("bw", [False, True])
+def test_gs2d_cluster_rows_cover_every_sweep_row_once(nx, ny, C, nsw, bw):
+    # at every step, the CTAs together handle exactly the (sweep, row) pairs
+    # of the one-block wavefront: row s - 2t - i of sweep t, for every sweep
+    # whose diagonal crosses column i
+    nsteps = (nx + ny - 2) + 1 + 2 * (nsw - 1)
+    seen = set()
+    for s in range(nsteps):
+        for i in range(nx):
+            got = _gs2dc_work(nx, ny, C, nsw, bw, s, i)
+            want = [(t, s - 2 * t - i) for t in range(nsw) if 0 <= s - 2 * t - i < ny]
+            assert sorted(got) == sorted(want), (s, i, got, want)
+            for t, r in got:
+                assert (t, r, i) not in seen
+                seen.add((t, r, i))
+    assert len(seen) == nsw * nx * ny
