@@ -1,4 +1,4 @@
-"""Gauss-Seidel on small 2-D grids by one thread-block cluster (csrc/hs_gs.cu,
+"""Gauss-Seidel on small 2-D grids by one thread-block cluster (csrc/hs_gs2d.cu,
 k_gs2dc: rows split over 8 CTAs, the south / north rows of other CTAs read
 through distributed shared memory, a cluster barrier per wavefront step)
 against the one-block kernel (max_blocks = 1), the tile schedule

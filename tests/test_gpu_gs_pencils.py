@@ -1,6 +1,6 @@
 """The pencil schedule of lexicographic Gauss-Seidel (hs_opts.gs_schedule = 2;
 the default for batches of four or more sweeps of one direction on 3-D
-constant-coefficient operators; csrc/hs_gs.cu, k_gsp) against the tile
+constant-coefficient operators; csrc/hs_gsp.cu, k_gsp) against the tile
 schedule (gs_schedule = 1) and the oracle.
 
 Both schedules apply the same two-part update to every node in an order that

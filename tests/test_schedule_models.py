@@ -285,7 +285,7 @@ def test_gs2d_schedule_model_catches_one_diagonal_shift():
 # ---------------------------------------------------------------- 7-point pencils
 
 def _model_gsp(shape, PY, PZ, W, dirs, seed, CH=3, PF=2, PFO=3, short_need=0, drop_old_side=False):
-    """The pencil schedule of the 7-point Gauss-Seidel kernel (hs_gs.cu,
+    """The pencil schedule of the 7-point Gauss-Seidel kernel (hs_gsp.cu,
     k_gsp).  A warp owns PY x PZ x-lines (lane = jl + PY kl) and sweeps them
     two nodes (a pair) per substep, lane (jl, kl) on sweep-frame pair u - D at
     substep u, D = jl + kl in the sweep's mirrored frame.  Neighbour lines of
