@@ -168,8 +168,20 @@ typedef struct {
                                Laplacian, upwind, HPCG 7-point; else
                                HS_ERR_INVALID); 3 one thread-block cluster
                                (2-D grids of at least 16 rows that fit, no
-                               max_blocks; else HS_ERR_INVALID).  All give
-                               bitwise the same iterates.                      */
+                               max_blocks; else HS_ERR_INVALID).  The HPCG
+                               27-point operator: 0 the plane-lagged schedule
+                               for single sweeps and the symmetric method when
+                               an x-y plane fits 200 KB of shared memory, the
+                               hyperplane schedule otherwise; 1 the hyperplane
+                               schedule (one grid-wide step per point
+                               hyperplane i + 2j + 4k, sweeps of one direction
+                               pipelined); 2 the plane-lagged schedule (whole
+                               z planes per block in shared memory, planes
+                               pipelined four in-plane steps apart; the plane
+                               must fit 200 KB with min(n_y, ceil(n_x / 2)) <=
+                               112, else HS_ERR_INVALID); 3
+                               HS_ERR_INVALID.  All give bitwise the same
+                               iterates.                                       */
 } hs_opts;
 
 typedef struct {

@@ -472,7 +472,7 @@ size_t gs_ws_vectors(const hs_op* A, hs_dtype dt) {
   size_t N = (size_t)(A->n[0] * A->n[1] * A->n[2]);
   size_t es = dt == HS_F64 ? 8 : 4;
   // 27-point sweep: b / a_ii and one progress word per block (hs_gs27.cu)
-  if (opkind_of(A) == OP_BOX27) return ((N * es + 255) & ~(size_t)255) + gs27_progress_bytes();
+  if (opkind_of(A) == OP_BOX27) return ((N * es + 255) & ~(size_t)255) + gs27_progress_bytes(A);
   int nt, P;
   gs_counts(A, &nt, &P);
   size_t ints = (size_t)nt + P + 1;

@@ -173,7 +173,7 @@ hs_status run_jacobi_tb(const SolveArgs& a, hs_result* res, double* hist);
 hs_status run_gauss_seidel(const SolveArgs& a, hs_result* res, double* hist);
 // 27-point operator: one step per point hyperplane i + 2j + 4k (hs_gs27.cu).
 hs_status run_gauss_seidel27(const SolveArgs& a, hs_result* res, double* hist);
-size_t gs27_progress_bytes();
+size_t gs27_progress_bytes(const hs_op* A);
 hs_status run_spmv(const hs_op* A, hs_dtype dt, const void* x, void* y, cudaStream_t st);
 hs_status run_residual_plain(const hs_op* A, hs_dtype dt, const void* b, const void* x, void* r, cudaStream_t st);
 size_t vark_coef_bytes(const hs_op* A, hs_dtype dt);

@@ -2,7 +2,9 @@
 HPCG's 7- and 27-point matrices (diagonal 27, -1 per neighbour), b = A 1,
 x0 = 0, absolute criterion ||r|| < 1e-6.  The 27-point operator runs on the
 box-sum tile engine (separable 3x3x3 sums); its lexicographic Gauss-Seidel on
-the point-hyperplane kernel (one step per i + 2j + 4k).
+the point-hyperplane kernel (one step per i + 2j + 4k; batches of four or more
+sweeps of one direction) or the plane-lagged kernel (single sweeps, short
+batches and the symmetric method; tests/test_gpu_gs27_planes.py).
 
 Tolerances: SpMV 1e-13 relative; Jacobi and GS iterates after k sweeps 1e-12
 (FP32 GS 2e-6);
@@ -105,8 +107,9 @@ GS27_SHAPES = [(37, 19, 11), (5, 4, 3), (1, 9, 7), (8, 1, 5), (6, 5, 1), (1, 1, 
 @pytest.mark.parametrize("shape", GS27_SHAPES)
 @pytest.mark.parametrize("mode", ["forward", "backward", "symmetric"])
 def test_hpcg27_gauss_seidel_sweeps(shape, mode):
-    # the 27-point sweep runs one step per point hyperplane i + 2j + 4k;
-    # tol = 0 pipelines all sweeps of a direction 8 hyperplanes apart
+    # 1 and 3 sweeps and the symmetric method take the plane-lagged kernel;
+    # 11 sweeps of one direction the hyperplane kernel, which pipelines them
+    # 8 hyperplanes apart
     A_o, A_g = ops(shape, 27)
     b = inputs.uniform_pm1(54, 1, A_o.N)
     x0 = inputs.uniform_pm1(55, 1, A_o.N)

@@ -10,7 +10,10 @@ executed on the CPU under random interleavings of the blocks.
 * 27-point (hs_gs27.cu): one step per point hyperplane i + 2j + 4k, z planes
   dealt to blocks round robin, sweeps of one direction pipelined 8
   hyperplanes apart; before a step with work a block waits until both ring
-  neighbours have completed the previous step.
+  neighbours have completed the previous step.  And the plane-lagged form
+  (k_gs27p): whole planes per block, in-plane steps i + 2j, each plane four
+  steps behind the one below it in the sweep and one sweep behind the one
+  above.
 
 Each block step is modelled as a read phase and a later write phase with
 other blocks' events in between, so a missing wait shows up as a value read
@@ -210,6 +213,104 @@ def test_gs27_ring_schedule_equals_sequential_sweeps(shape, G, batches):
 
 def test_gs27_model_detects_a_dropped_upper_wait():
     errs = [_model_gs27((9, 3, 11), 5, [(3, False)], seed=s, drop_upper_wait=True) for s in range(4)]
+    assert max(errs) > 1e-6
+
+
+def _model_gs27p(shape, G, dirs, seed, PUB=2, lag=4, drop_old_side=False):
+    """The plane-lagged 27-point schedule (hs_gs27.cu, k_gs27p).  Block g owns
+    planes k = g (mod G) and takes its items (t, k) sweep by sweep, planes in
+    the sweep's direction.  An item first waits until the old-side plane (k+1
+    forward, k-1 backward) has finished sweep t-1 (count >= t R), stages plane
+    k (a private copy, like shared memory), then runs the rem steps
+    r = i + 2j (sweep frame) in order: before step r it publishes its count
+    t R + r when r % PUB == 0 and waits until the new-side plane's count is
+    >= t R + min(r + lag, R); a step reads, then (after other blocks' events)
+    writes both the copy and the global iterate.  A finished plane publishes
+    (t + 1) R."""
+    nx, ny, nz = shape
+    R = (nx - 1) + 2 * (ny - 1) + 1
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(-1, 1, (nx, ny, nz))
+    b = rng.uniform(-1, 1, (nx, ny, nz))
+
+    def nbrs(p):
+        i, j, k = p
+        for dz, dy, dx in itertools.product((-1, 0, 1), repeat=3):
+            q = (i + dx, j + dy, k + dz)
+            if q != p and 0 <= q[0] < nx and 0 <= q[1] < ny and 0 <= q[2] < nz:
+                yield q
+
+    order = [(i, j, k) for k in range(nz) for j in range(ny) for i in range(nx)]
+    ref = _seq_sweeps(x, b, nbrs, order, dirs, 27.0)
+    G = min(G, nz)
+    prog = [0] * nz
+
+    def items(g):
+        for t, bw in enumerate(dirs):
+            ks = list(range(g, nz, G))
+            for k in (reversed(ks) if bw else ks):
+                yield t, k, bw
+
+    def block(g):
+        # a generator: yields whenever it has to wait or between a step's
+        # read and write phases, so that other blocks interleave
+        for t, k, bw in items(g):
+            kp, kn = (k + 1, k - 1) if bw else (k - 1, k + 1)
+            if 0 <= kn < nz and not drop_old_side:
+                while prog[kn] < t * R:
+                    yield
+            xs = x[:, :, k].copy()
+            for r in range(R):
+                if r > 0 and r % PUB == 0:
+                    prog[k] = t * R + r
+                if 0 <= kp < nz:
+                    while prog[kp] < t * R + min(r + lag, R):
+                        yield
+                nodes = []
+                for j in range(max(0, -(-(r - nx + 1) // 2)), min(ny - 1, r // 2) + 1):
+                    i = r - 2 * j
+                    nodes.append((nx - 1 - i, ny - 1 - j) if bw else (i, j))
+                new = []
+                for i, j in nodes:
+                    acc = b[i, j, k]
+                    for q in nbrs((i, j, k)):
+                        acc += xs[q[0], q[1]] if q[2] == k else x[q]
+                    new.append(acc / 27.0)
+                yield
+                for (i, j), v in zip(nodes, new):
+                    xs[i, j] = v
+                    x[i, j, k] = v
+            prog[k] = (t + 1) * R
+
+    gens = [block(g) for g in range(G)]
+    live = list(range(G))
+    rnd = random.Random(seed)
+    stalls = 0
+    while live:
+        g = rnd.choice(live)
+        before = list(prog)
+        try:
+            next(gens[g])
+        except StopIteration:
+            live.remove(g)
+        stalls = 0 if prog != before else stalls + 1
+        assert stalls < 200000, "no block can make progress"
+    return np.max(np.abs(x - ref))
+
+
+@pytest.mark.parametrize("shape", [(5, 4, 6), (1, 7, 9), (8, 1, 5), (3, 2, 13), (6, 5, 1)])
+@pytest.mark.parametrize("G", [1, 2, 3, 7])
+@pytest.mark.parametrize("dirs", [(False,), (True,), (False, False, False), (False, True, False, True),
+                                  (True, True, False)])
+def test_gs27_plane_lagged_schedule_equals_sequential_sweeps(shape, G, dirs):
+    assert _model_gs27p(shape, G, list(dirs), seed=hash((shape, G, dirs)) % 9973) < 1e-12
+
+
+@pytest.mark.parametrize("kw", [dict(lag=3), dict(drop_old_side=True)])
+def test_gs27p_model_detects_a_weakened_wait(kw):
+    # one plane per block, so that no block's own earlier planes imply the
+    # old-side wait
+    errs = [_model_gs27p((6, 4, 9), 9, [False, False, True], seed=s, **kw) for s in range(6)]
     assert max(errs) > 1e-6
 
 
