@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(GS27_THREADS) k_gs27(Gs27Args<T> a) {
 // ---------------------------------------------------------------------------
 
 #ifndef HS_GS27P_PUB
-#define HS_GS27P_PUB 2
+#define HS_GS27P_PUB 1
 #endif
 constexpr int GS27P_PUB = HS_GS27P_PUB;       // rem steps between publications
 constexpr size_t GS27P_SMEM_MAX = 200 * 1024;  // largest staged plane

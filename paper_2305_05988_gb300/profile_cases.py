@@ -6,8 +6,9 @@ CASE picks the kernel: spmv, jacobi, gs, cg, bicgstab, cg_nb (7-point, FP64,
 N^3 grid, b ~ U(-1, 1)); jacobi32 (the same in FP32); cg32v (FP32 CG on variable-coefficient diffusion,
 log k ~ N(0, 1), stored coefficients), cg32v_tma (the same with TMA-staged
 planes); gs2d (Gauss-Seidel on the N^2 Laplacian); hpcg27_spmv, hpcg27_jacobi,
-hpcg27_cg, hpcg27_bicgstab, hpcg27_gs (symmetric) and hpcg7_cg (the HPCG
-matrices of section 4.1 on 128 x 128 x N, b = A 1).  Each case first runs once to
+hpcg27_cg, hpcg27_bicgstab, hpcg27_gs (symmetric: the plane-lagged kernel),
+hpcg27_gs_hyper (symmetric on the point-hyperplane kernel) and hpcg7_cg (the
+HPCG matrices of section 4.1 on 128 x 128 x N, b = A 1).  Each case first runs once to
 warm up (CUDA context, workspace), then runs ITERS iterations (sweeps) once
 more: profile that second launch (ncu -s <launches of the first run> -c 1).
 Prints the wall time of the second run.
@@ -62,11 +63,13 @@ def main(argv):
         A = hs.Operator.hpcg(shape, 7 if case.startswith("hpcg7") else 27)
         b = A.spmv(torch.ones(A.N, dtype=torch.float64, device="cuda"))
         which = case.split("_", 1)[1]
+        gsk = dict(kw, mode="symmetric", gs_schedule=1 if which == "gs_hyper" else 0)
         run = {"spmv": lambda: A.spmv(b),
                "jacobi": lambda: hs.jacobi(A, b, maxit=iters, **kw),
                "cg": lambda: hs.cg(A, b, tol=0.0, maxit=iters, history=False, **kw),
                "bicgstab": lambda: hs.bicgstab(A, b, tol=0.0, maxit=iters, history=False, **kw),
-               "gs": lambda: hs.gauss_seidel(A, b, maxit=iters, mode="symmetric", **kw)}[which]
+               "gs": lambda: hs.gauss_seidel(A, b, maxit=iters, **gsk),
+               "gs_hyper": lambda: hs.gauss_seidel(A, b, maxit=iters, **gsk)}[which]
     else:
         raise SystemExit("unknown case %r" % case)
     run()
