@@ -463,7 +463,10 @@ hs_status hs_batch_team_sizes(const hs_batch *batch, int *teams);
  *   1  the Gauss-Seidel tile-dependency wait (a sweep count that nothing
  *      publishes),
  *   2  the 27-point Gauss-Seidel ring-neighbour wait (progress words that
- *      nothing publishes).
+ *      nothing publishes),
+ *   3  the waits of the plane-lagged 27-point Gauss-Seidel (a block's wait for
+ *      the plane above, its polling warp and the compute warps waiting on it,
+ *      for plane counts that nothing publishes).
  * timeout_s: the wait's limit, 0 < timeout_s <= 10 seconds.  Allocates 4 KB of
  * device memory for the call and synchronises `stream`.
  * Returns HS_ERR_TIMEOUT when the wait gave up as designed, HS_OK if it ended

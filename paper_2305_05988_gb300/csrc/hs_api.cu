@@ -251,8 +251,9 @@ const char* hs_version(void) { return "hsolve 0.1 (sm_103a)"; }
 int hs_last_staging(void) { return g_last_staging; }
 
 hs_status hs_diag_wait_timeout(int kind, double timeout_s, void* stream) {
-  if (kind < 0 || kind > 2) {
-    set_error("kind must be 0 (grid barrier), 1 (Gauss-Seidel tile wait) or 2 (27-point ring wait)");
+  if (kind < 0 || kind > 3) {
+    set_error("kind must be 0 (grid barrier), 1 (Gauss-Seidel tile wait), 2 (27-point ring wait) or 3 (27-point "
+              "plane waits)");
     return HS_ERR_INVALID;
   }
   if (!(timeout_s > 0.0) || timeout_s > 10.0) {
@@ -274,7 +275,8 @@ hs_status hs_diag_wait_timeout(int kind, double timeout_s, void* stream) {
   if (s == HS_OK) {
     if (kind == 0) s = diag_team_wait(cm.ctrl, cm.partials, st);
     else if (kind == 1) s = diag_gs_wait(cm.ctrl, reinterpret_cast<const unsigned*>(buf + 1024), st);
-    else s = diag_gs27_wait(cm.ctrl, reinterpret_cast<const unsigned long long*>(buf + 1024), st);
+    else if (kind == 2) s = diag_gs27_wait(cm.ctrl, reinterpret_cast<const unsigned long long*>(buf + 1024), st);
+    else s = diag_gs27p_wait(cm.ctrl, reinterpret_cast<unsigned long long*>(buf + 1024), st);
   }
   int status = 0;
   if (s == HS_OK) {

@@ -764,6 +764,36 @@ hs_status diag_gs27_wait(Ctrl* ctrl, const unsigned long long* words, cudaStream
   return e == cudaSuccess ? HS_OK : cuda_fail(e, "diagnostic launch");
 }
 
+// The plane-lagged waits on a plane count that nothing publishes
+// (diagnostic): lane 0 of warp 2 waits for an old-side plane (wait_count),
+// lane 0 of warp 1 polls a new-side plane (gs27p_sync) and compute thread 0
+// waits for the count the poller has seen (gs27p_wait_seen).
+__global__ void k_diag_gs27p(Ctrl* ctrl, unsigned long long* words) {
+  __shared__ volatile unsigned long long s_seen;
+  __shared__ volatile int s_done, s_fail;
+  if (threadIdx.x == 0) {
+    s_seen = 0;
+    s_done = 0;
+    s_fail = 0;
+  }
+  __syncthreads();
+  Gs27Args<double> a = {};
+  a.prog = words;
+  a.cm.ctrl = ctrl;
+  if (threadIdx.x == 0) gs27p_wait_seen(&s_seen, &s_fail, 1ull, ctrl);
+  if (threadIdx.x == 32) gs27p_sync(a, 1, 0, true, 0ull, 1, &s_seen, &s_done, &s_fail);
+  if (threadIdx.x == 64) {
+    unsigned long long v = 0;
+    wait_count(words + GS27P_PSTRIDE, 1ull, ctrl, &v);
+  }
+}
+
+hs_status diag_gs27p_wait(Ctrl* ctrl, unsigned long long* words, cudaStream_t st) {
+  k_diag_gs27p<<<1, 96, 0, st>>>(ctrl, words);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? HS_OK : cuda_fail(e, "diagnostic launch");
+}
+
 // Progress words: one per block (hyperplane schedule) or per z plane
 // (plane-lagged schedule).
 size_t gs27_progress_bytes(const hs_op* A) {

@@ -190,6 +190,7 @@ hs_status finish_solve_pub(const SolveArgs& sa, const Common& cm, const void* D,
 hs_status diag_team_wait(Ctrl* ctrl, double* partials, cudaStream_t st);       // hs_kernels.cu
 hs_status diag_gs_wait(Ctrl* ctrl, const unsigned* flag, cudaStream_t st);     // hs_gs.cu
 hs_status diag_gs27_wait(Ctrl* ctrl, const unsigned long long* words, cudaStream_t st);   // hs_gs27.cu
+hs_status diag_gs27p_wait(Ctrl* ctrl, unsigned long long* words, cudaStream_t st);         // hs_gs27.cu
 
 // Options with defaults filled in and validated (false: invalid, error set).
 bool merge_opts(const hs_opts* in, hs_opts* out);

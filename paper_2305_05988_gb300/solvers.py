@@ -302,7 +302,7 @@ def bicgstab(A: Operator, b, x0=None, tol: float = 1e-10, maxit: int = 10000, hi
     return _solve(_lib.HS_SOLVER_BICGSTAB, A, b, x0, tol, maxit, history, restart_eps=restart_eps, **kw)
 
 
-DIAG_WAITS = {"grid_barrier": 0, "gs_tile": 1, "gs27_ring": 2}
+DIAG_WAITS = {"grid_barrier": 0, "gs_tile": 1, "gs27_ring": 2, "gs27_planes": 3}
 
 
 def diag_wait_timeout(kind: str, timeout_s: float = 0.05) -> str:

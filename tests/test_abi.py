@@ -194,7 +194,7 @@ def test_cg_nb_and_batch_reject_bad_operators(lib):
 
 def test_diag_wait_validation(lib):
     # rejected before anything reaches the GPU
-    assert lib.hs_diag_wait_timeout(3, 0.1, None) == _lib.HS_ERR_INVALID
+    assert lib.hs_diag_wait_timeout(4, 0.1, None) == _lib.HS_ERR_INVALID
     assert lib.hs_diag_wait_timeout(-1, 0.1, None) == _lib.HS_ERR_INVALID
     assert lib.hs_diag_wait_timeout(0, 0.0, None) == _lib.HS_ERR_INVALID
     assert lib.hs_diag_wait_timeout(1, 10.5, None) == _lib.HS_ERR_INVALID

@@ -17,7 +17,7 @@ import paper_2305_05988_gb300 as hs  # noqa: E402
 from test_gpu_parity import dev, host, rel  # noqa: E402
 
 
-@pytest.mark.parametrize("kind", ["grid_barrier", "gs_tile", "gs27_ring"])
+@pytest.mark.parametrize("kind", ["grid_barrier", "gs_tile", "gs27_ring", "gs27_planes"])
 def test_wait_gives_up_and_context_survives(kind):
     t0 = time.time()
     status = hs.diag_wait_timeout(kind, timeout_s=0.05)
