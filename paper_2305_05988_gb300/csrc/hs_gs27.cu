@@ -366,7 +366,7 @@ constexpr size_t GS27P_SMEM_MAX = 200 * 1024;  // largest staged plane
 // progress words 128 bytes apart: each in a cache line of its own
 constexpr int GS27P_PSTRIDE = 16;
 
-// Thread 0: wait until *p >= target, bounded by the solve's timeout (status
+// One thread: wait until *p >= target, bounded by the solve's timeout (status
 // DS_TIMEOUT); ends early when another block has flagged an error.  The last
 // value read goes to *seen.
 __device__ __forceinline__ bool wait_count(const unsigned long long* p, unsigned long long target, Ctrl* ctrl,
