@@ -306,6 +306,15 @@ def test_gs27_plane_lagged_schedule_equals_sequential_sweeps(shape, G, dirs):
     assert _model_gs27p(shape, G, list(dirs), seed=hash((shape, G, dirs)) % 9973) < 1e-12
 
 
+@pytest.mark.parametrize("PUB", [1, 2])
+@pytest.mark.parametrize("lag", [4, 5])
+def test_gs27_plane_lagged_kernel_parameters(PUB, lag):
+    # the kernel publishes after every rem step and, loading each step's
+    # operands a step ahead, waits for one rem more than the data needs
+    for shape, G, dirs in (((7, 5, 11), 3, (False, False, True)), ((4, 9, 6), 2, (True, False, False))):
+        assert _model_gs27p(shape, G, list(dirs), seed=17 * PUB + lag, PUB=PUB, lag=lag) < 1e-12
+
+
 @pytest.mark.parametrize("kw", [dict(lag=3), dict(drop_old_side=True)])
 def test_gs27p_model_detects_a_weakened_wait(kw):
     # one plane per block, so that no block's own earlier planes imply the
