@@ -535,6 +535,7 @@ __device__ __forceinline__ void gs27p_fetch(const Gs27Args<T>& a, int r, int m, 
     sl.bD = side ? __ldcg(a.bD + sl.idx) : T(0);
   } else {
     sl.act = false;
+    sl.bD = T(0);
   }
 }
 
